@@ -1,0 +1,164 @@
+/*
+ * pbpqlp.h — C ABI of the GB300 (sm_103a) Projection-based Partial QLP library.
+ *
+ * The method (Kaloorazi & Chen, "Projection-based QLP Algorithm for
+ * Efficiently Computing Low-Rank Approximation of Matrices", Section III,
+ * Algorithm 3) factors a dense A (m x n) as A ~= Qa L Qb^T with Qa (m x l) and
+ * Qb (n x l) orthonormal and L (l x l) lower triangular, l = k + p (the
+ * paper's sampling size d), using q power iterations:
+ *     Phi = randn(m, l);  C = A^T Phi;  Pbar = orth(C);
+ *     repeat q times: C = A Pbar, Pbar = orth(C); C = A^T Pbar, Pbar = orth(C);
+ *     D = A Pbar;  [Qa, R] = qr(D);  [Ptil, Rtil] = qr(R^T);
+ *     Qb = Pbar Ptil;  L = Rtil^T.
+ * Every orth/qr is an unpivoted thin QR with diag(R) >= 0, so diag(L) >= 0.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major.  A has leading dimension lda >= n (elements).
+ *     Qa, Qb, L and the Gaussian Phi are contiguous (leading dimension l).
+ *   - Pointers named A, Qa, L, Qb, Ahat, omega, workspace are DEVICE pointers
+ *     the caller allocates and owns; pointers named *_host are host memory.
+ *   - Work is enqueued on the plan's CUDA stream and returns before it runs.
+ *     Argument errors are returned at once; numerical failures found on the
+ *     device (breakdown, non-finite data) are latched in a status word inside
+ *     the workspace and reported by pbpqlp_sync_status() or by the synchronous
+ *     calls (pbpqlp_error).
+ *   - A plan is used by one host thread / one stream at a time.  Nothing
+ *     throws across the ABI.  No entry point allocates device memory except
+ *     where stated.
+ */
+#ifndef PBPQLP_H
+#define PBPQLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    PBPQLP_OK = 0,
+    PBPQLP_EINVAL = 1,       /* bad argument (sizes, null pointers, modes) */
+    PBPQLP_ENOMEM = 2,       /* host allocation failed */
+    PBPQLP_ECUDA = 3,        /* a CUDA runtime call failed */
+    PBPQLP_ENONFINITE = 4,   /* NaN/Inf met in A or in an intermediate panel */
+    PBPQLP_EBREAKDOWN = 5,   /* orthonormalisation failed even after the shifted retries */
+    PBPQLP_ETIMEOUT = 6,     /* a bounded device wait gave up */
+    PBPQLP_EUNSUPPORTED = 7, /* mode / size not supported by this build */
+    PBPQLP_EWORKSPACE = 8    /* workspace missing or smaller than pbpqlp_workspace_bytes() */
+};
+
+/* Arithmetic modes of the three products with A (the sketch, the power
+ * iterations and the projection).  Gram accumulation, Cholesky and the final
+ * l x l QR are FP64 in every mode. */
+enum {
+    PBPQLP_MODE_FP64 = 0,    /* A FP64, FP64 products */
+    PBPQLP_MODE_BF16 = 1,    /* A and panels rounded to BF16, FP32 accumulate */
+    PBPQLP_MODE_BF16X3 = 2,  /* BF16 hi/lo split, three products hi*hi + lo*hi + hi*lo */
+    PBPQLP_MODE_TF32 = 3,    /* TF32 operands, FP32 accumulate */
+    PBPQLP_MODE_TF32X3 = 4   /* TF32 hi/lo split, three products */
+};
+
+/* Element type of A. */
+enum { PBPQLP_F64 = 0, PBPQLP_F32 = 1 };
+
+/* Methods of pbpqlp_error. */
+enum {
+    PBPQLP_ERR_IDENTITY = 0, /* sqrt(||A||_F^2 - ||L_r||_F^2) / ||A||_F (exact in exact arithmetic) */
+    PBPQLP_ERR_RESIDUAL = 1, /* ||A - Qa_r L_r Qb_r^T||_F / ||A||_F, formed explicitly */
+    PBPQLP_ERR_PROBES = 2    /* randomized estimate from Gaussian probes */
+};
+
+typedef struct pbpqlp_plan_s* pbpqlp_plan_t;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int pbpqlp_version(void);
+
+/* Human-readable text of a status code (static string; never NULL). */
+const char* pbpqlp_strerror(int status);
+
+/*
+ * Create a plan for one factorization shape (Algorithm 3 inputs).
+ *   m, n   : rows / columns of A (m, n >= 1).
+ *   k, p   : target rank and oversampling; l = k + p must satisfy
+ *            1 <= k <= l <= min(m, n) and l <= 256.
+ *   q      : power iterations, q >= 0 (q = 0 is the basic form, Eqs. 3-8).
+ *   seed   : seed of the Philox4x32-10 Gaussian stream of Phi.
+ *   mode   : PBPQLP_MODE_*.
+ *   stream : cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Host memory only; *out is owned by the caller and freed by
+ * pbpqlp_plan_destroy.  Returns PBPQLP_EINVAL on bad sizes.
+ */
+int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q,
+                uint64_t seed, int mode, void* stream);
+
+/* Release a plan (NULL is accepted). */
+int pbpqlp_plan_destroy(pbpqlp_plan_t plan);
+
+/* Bytes of device workspace pbpqlp_factor / _reconstruct / _error need
+ * (256-byte aligned base required).  Returns 0 for a NULL plan. */
+size_t pbpqlp_workspace_bytes(pbpqlp_plan_t plan);
+
+/*
+ * Write the Gaussian test matrix Phi (m x l, FP64, row-major) the plan's seed
+ * defines into the device buffer omega (Section III-A, randn(n1, d)).
+ * Element (i, j) is sample t = i*l + j of the stream: Philox4x32-10 block
+ * t/2 with counter {t/2 lo, t/2 hi, 0, 0} and key {seed lo, seed hi}; its
+ * words give u1 = (a53 + 1) 2^-53 and u2 = b53 2^-53, and sample t is
+ * sqrt(-2 ln u1) * (t even ? cos : sin)(2 pi u2)  (Box-Muller).
+ */
+int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
+
+/*
+ * Algorithm 3: factor A ~= Qa L Qb^T.
+ *   A         : device, m x n, row-major, leading dimension lda >= n,
+ *               element type a_dtype (PBPQLP_F64 in MODE_FP64; PBPQLP_F32 or
+ *               PBPQLP_F64 in the mixed modes).
+ *   workspace : device, >= pbpqlp_workspace_bytes(plan) bytes, 256-aligned;
+ *               ws_bytes is its size.  Contents are scratch between calls.
+ *   omega     : optional device m x l FP64 test matrix; NULL draws Phi from
+ *               the plan's seed (as pbpqlp_generate_omega).
+ *   Qa        : device, m x l FP64 output (orthonormal columns).
+ *   L         : device, l x l FP64 output, lower triangular, diag >= 0.
+ *   Qb        : device, n x l FP64 output (orthonormal columns).
+ * Asynchronous; device-side failures are read with pbpqlp_sync_status.
+ */
+int pbpqlp_factor(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
+                  void* workspace, size_t ws_bytes, const double* omega,
+                  double* Qa, double* L, double* Qb);
+
+/*
+ * Rank-r reconstruction Ahat = Qa[:, :r] L[:r, :r] Qb[:, :r]^T (Eq. 8 and its
+ * truncation), FP64, m x n row-major with leading dimension ldh >= n.
+ * 1 <= r <= l.  Uses the workspace (same size rule as pbpqlp_factor).
+ */
+int pbpqlp_reconstruct(pbpqlp_plan_t plan, const double* Qa, const double* L, const double* Qb,
+                       int r, double* Ahat, int64_t ldh, void* workspace, size_t ws_bytes);
+
+/*
+ * Relative Frobenius error of the rank-r truncation, returned in *rel_err
+ * (host).  Synchronous (waits on the plan's stream).  method is
+ * PBPQLP_ERR_IDENTITY, _RESIDUAL or _PROBES (nprobes Gaussian probes drawn
+ * from probe_seed).  A and a_dtype as in pbpqlp_factor.  Also returns any
+ * latched device status of the preceding factorization.
+ */
+int pbpqlp_error(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
+                 const double* Qa, const double* L, const double* Qb, int r,
+                 int method, int nprobes, uint64_t probe_seed,
+                 void* workspace, size_t ws_bytes, double* rel_err);
+
+/*
+ * Wait for the plan's stream and return the latched device status of the
+ * last pbpqlp_factor on this plan's workspace (PBPQLP_OK, _ENONFINITE,
+ * _EBREAKDOWN or _ETIMEOUT), then clear it.  *flags_host (optional) gets the
+ * raw status bits: 1 = a shifted Cholesky retry was used, 2 = breakdown after
+ * all retries, 4 = non-finite value, 8 = timeout.
+ */
+int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBPQLP_H */

@@ -1,0 +1,216 @@
+"""Python binding of the GB300 PbP-QLP library (argument marshalling only).
+
+Every function here forwards to the C ABI of ``libpbpqlp.so`` (declared in
+``include/pbpqlp.h``) under the same name.  Device buffers are torch CUDA
+tensors (or raw integer device addresses); the CUDA stream is torch's current
+stream unless one is given.  There is no CPU fallback: if the shared library
+is missing the import of the binding raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+PBPQLP_OK = 0
+PBPQLP_EINVAL = 1
+PBPQLP_ENOMEM = 2
+PBPQLP_ECUDA = 3
+PBPQLP_ENONFINITE = 4
+PBPQLP_EBREAKDOWN = 5
+PBPQLP_ETIMEOUT = 6
+PBPQLP_EUNSUPPORTED = 7
+PBPQLP_EWORKSPACE = 8
+
+PBPQLP_MODE_FP64 = 0
+PBPQLP_MODE_BF16 = 1
+PBPQLP_MODE_BF16X3 = 2
+PBPQLP_MODE_TF32 = 3
+PBPQLP_MODE_TF32X3 = 4
+
+PBPQLP_F64 = 0
+PBPQLP_F32 = 1
+
+PBPQLP_ERR_IDENTITY = 0
+PBPQLP_ERR_RESIDUAL = 1
+PBPQLP_ERR_PROBES = 2
+
+MAX_ELL = 224
+
+_lib = None
+
+
+class PbpqlpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, strerror(status), status))
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libpbpqlp.so (optionally building it first) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libpbpqlp.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, u64, sz, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_int
+    L.pbpqlp_version.argtypes = []
+    L.pbpqlp_version.restype = ci
+    L.pbpqlp_strerror.argtypes = [ci]
+    L.pbpqlp_strerror.restype = ctypes.c_char_p
+    L.pbpqlp_plan.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ci, u64, ci, vp]
+    L.pbpqlp_plan.restype = ci
+    L.pbpqlp_plan_destroy.argtypes = [vp]
+    L.pbpqlp_plan_destroy.restype = ci
+    L.pbpqlp_workspace_bytes.argtypes = [vp]
+    L.pbpqlp_workspace_bytes.restype = sz
+    L.pbpqlp_generate_omega.argtypes = [vp, vp]
+    L.pbpqlp_generate_omega.restype = ci
+    L.pbpqlp_factor.argtypes = [vp, vp, i64, ci, vp, sz, vp, vp, vp, vp]
+    L.pbpqlp_factor.restype = ci
+    L.pbpqlp_reconstruct.argtypes = [vp, vp, vp, vp, ci, vp, i64, vp, sz]
+    L.pbpqlp_reconstruct.restype = ci
+    L.pbpqlp_error.argtypes = [vp, vp, i64, ci, vp, vp, vp, ci, ci, ci, u64, vp, sz, ctypes.POINTER(ctypes.c_double)]
+    L.pbpqlp_error.restype = ci
+    L.pbpqlp_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.pbpqlp_sync_status.restype = ci
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return load().pbpqlp_strerror(int(status)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, where):
+    if rc != PBPQLP_OK:
+        raise PbpqlpError(rc, where)
+
+
+# ------------------------------------------------------------------ C ABI names
+def pbpqlp_version() -> int:
+    return load().pbpqlp_version()
+
+
+def pbpqlp_plan(m, n, k, p, q, seed, mode=PBPQLP_MODE_FP64, stream=None):
+    """Create a plan; returns the opaque handle (ctypes.c_void_p)."""
+    h = ctypes.c_void_p()
+    _check(load().pbpqlp_plan(ctypes.byref(h), int(m), int(n), int(k), int(p), int(q),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(mode), _stream(stream)), "pbpqlp_plan")
+    return h
+
+
+def pbpqlp_plan_destroy(plan):
+    _check(load().pbpqlp_plan_destroy(plan), "pbpqlp_plan_destroy")
+
+
+def pbpqlp_workspace_bytes(plan) -> int:
+    return int(load().pbpqlp_workspace_bytes(plan))
+
+
+def pbpqlp_generate_omega(plan, omega):
+    _check(load().pbpqlp_generate_omega(plan, _ptr(omega)), "pbpqlp_generate_omega")
+
+
+def pbpqlp_factor(plan, A, lda, a_dtype, workspace, ws_bytes, omega, Qa, L, Qb):
+    _check(load().pbpqlp_factor(plan, _ptr(A), int(lda), int(a_dtype), _ptr(workspace), int(ws_bytes),
+                                _ptr(omega), _ptr(Qa), _ptr(L), _ptr(Qb)), "pbpqlp_factor")
+
+
+def pbpqlp_reconstruct(plan, Qa, L, Qb, r, Ahat, ldh, workspace, ws_bytes):
+    _check(load().pbpqlp_reconstruct(plan, _ptr(Qa), _ptr(L), _ptr(Qb), int(r), _ptr(Ahat), int(ldh),
+                                     _ptr(workspace), int(ws_bytes)), "pbpqlp_reconstruct")
+
+
+def pbpqlp_error(plan, A, lda, a_dtype, Qa, L, Qb, r, method, nprobes, probe_seed, workspace, ws_bytes) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().pbpqlp_error(plan, _ptr(A), int(lda), int(a_dtype), _ptr(Qa), _ptr(L), _ptr(Qb), int(r),
+                               int(method), int(nprobes), int(probe_seed) & 0xFFFFFFFFFFFFFFFF,
+                               _ptr(workspace), int(ws_bytes), ctypes.byref(out)), "pbpqlp_error")
+    return out.value
+
+
+def pbpqlp_sync_status(plan):
+    """Returns (status, flags)."""
+    f = ctypes.c_uint32(0)
+    rc = load().pbpqlp_sync_status(plan, ctypes.byref(f))
+    return rc, int(f.value)
+
+
+# ------------------------------------------------------- torch convenience layer
+class Plan:
+    """Owns a plan handle and a torch-allocated workspace for one shape."""
+
+    def __init__(self, m, n, k, p, q, seed, mode=PBPQLP_MODE_FP64, stream=None, device="cuda"):
+        import torch
+        self.m, self.n, self.k, self.p, self.q, self.l = int(m), int(n), int(k), int(p), int(q), int(k) + int(p)
+        self.seed, self.mode = int(seed), int(mode)
+        self.handle = pbpqlp_plan(m, n, k, p, q, seed, mode, stream)
+        self.ws_bytes = pbpqlp_workspace_bytes(self.handle)
+        # 256-byte aligned: torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+    def outputs(self, device="cuda"):
+        import torch
+        f = torch.float64
+        return (torch.empty(self.m, self.l, dtype=f, device=device), torch.empty(self.l, self.l, dtype=f, device=device),
+                torch.empty(self.n, self.l, dtype=f, device=device))
+
+    def factor(self, A, omega=None, out=None):
+        import torch
+        a_dtype = PBPQLP_F32 if A.dtype == torch.float32 else PBPQLP_F64
+        Qa, L, Qb = out if out is not None else self.outputs(A.device)
+        pbpqlp_factor(self.handle, A, A.stride(0), a_dtype, self.workspace, self.ws_bytes, omega, Qa, L, Qb)
+        return Qa, L, Qb
+
+    def omega(self, device="cuda"):
+        import torch
+        o = torch.empty(self.m, self.l, dtype=torch.float64, device=device)
+        pbpqlp_generate_omega(self.handle, o)
+        return o
+
+    def reconstruct(self, Qa, L, Qb, r=None):
+        import torch
+        r = self.k if r is None else r
+        Ahat = torch.empty(self.m, self.n, dtype=torch.float64, device=Qa.device)
+        pbpqlp_reconstruct(self.handle, Qa, L, Qb, r, Ahat, self.n, self.workspace, self.ws_bytes)
+        return Ahat
+
+    def error(self, A, Qa, L, Qb, r=None, method=PBPQLP_ERR_RESIDUAL, nprobes=10, probe_seed=0):
+        import torch
+        r = self.k if r is None else r
+        a_dtype = PBPQLP_F32 if A.dtype == torch.float32 else PBPQLP_F64
+        return pbpqlp_error(self.handle, A, A.stride(0), a_dtype, Qa, L, Qb, r, method, nprobes, probe_seed,
+                            self.workspace, self.ws_bytes)
+
+    def sync_status(self):
+        return pbpqlp_sync_status(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.pbpqlp_plan_destroy(h)
+            self.handle = None

@@ -1,0 +1,78 @@
+// Internal launcher interface of the PbP-QLP CUDA library (not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pbq {
+
+constexpr int kMaxEll = 224;          // l = k + p limit (packed l x l factor fits one SM's smem)
+constexpr int kGemmBM = 64;           // rows per CTA tile of the skinny FP64 GEMM
+constexpr int kGemmBK = 16;           // contraction depth per shared-memory stage
+
+// Device status bits (latched in the workspace status word).
+constexpr uint32_t kStShifted = 1u;    // a shifted Cholesky retry was used
+constexpr uint32_t kStBreakdown = 2u;  // Cholesky failed even with the shift
+constexpr uint32_t kStNonFinite = 4u;  // NaN/Inf met
+constexpr uint32_t kStTimeout = 8u;    // bounded wait gave up
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int64_t packed_tri(int l) { return (int64_t)l * (l + 1) / 2; }
+
+// ---- FP64 kernels (kernels_fp64.cu) -------------------------------------
+// Phi[i*ld + j] = sample (i*l + j) of the Philox4x32-10 / Box-Muller stream.
+cudaError_t launch_gaussian(uint64_t seed, int64_t rows, int l, double* out, int64_t ld, cudaStream_t s);
+
+// C (M x N) = op(A) B, op(A) = A (M x K, lda) or A^T (A stored K x M).  B is K x N (ldb).
+// With S > 1 the contraction is split in S chunks of kchunk rows; chunk s
+// writes C + s*part_stride (a partial sum) and reduce_partials adds them in
+// chunk order.  N <= kMaxEll.  cond (device, optional): skip when *cond == 0.
+cudaError_t launch_dgemm_skinny(bool transA, int64_t M, int N, int64_t K, const double* A, int64_t lda,
+                                const double* B, int64_t ldb, double* C, int64_t ldc, int S, int64_t kchunk,
+                                int64_t part_stride, const int* cond, cudaStream_t s);
+// Max resident CTAs per SM of the skinny GEMM for this N.
+int dgemm_skinny_occupancy(int N);
+
+// C[i*ldc + c] = sum_{s<S} part[s*part_stride + i*ldp + c]  (fixed order; deterministic).
+cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, int64_t part_stride,
+                                   int64_t ldp, double* C, int64_t ldc, const int* cond, cudaStream_t s);
+
+// One-CTA Cholesky G = R^T R of the l x l Gram (ld l) of a rows x l panel.
+// Writes R packed (upper, row-major packed) plus 1/diag (l values after the
+// packed triangle).  On a pivot below tau*G0_jj retries once on G + shift*I
+// (shifted CholeskyQR, Fukaya et al. 2020).  ctl layout: see kernels_fp64.cu.
+cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rpacked, uint32_t* status,
+                            int* ctl, int pass, cudaStream_t s);
+
+// Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels.
+cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rpacked, const double* X, int64_t ldx,
+                             double* Y, int64_t ldy, const int* cond, cudaStream_t s);
+
+// One-CTA Householder QR of R^T (R upper, l x l dense ld l, only upper part read):
+// R^T = Ptil Rtil with diag(Rtil) >= 0.  Writes L = Rtil^T (l x l, ld l) and
+// Ptil (l x l row-major, ld l).  work: 2*l*l + 2*l doubles.
+cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s);
+
+// Zero the strictly-lower part of an l x l matrix (ld l) in place.
+cudaError_t launch_triu(int l, double* R, cudaStream_t s);
+
+// C (M x N) = A (M x K) B^T with B stored N x K; general N (reconstruction).
+// If Aref != nullptr, C is not written; instead per-CTA partial sums of
+// (Aref - A B^T)^2 go to sqpart[blockId] (FP64).  Returns the CTA count via *nblocks.
+cudaError_t launch_dgemm_nt(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B,
+                            int64_t ldb, double* C, int64_t ldc, const void* Aref, int aref_f32,
+                            int64_t ldref, double* sqpart, int* nblocks, cudaStream_t s);
+
+// Sum of squares of a rows x cols matrix X (FP64 or FP32 elements), minus
+// Ysub (FP64) when given: per-CTA partials to part[0..nb) (nb <= 1024) then a
+// one-CTA sum to out[0].  Fixed reduction order (deterministic).
+cudaError_t launch_sumsq(int64_t rows, int64_t cols, const void* X, int x_f32, int64_t ldx, const double* Ysub,
+                         int64_t ldy, double* part, double* out, cudaStream_t s);
+// out[0] = sum of part[0..n) in index order (one CTA).
+cudaError_t launch_sum(int n, const double* part, double* out, cudaStream_t s);
+
+// Copy a rows x cols FP64 block between leading dimensions.
+cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
+                   cudaStream_t s);
+
+}  // namespace pbq

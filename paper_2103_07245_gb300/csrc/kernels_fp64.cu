@@ -1,0 +1,618 @@
+// FP64 kernels of the PbP-QLP path (Algorithm 3): Gaussian test matrix,
+// skinny DFMA GEMMs for the products with A and A^T, deterministic split-K
+// reduction, CholeskyQR passes (Gram -> Cholesky -> row-wise triangular
+// solve) with a shifted retry, and the one-CTA Householder QR of R^T.
+//
+// GB300 has 2 FP64 FMA lanes per SM per clock (~1.2 TFLOP/s for the chip), so
+// every FP64 kernel here is DFMA-issue bound and the tiling aims at keeping
+// all 152 SMs issuing DFMAs with no wasted (padded) lanes.
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace pbq {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+__global__ void k_gaussian(uint64_t seed, int64_t rows, int l, double* __restrict__ out, int64_t ld) {
+    const int64_t total = rows * (int64_t)l;
+    const int64_t npairs = (total + 1) / 2;
+    const double inv53 = 1.0 / 9007199254740992.0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npairs;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)b, (uint32_t)((uint64_t)b >> 32), 0u, 0u};
+        philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t a53 = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);
+        const uint64_t b53 = ((uint64_t)(c[2] >> 5) << 26) | (uint64_t)(c[3] >> 6);
+        const double u1 = ((double)a53 + 1.0) * inv53;
+        const double u2 = (double)b53 * inv53;
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const int64_t t0 = 2 * b;
+        out[(t0 / l) * ld + (t0 % l)] = rad * cs;
+        if (t0 + 1 < total) out[((t0 + 1) / l) * ld + ((t0 + 1) % l)] = rad * sn;
+    }
+}
+
+cudaError_t launch_gaussian(uint64_t seed, int64_t rows, int l, double* out, int64_t ld, cudaStream_t s) {
+    const int64_t npairs = (rows * (int64_t)l + 1) / 2;
+    int64_t blocks = (npairs + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_gaussian<<<(unsigned)blocks, 256, 0, s>>>(seed, rows, l, out, ld);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Skinny FP64 GEMM: C (M x N, N <= 224) = op(A) B.  256 threads = 16 column
+// lanes x 16 row groups; a thread owns 4 rows x TN columns (column stride 16),
+// so the CTA tile is 64 x 16*TN and TN = ceil(N/16) wastes < 16 columns.
+// The split-K index is blockIdx.y.
+// ---------------------------------------------------------------------------
+template <int TN, bool TA>
+__global__ void __launch_bounds__(256)
+k_dgemm_skinny(int64_t M, int N, int64_t K, const double* __restrict__ A, int64_t lda,
+               const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc,
+               int64_t kchunk, int64_t part_stride, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    constexpr int BM = kGemmBM, BK = kGemmBK, BN = 16 * TN;
+    __shared__ double As[BK][BM];
+    __shared__ double Bs[BK][BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
+
+    double acc[4][TN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = 0.0;
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + 256 * i;
+            int r, kk;
+            if (!TA) { r = idx >> 4; kk = idx & 15; }
+            else     { kk = idx >> 6; r = idx & 63; }
+            const int64_t gm = m0 + r, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < kend) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+            As[kk][r] = v;
+        }
+        for (int idx = tid; idx < BK * BN; idx += 256) {
+            const int kk = idx / BN, c = idx - kk * BN;
+            const int64_t gk = k0 + kk;
+            Bs[kk][c] = (c < N && gk < kend) ? B[gk * ldb + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[TN];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < TN; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double* Cb = C + (int64_t)blockIdx.y * part_stride;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gm = m0 + ty * 4 + r;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int col = tx + 16 * c;
+            if (col < N) Cb[gm * ldc + col] = acc[r][c];
+        }
+    }
+}
+
+template <bool TA>
+static cudaError_t dispatch_dgemm(int TN, dim3 grid, int64_t M, int N, int64_t K, const double* A, int64_t lda,
+                                  const double* B, int64_t ldb, double* C, int64_t ldc, int64_t kchunk,
+                                  int64_t ps, const int* cond, cudaStream_t s) {
+#define PBQ_CASE(T) case T: k_dgemm_skinny<T, TA><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk, ps, cond); break;
+    switch (TN) {
+        PBQ_CASE(1) PBQ_CASE(2) PBQ_CASE(3) PBQ_CASE(4) PBQ_CASE(5) PBQ_CASE(6) PBQ_CASE(7)
+        PBQ_CASE(8) PBQ_CASE(9) PBQ_CASE(10) PBQ_CASE(11) PBQ_CASE(12) PBQ_CASE(13) PBQ_CASE(14)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PBQ_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dgemm_skinny(bool transA, int64_t M, int N, int64_t K, const double* A, int64_t lda,
+                                const double* B, int64_t ldb, double* C, int64_t ldc, int S, int64_t kchunk,
+                                int64_t part_stride, const int* cond, cudaStream_t s) {
+    if (N < 1 || N > kMaxEll || M < 1 || S < 1) return cudaErrorInvalidValue;
+    const int TN = (N + 15) / 16;
+    dim3 grid((unsigned)((M + kGemmBM - 1) / kGemmBM), (unsigned)S);
+    return transA ? dispatch_dgemm<true>(TN, grid, M, N, K, A, lda, B, ldb, C, ldc, kchunk, part_stride, cond, s)
+                  : dispatch_dgemm<false>(TN, grid, M, N, K, A, lda, B, ldb, C, ldc, kchunk, part_stride, cond, s);
+}
+
+int dgemm_skinny_occupancy(int N) {
+    const int TN = (N + 15) / 16;
+    int occ = 1;
+    cudaError_t e = cudaSuccess;
+#define PBQ_OCC(T) case T: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dgemm_skinny<T, false>, 256, 0); break;
+    switch (TN) {
+        PBQ_OCC(1) PBQ_OCC(2) PBQ_OCC(3) PBQ_OCC(4) PBQ_OCC(5) PBQ_OCC(6) PBQ_OCC(7)
+        PBQ_OCC(8) PBQ_OCC(9) PBQ_OCC(10) PBQ_OCC(11) PBQ_OCC(12) PBQ_OCC(13) PBQ_OCC(14)
+        default: break;
+    }
+#undef PBQ_OCC
+    if (e != cudaSuccess || occ < 1) occ = 1;
+    return occ;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic split-K reduction.
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_partials(int64_t M, int N, int S, const double* __restrict__ part, int64_t ps,
+                                  int64_t ldp, double* __restrict__ C, int64_t ldc, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    const int64_t total = M * (int64_t)N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / N;
+        const int c = (int)(e - i * N);
+        const double* p = part + i * ldp + c;
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += p[(int64_t)s * ps];
+        C[i * ldc + c] = acc;
+    }
+}
+
+cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, int64_t ps, int64_t ldp,
+                                   double* C, int64_t ldc, const int* cond, cudaStream_t s) {
+    const int64_t total = M * (int64_t)N;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_reduce_partials<<<(unsigned)blocks, 256, 0, s>>>(M, N, S, part, ps, ldp, C, ldc, cond);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of the l x l Gram in shared memory (packed upper triangle).
+// ctl (ints): ctl[p] = 1 if pass p (1-based) used the shift; ctl[8 + j] = 1 if
+// pass pair j (passes 2j-1, 2j) must run.  Pair 1 always runs; pair j+1 runs
+// iff a pass of pair j was shifted.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t pidx(int l, int a, int b) {
+    return (int64_t)a * (2 * l - a + 1) / 2 + (b - a);
+}
+
+__global__ void __launch_bounds__(1024)
+k_cholesky(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
+           uint32_t* __restrict__ status, int* __restrict__ ctl, int pass) {
+    if (pass >= 3 && ctl[8 + (pass + 1) / 2] == 0) return;
+    extern __shared__ double sm[];
+    const int64_t P = (int64_t)l * (l + 1) / 2;
+    double* S = sm;
+    double* dg0 = sm + P;
+    double* dinv = dg0 + l;
+    __shared__ int s_fail;
+    __shared__ double s_inv, s_shift;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    const double tau = 1e-12;
+
+    for (int j = tid; j < l; j += nth) dg0[j] = G[(int64_t)j * l + j];
+    if (tid == 0) { s_shift = 0.0; s_fail = 0; }
+    __syncthreads();
+
+    int shifted = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const double shift = s_shift;
+        for (int a = warp; a < l; a += nwarp)
+            for (int b = a + lane; b < l; b += 32)
+                S[pidx(l, a, b)] = G[(int64_t)a * l + b] + (a == b ? shift : 0.0);
+        if (tid == 0) s_fail = 0;
+        __syncthreads();
+        for (int j = 0; j < l; ++j) {
+            if (tid == 0) {
+                const double d = S[pidx(l, j, j)];
+                const double thr = (attempt == 0) ? tau * dg0[j] : 0.0;
+                if (!isfinite(d)) s_fail = 2;
+                else if (!(d > thr)) s_fail = 1;
+                else {
+                    const double r = sqrt(d);
+                    S[pidx(l, j, j)] = r;
+                    s_inv = 1.0 / r;
+                    dinv[j] = s_inv;
+                }
+            }
+            __syncthreads();
+            if (s_fail) break;
+            const double inv = s_inv;
+            const int64_t rj = pidx(l, j, 0);
+            for (int c = j + 1 + tid; c < l; c += nth) S[rj + c] *= inv;
+            __syncthreads();
+            for (int a = j + 1 + warp; a < l; a += nwarp) {
+                const double rja = S[rj + a];
+                const int64_t ra = pidx(l, a, 0);
+                for (int b = a + lane; b < l; b += 32) S[ra + b] -= rja * S[rj + b];
+            }
+            __syncthreads();
+        }
+        const int fail = s_fail;
+        __syncthreads();
+        if (!fail) break;
+        if (fail == 2 || attempt == 1) {
+            if (tid == 0) atomicOr(status, fail == 2 ? kStNonFinite : kStBreakdown);
+            // leave a finite identity factor so later kernels stay finite
+            for (int a = warp; a < l; a += nwarp)
+                for (int b = a + lane; b < l; b += 32) S[pidx(l, a, b)] = (a == b) ? 1.0 : 0.0;
+            for (int j = tid; j < l; j += nth) dinv[j] = 1.0;
+            __syncthreads();
+            break;
+        }
+        // shifted retry: G + s I, s = 11 (rows*l + l(l+1)) u tr(G)  (u = 2^-53)
+        if (tid == 0) {
+            double tr = 0.0;
+            for (int j = 0; j < l; ++j) tr += dg0[j];
+            double sh = 11.0 * ((double)rows * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
+            if (!(sh > 0.0) || !isfinite(sh)) sh = 1.0;  // all-zero panel: any factor will do
+            s_shift = sh;
+        }
+        shifted = 1;
+        __syncthreads();
+    }
+    for (int64_t e = tid; e < P; e += nth) Rp[e] = S[e];
+    for (int j = tid; j < l; j += nth) Rp[P + j] = dinv[j];
+    if (tid == 0) {
+        ctl[pass] = shifted;
+        if ((pass & 1) == 0) ctl[8 + pass / 2 + 1] = (ctl[pass - 1] | ctl[pass]) ? 1 : 0;
+        if (shifted) atomicOr(status, kStShifted);
+    }
+}
+
+cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rp, uint32_t* status, int* ctl, int pass,
+                            cudaStream_t s) {
+    const size_t smem = (size_t)(packed_tri(l) + 2 * (int64_t)l) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cholesky<<<1, 1024, smem, s>>>(l, rows, G, Rp, status, ctl, pass);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Y = X R^{-1}: one warp per row, forward substitution y_t = x_t / r_tt then
+// x_c -= y_t r_tc (c > t); lane owns columns lane + 32u.  R (packed) and
+// 1/diag(R) sit in shared memory.
+// ---------------------------------------------------------------------------
+template <int U>
+__global__ void __launch_bounds__(256)
+k_trsm_rows(int64_t rows, int l, const double* __restrict__ Rp, const double* __restrict__ X, int64_t ldx,
+            double* __restrict__ Y, int64_t ldy, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    extern __shared__ double sR[];
+    const int64_t P = (int64_t)l * (l + 1) / 2;
+    for (int64_t e = threadIdx.x; e < P + l; e += blockDim.x) sR[e] = Rp[e];
+    __syncthreads();
+    const double* dinv = sR + P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < rows; r += (int64_t)gridDim.x * 8) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = lane + 32 * u;
+            x[u] = (c < l) ? X[r * ldx + c] : 0.0;
+        }
+#pragma unroll
+        for (int u0 = 0; u0 < U; ++u0) {
+            for (int tt = 0; tt < 32; ++tt) {
+                const int t = 32 * u0 + tt;
+                if (t >= l) break;
+                const double y = __shfl_sync(0xffffffffu, x[u0], tt) * dinv[t];
+                if (lane == tt) x[u0] = y;
+                const int64_t rt = pidx(l, t, 0);
+#pragma unroll
+                for (int u = u0; u < U; ++u) {
+                    const int c = lane + 32 * u;
+                    if (c > t && c < l) x[u] -= y * sR[rt + c];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = lane + 32 * u;
+            if (c < l) Y[r * ldy + c] = x[u];
+        }
+    }
+}
+
+cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double* X, int64_t ldx, double* Y,
+                             int64_t ldy, const int* cond, cudaStream_t s) {
+    const size_t smem = (size_t)(packed_tri(l) + l) * sizeof(double);
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 152 * 2) blocks = 152 * 2;
+    if (blocks < 1) blocks = 1;
+    const int U = (l + 31) / 32;
+    cudaError_t e = cudaSuccess;
+#define PBQ_TR(UU) case UU: \
+        e = cudaFuncSetAttribute(k_trsm_rows<UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e; \
+        k_trsm_rows<UU><<<(unsigned)blocks, 256, smem, s>>>(rows, l, Rp, X, ldx, Y, ldy, cond); break;
+    switch (U) {
+        PBQ_TR(1) PBQ_TR(2) PBQ_TR(3) PBQ_TR(4) PBQ_TR(5) PBQ_TR(6) PBQ_TR(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PBQ_TR
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of W = R^T (Eq. 7), one CTA.  The kernel stores W transposed
+// (Wt = R, so a column of W is a contiguous row of Wt); reflector j (entries
+// i >= j) is row j of V.  Rtil = upper(W) with signs fixed to diag >= 0,
+// L = Rtil^T, Ptil = H_0 ... H_{l-1} [I] with the matching column signs.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_small_qr(int l, const double* __restrict__ R, double* __restrict__ L, double* __restrict__ Ptil,
+           double* __restrict__ work) {
+    double* Wt = work;
+    double* V = Wt + (int64_t)l * l;
+    double* Pt = V + (int64_t)l * l;   // Ptil transposed: row c = column c of Ptil
+    double* vv = Pt + (int64_t)l * l;
+    double* sg = vv + l;
+    __shared__ double s_alpha;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    const int64_t ll = (int64_t)l * l;
+    for (int64_t e = tid; e < ll; e += nth) {
+        const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
+        Wt[e] = (i >= c) ? R[e] : 0.0;
+        V[e] = 0.0;
+        Pt[e] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < l; ++j) {
+        double* wj = Wt + (int64_t)j * l;
+        if (warp == 0) {
+            double t = 0.0;
+            for (int i = j + 1 + lane; i < l; i += 32) t += wj[i] * wj[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) {
+                const double x0 = wj[j];
+                const double nrm = sqrt(x0 * x0 + t);
+                if (nrm == 0.0) { vv[j] = 0.0; s_alpha = 0.0; }
+                else {
+                    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+                    const double v0 = x0 - alpha;
+                    V[(int64_t)j * l + j] = v0;
+                    vv[j] = v0 * v0 + t;
+                    s_alpha = alpha;
+                }
+            }
+        }
+        __syncthreads();
+        double* vj = V + (int64_t)j * l;
+        for (int i = j + 1 + tid; i < l; i += nth) vj[i] = wj[i];
+        __syncthreads();
+        const double vvj = vv[j];
+        if (vvj != 0.0) {
+            for (int c = j + 1 + warp; c < l; c += nwarp) {
+                double* wc = Wt + (int64_t)c * l;
+                double d = 0.0;
+                for (int i = j + lane; i < l; i += 32) d += vj[i] * wc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                const double f = 2.0 * d / vvj;
+                for (int i = j + lane; i < l; i += 32) wc[i] -= f * vj[i];
+            }
+            if (tid == 0) wj[j] = s_alpha;
+            for (int i = j + 1 + tid; i < l; i += nth) wj[i] = 0.0;
+        }
+        __syncthreads();
+    }
+    // Ptil = H_0 ... H_{l-1} [I]: columns c < j are untouched unit vectors at step j.
+    for (int j = l - 1; j >= 0; --j) {
+        const double vvj = vv[j];
+        if (vvj != 0.0) {
+            const double* vj = V + (int64_t)j * l;
+            for (int c = j + warp; c < l; c += nwarp) {
+                double* pc = Pt + (int64_t)c * l;
+                double d = 0.0;
+                for (int i = j + lane; i < l; i += 32) d += vj[i] * pc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                const double f = 2.0 * d / vvj;
+                for (int i = j + lane; i < l; i += 32) pc[i] -= f * vj[i];
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < l; j += nth) sg[j] = (Wt[(int64_t)j * l + j] < 0.0) ? -1.0 : 1.0;
+    __syncthreads();
+    // L[b][a] = Rtil[a][b] = sg[a] * W[a][b] = sg[a] * Wt[b][a]  (b >= a)
+    for (int64_t e = tid; e < ll; e += nth) {
+        const int b = (int)(e / l), a = (int)(e - (int64_t)b * l);
+        L[e] = (b >= a) ? sg[a] * Wt[e] : 0.0;
+        // Ptil[i][c] = sg[c] * Pt[c][i]  with (i, c) = (b, a)
+        Ptil[e] = sg[a] * Pt[(int64_t)a * l + b];
+    }
+}
+
+cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s) {
+    k_small_qr<<<1, 1024, 0, s>>>(l, R, L, Ptil, work);
+    return cudaGetLastError();
+}
+
+__global__ void k_triu(int l, double* R) {
+    const int64_t ll = (int64_t)l * l;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ll; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / l), j = (int)(e - (int64_t)i * l);
+        if (j < i) R[e] = 0.0;
+    }
+}
+
+cudaError_t launch_triu(int l, double* R, cudaStream_t s) {
+    k_triu<<<64, 256, 0, s>>>(l, R);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// General C = A B^T (reconstruction), 64 x 64 tiles, 4 x 4 per thread, with
+// an optional fused residual epilogue sum((Aref - A B^T)^2) per CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_dgemm_nt(int64_t M, int64_t N, int K, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+           int64_t ldb, double* __restrict__ C, int64_t ldc, const void* __restrict__ Aref, int aref_f32,
+           int64_t ldref, double* __restrict__ sqpart) {
+    __shared__ double As[16][64];
+    __shared__ double Bs[16][64];
+    __shared__ double red[8];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 64;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + 256 * i, r = idx >> 4, kk = idx & 15;
+            const int gk = k0 + kk;
+            As[kk][r] = (m0 + r < M && gk < K) ? A[(m0 + r) * lda + gk] : 0.0;
+            Bs[kk][r] = (n0 + r < N && gk < K) ? B[(n0 + r) * ldb + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double sq = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gm = m0 + ty * 4 + r;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t gn = n0 + tx + 16 * c;
+            if (gn >= N) continue;
+            if (Aref) {
+                const double ref = aref_f32 ? (double)((const float*)Aref)[gm * ldref + gn]
+                                            : ((const double*)Aref)[gm * ldref + gn];
+                const double d = ref - acc[r][c];
+                sq += d * d;
+            } else {
+                C[gm * ldc + gn] = acc[r][c];
+            }
+        }
+    }
+    if (Aref) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((tid & 31) == 0) red[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[w];
+            sqpart[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+    }
+}
+
+cudaError_t launch_dgemm_nt(int64_t M, int64_t N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                            double* C, int64_t ldc, const void* Aref, int aref_f32, int64_t ldref, double* sqpart,
+                            int* nblocks, cudaStream_t s) {
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+    if (nblocks) *nblocks = (int)(grid.x * grid.y);
+    k_dgemm_nt<<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, Aref, aref_f32, ldref, sqpart);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic sums of squares.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_sumsq(int64_t rows, int64_t cols, const void* __restrict__ X, int x_f32, int64_t ldx,
+        const double* __restrict__ Ysub, int64_t ldy, double* __restrict__ part) {
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+            double v = x_f32 ? (double)((const float*)X)[r * ldx + c] : ((const double*)X)[r * ldx + c];
+            if (Ysub) v -= Ysub[r * ldy + c];
+            s += v * v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_sum(int n, const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    // fixed assignment: thread t sums t, t+blockDim, ... in order
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[0] = t;
+    }
+}
+
+cudaError_t launch_sum(int n, const double* part, double* out, cudaStream_t s) {
+    k_sum<<<1, 1024, 0, s>>>(n, part, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(int64_t rows, int64_t cols, const void* X, int x_f32, int64_t ldx, const double* Ysub,
+                         int64_t ldy, double* part, double* out, cudaStream_t s) {
+    int64_t nb = rows < 1024 ? rows : 1024;
+    if (nb < 1) nb = 1;
+    k_sumsq<<<(unsigned)nb, 256, 0, s>>>(rows, cols, X, x_f32, ldx, Ysub, ldy, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_sum((int)nb, part, out, s);
+}
+
+cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
+                   cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst, (size_t)ldd * sizeof(double), src, (size_t)lds * sizeof(double),
+                             (size_t)cols * sizeof(double), (size_t)rows, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace pbq

@@ -1,0 +1,341 @@
+// C ABI and host driver of the PbP-QLP library (Algorithm 3 of Kaloorazi &
+// Chen).  The plan holds sizes, split-K choices and the workspace layout; all
+// device memory comes from the caller.  Every step of the factorization runs
+// in this library's kernels on the plan's stream.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/pbpqlp.h"
+#include "internal.h"
+
+using namespace pbq;
+
+struct pbpqlp_plan_s {
+    int64_t m = 0, n = 0;
+    int k = 0, p = 0, q = 0, l = 0;
+    uint64_t seed = 0;
+    int mode = 0;
+    cudaStream_t stream = nullptr;
+    int64_t ldp = 0;      // leading dimension of the internal panels
+    int num_sms = 152;
+    // split-K choices: A passes (NN: M=m, K=n; TN: M=n, K=m) and Grams (K = m or n)
+    int S_nn = 1, S_tn = 1, S_gm = 1, S_gn = 1;
+    int64_t kc_nn = 0, kc_tn = 0, kc_gm = 0, kc_gn = 0;
+    // workspace layout (byte offsets)
+    size_t off_status = 0, off_ctl = 0, off_scal = 0, off_Xm = 0, off_Ym = 0, off_Dm = 0, off_Xn = 0, off_Yn = 0;
+    size_t off_part = 0, off_G = 0, off_Rp = 0, off_R = 0, off_Pt = 0, off_work = 0, off_red = 0, total = 0;
+    void* last_ws = nullptr;
+};
+
+namespace {
+
+struct Ws {
+    uint32_t* status;
+    int* ctl;
+    double* scal;
+    double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red;
+};
+
+Ws carve(const pbpqlp_plan_s* P, void* base) {
+    char* b = (char*)base;
+    Ws w;
+    w.status = (uint32_t*)(b + P->off_status);
+    w.ctl = (int*)(b + P->off_ctl);
+    w.scal = (double*)(b + P->off_scal);
+    w.Xm = (double*)(b + P->off_Xm);
+    w.Ym = (double*)(b + P->off_Ym);
+    w.Dm = (double*)(b + P->off_Dm);
+    w.Xn = (double*)(b + P->off_Xn);
+    w.Yn = (double*)(b + P->off_Yn);
+    w.part = (double*)(b + P->off_part);
+    w.G = (double*)(b + P->off_G);
+    w.Rp = (double*)(b + P->off_Rp);
+    w.R = (double*)(b + P->off_R);
+    w.Pt = (double*)(b + P->off_Pt);
+    w.work = (double*)(b + P->off_work);
+    w.red = (double*)(b + P->off_red);
+    return w;
+}
+
+// Split-K count for Mtiles output tiles over a contraction of K: the S that
+// best fills whole waves of `slots` resident CTAs with chunks of >= 64 rows.
+void choose_split(int64_t Mtiles, int64_t K, int64_t slots, int* S_out, int64_t* kc_out) {
+    int bestS = 1;
+    double best = -1.0;
+    const int64_t maxS = K / 64 > 1 ? K / 64 : 1;
+    for (int64_t S = 1; S <= maxS && S <= 512; ++S) {
+        const int64_t kc = round_up((K + S - 1) / S, kGemmBK);
+        const int64_t Seff = (K + kc - 1) / kc;
+        const int64_t ctas = Mtiles * Seff;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        // efficiency: useful work over occupied slot-time, with per-CTA time ~ kc
+        const double eff = (double)K * Mtiles / ((double)waves * slots * kc);
+        if (eff > best + 1e-9) { best = eff; bestS = (int)Seff; }
+        if (waves >= 8) break;
+    }
+    const int64_t kc = round_up((K + bestS - 1) / bestS, kGemmBK);
+    *S_out = (int)((K + kc - 1) / kc);
+    *kc_out = kc;
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA; }
+
+#define PBQ_TRY(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
+
+// C (M x l) = op(A) B through the split-K partial buffer when S > 1.
+int gemm_pass(const pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double* C, int64_t ldc, int N, int S, int64_t kc) {
+    cudaStream_t s = P->stream;
+    if (S <= 1) {
+        PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, C, ldc, 1, K, 0, nullptr, s));
+        return PBPQLP_OK;
+    }
+    const int64_t ps = M * P->ldp;
+    PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, w.part, P->ldp, S, kc, ps, nullptr, s));
+    PBQ_TRY(launch_reduce_partials(M, N, S, w.part, ps, P->ldp, C, ldc, nullptr, s));
+    return PBPQLP_OK;
+}
+
+// Orthonormalise X (rows x l, ld ldp) in place: CholeskyQR in pass pairs
+// (X -> Y -> X).  Pair 1 is CholeskyQR2; pairs 2 and 3 run on the device
+// only if a pass of the previous pair needed the shifted retry.
+int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y, int Sg, int64_t kcg) {
+    cudaStream_t s = P->stream;
+    const int l = P->l;
+    const int64_t ldp = P->ldp;
+    PBQ_TRY(cudaMemsetAsync(w.ctl, 0, 16 * sizeof(int), s));
+    for (int pass = 1; pass <= 6; ++pass) {
+        const double* src = (pass & 1) ? X : Y;
+        double* dst = (pass & 1) ? Y : X;
+        const int* cond = pass <= 2 ? nullptr : w.ctl + 8 + (pass + 1) / 2;
+        const int64_t ps = (int64_t)l * ldp;
+        PBQ_TRY(launch_dgemm_skinny(true, l, l, rows, src, ldp, src, ldp, w.part, ldp, Sg, kcg, ps, cond, s));
+        PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s));
+        PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
+        PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s));
+    }
+    return PBPQLP_OK;
+}
+
+int check_ws(pbpqlp_plan_t P, void* ws, size_t ws_bytes) {
+    if (!ws || ws_bytes < P->total || ((uintptr_t)ws & 255u) != 0) return PBPQLP_EWORKSPACE;
+    return PBPQLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbpqlp_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* pbpqlp_strerror(int st) {
+    switch (st) {
+        case PBPQLP_OK: return "ok";
+        case PBPQLP_EINVAL: return "invalid argument";
+        case PBPQLP_ENOMEM: return "host allocation failed";
+        case PBPQLP_ECUDA: return "CUDA runtime error";
+        case PBPQLP_ENONFINITE: return "non-finite value in input or intermediate panel";
+        case PBPQLP_EBREAKDOWN: return "orthonormalisation broke down after shifted retries";
+        case PBPQLP_ETIMEOUT: return "bounded device wait timed out";
+        case PBPQLP_EUNSUPPORTED: return "mode or size not supported";
+        case PBPQLP_EWORKSPACE: return "workspace missing, misaligned or too small";
+        default: return "unknown status";
+    }
+}
+
+int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, uint64_t seed, int mode,
+                void* stream) {
+    if (!out) return PBPQLP_EINVAL;
+    *out = nullptr;
+    const int64_t l64 = (int64_t)k + (int64_t)p;
+    if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
+    if (l64 > m || l64 > n || l64 > kMaxEll) return PBPQLP_EINVAL;
+    if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_TF32X3) return PBPQLP_EINVAL;
+    if (mode != PBPQLP_MODE_FP64) return PBPQLP_EUNSUPPORTED;
+    pbpqlp_plan_s* P = new (std::nothrow) pbpqlp_plan_s();
+    if (!P) return PBPQLP_ENOMEM;
+    P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
+    P->seed = seed; P->mode = mode; P->stream = (cudaStream_t)stream;
+    P->ldp = round_up(P->l, 8);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            P->num_sms = sms;
+    }
+    const int64_t slots = (int64_t)P->num_sms * dgemm_skinny_occupancy(P->l);
+    const int64_t mt = (m + kGemmBM - 1) / kGemmBM, nt = (n + kGemmBM - 1) / kGemmBM;
+    const int64_t lt = (P->l + kGemmBM - 1) / kGemmBM;
+    choose_split(mt, n, slots, &P->S_nn, &P->kc_nn);
+    choose_split(nt, m, slots, &P->S_tn, &P->kc_tn);
+    choose_split(lt, m, slots, &P->S_gm, &P->kc_gm);
+    choose_split(lt, n, slots, &P->S_gn, &P->kc_gn);
+
+    const int64_t ldp = P->ldp, l = P->l;
+    int64_t part = (int64_t)P->S_nn * m * ldp;
+    part = part > (int64_t)P->S_tn * n * ldp ? part : (int64_t)P->S_tn * n * ldp;
+    int64_t pg = (int64_t)(P->S_gm > P->S_gn ? P->S_gm : P->S_gn) * l * ldp;
+    part = part > pg ? part : pg;
+    const int64_t tiles = ((m + 63) / 64) * ((n + 63) / 64);   // residual partials of pbpqlp_error
+    part = part > tiles ? part : tiles;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
+    P->off_status = take(256);
+    P->off_ctl = take(256);
+    P->off_scal = take(256);
+    P->off_Xm = take(sizeof(double) * m * ldp);
+    P->off_Ym = take(sizeof(double) * m * ldp);
+    P->off_Dm = take(sizeof(double) * m * ldp);
+    P->off_Xn = take(sizeof(double) * n * ldp);
+    P->off_Yn = take(sizeof(double) * n * ldp);
+    P->off_part = take(sizeof(double) * (size_t)part);
+    P->off_G = take(sizeof(double) * l * l);
+    P->off_Rp = take(sizeof(double) * (packed_tri((int)l) + l));
+    P->off_R = take(sizeof(double) * l * ldp);
+    P->off_Pt = take(sizeof(double) * l * ldp);
+    P->off_work = take(sizeof(double) * (3 * l * l + 2 * l));
+    P->off_red = take(sizeof(double) * 2048);
+    P->total = off;
+    *out = P;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_plan_destroy(pbpqlp_plan_t plan) {
+    delete plan;
+    return PBPQLP_OK;
+}
+
+size_t pbpqlp_workspace_bytes(pbpqlp_plan_t plan) { return plan ? plan->total : 0; }
+
+int pbpqlp_generate_omega(pbpqlp_plan_t P, double* omega) {
+    if (!P || !omega) return PBPQLP_EINVAL;
+    return cuda_err(launch_gaussian(P->seed, P->m, P->l, omega, P->l, P->stream));
+}
+
+int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
+                  const double* omega, double* Qa, double* L, double* Qb) {
+    if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
+    if (a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    P->last_ws = workspace;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    const double* A = (const double*)Av;
+    const int64_t m = P->m, n = P->n, ldp = P->ldp;
+    const int l = P->l;
+    PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    // Phi (m x l)
+    if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
+    else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
+    // C = A^T Phi (Eq. 3); Pbar = orth(C) (Eq. 4)
+    if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn))) return rc;
+    if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
+    // power iterations with an orth after every product (Section III-B)
+    for (int it = 0; it < P->q; ++it) {
+        if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Xm, ldp, l, P->S_nn, P->kc_nn))) return rc;
+        if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
+        if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn))) return rc;
+        if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
+    }
+    // D = A Pbar (Eq. 5); [Q, R] = qr(D) (Eq. 6) with R = Q^T D
+    if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Dm, ldp, l, P->S_nn, P->kc_nn))) return rc;
+    PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
+    if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
+    {
+        const int64_t ps = (int64_t)l * ldp;
+        PBQ_TRY(launch_dgemm_skinny(true, l, l, m, w.Xm, ldp, w.Dm, ldp, w.part, ldp, P->S_gm, P->kc_gm, ps, nullptr, s));
+        PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s));
+        PBQ_TRY(launch_triu(l, w.R, s));
+    }
+    // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
+    PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
+    PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
+    PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
+    return PBPQLP_OK;
+}
+
+int pbpqlp_reconstruct(pbpqlp_plan_t P, const double* Qa, const double* L, const double* Qb, int r, double* Ahat,
+                       int64_t ldh, void* workspace, size_t ws_bytes) {
+    if (!P || !Qa || !L || !Qb || !Ahat || r < 1 || r > P->l || ldh < P->n) return PBPQLP_EINVAL;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    const int l = P->l;
+    // T = Qa_r L_r (m x r), then Ahat = T Qb_r^T
+    PBQ_TRY(launch_dgemm_skinny(false, P->m, r, r, Qa, l, L, l, w.Ym, P->ldp, 1, r, 0, nullptr, s));
+    PBQ_TRY(launch_dgemm_nt(P->m, P->n, r, w.Ym, P->ldp, Qb, l, Ahat, ldh, nullptr, 0, 0, nullptr, nullptr, s));
+    return PBPQLP_OK;
+}
+
+int pbpqlp_sync_status(pbpqlp_plan_t P, uint32_t* flags_host) {
+    if (!P) return PBPQLP_EINVAL;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return PBPQLP_ECUDA;
+    uint32_t st = 0;
+    if (P->last_ws) {
+        if (cudaMemcpy(&st, (char*)P->last_ws + P->off_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PBPQLP_ECUDA;
+    }
+    if (flags_host) *flags_host = st;
+    if (st & kStNonFinite) return PBPQLP_ENONFINITE;
+    if (st & kStTimeout) return PBPQLP_ETIMEOUT;
+    if (st & kStBreakdown) return PBPQLP_EBREAKDOWN;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_error(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, const double* Qa, const double* L,
+                 const double* Qb, int r, int method, int nprobes, uint64_t probe_seed, void* workspace,
+                 size_t ws_bytes, double* rel_err) {
+    if (!P || !A || !Qa || !L || !Qb || !rel_err || r < 1 || r > P->l || lda < P->n) return PBPQLP_EINVAL;
+    if (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) return PBPQLP_EINVAL;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    const int l = P->l;
+    const int64_t m = P->m, n = P->n, ldp = P->ldp;
+    const int f32 = a_dtype == PBPQLP_F32;
+    double host[2] = {0.0, 0.0};
+    if (method == PBPQLP_ERR_IDENTITY) {
+        PBQ_TRY(launch_sumsq(m, n, A, f32, lda, nullptr, 0, w.red, w.scal + 0, s));
+        PBQ_TRY(launch_sumsq(r, r, L, 0, l, nullptr, 0, w.red + 1024, w.scal + 1, s));
+        PBQ_TRY(cudaMemcpyAsync(host, w.scal, sizeof(host), cudaMemcpyDeviceToHost, s));
+        PBQ_TRY(cudaStreamSynchronize(s));
+        const double d = host[0] - host[1];
+        *rel_err = host[0] > 0.0 ? std::sqrt(d > 0.0 ? d : 0.0) / std::sqrt(host[0]) : 0.0;
+    } else if (method == PBPQLP_ERR_RESIDUAL) {
+        PBQ_TRY(launch_sumsq(m, n, A, f32, lda, nullptr, 0, w.red, w.scal + 0, s));
+        PBQ_TRY(launch_dgemm_skinny(false, m, r, r, Qa, l, L, l, w.Ym, ldp, 1, r, 0, nullptr, s));
+        int nb = 0;
+        PBQ_TRY(launch_dgemm_nt(m, n, r, w.Ym, ldp, Qb, l, nullptr, 0, A, f32, lda, w.part, &nb, s));
+        PBQ_TRY(launch_sum(nb, w.part, w.scal + 1, s));
+        PBQ_TRY(cudaMemcpyAsync(host, w.scal, sizeof(host), cudaMemcpyDeviceToHost, s));
+        PBQ_TRY(cudaStreamSynchronize(s));
+        *rel_err = host[0] > 0.0 ? std::sqrt(host[1]) / std::sqrt(host[0]) : 0.0;
+    } else if (method == PBPQLP_ERR_PROBES) {
+        if (nprobes < 1 || nprobes > ldp || nprobes > kMaxEll) return PBPQLP_EINVAL;
+        if (f32) return PBPQLP_EUNSUPPORTED;
+        const int ns = nprobes;
+        // W (n x s) Gaussian; AW = A W (m x s); T = Qa_r (L_r (Qb_r^T W))
+        PBQ_TRY(launch_gaussian(probe_seed, n, ns, w.Yn, ldp, s));
+        if ((rc = gemm_pass(P, w, false, m, n, (const double*)A, lda, w.Yn, ldp, w.Ym, ldp, ns, P->S_nn, P->kc_nn)))
+            return rc;
+        PBQ_TRY(launch_dgemm_skinny(true, r, ns, n, Qb, l, w.Yn, ldp, w.R, ldp, 1, n, 0, nullptr, s));
+        PBQ_TRY(launch_dgemm_skinny(false, r, ns, r, L, l, w.R, ldp, w.Pt, ldp, 1, r, 0, nullptr, s));
+        PBQ_TRY(launch_dgemm_skinny(false, m, ns, r, Qa, l, w.Pt, ldp, w.Xm, ldp, 1, r, 0, nullptr, s));
+        PBQ_TRY(launch_sumsq(m, ns, w.Ym, 0, ldp, nullptr, 0, w.red, w.scal + 0, s));
+        PBQ_TRY(launch_sumsq(m, ns, w.Ym, 0, ldp, w.Xm, ldp, w.red + 1024, w.scal + 1, s));
+        PBQ_TRY(cudaMemcpyAsync(host, w.scal, sizeof(host), cudaMemcpyDeviceToHost, s));
+        PBQ_TRY(cudaStreamSynchronize(s));
+        *rel_err = host[0] > 0.0 ? std::sqrt(host[1] / host[0]) : 0.0;
+    } else {
+        return PBPQLP_EINVAL;
+    }
+    if (!std::isfinite(*rel_err)) return PBPQLP_ENONFINITE;
+    return PBPQLP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/*.h declares, and validates arguments without touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for mt in re.finditer(r"\b(pbpqlp_\w+)\s*\(", src):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def pq():
+    import paper_2103_07245_gb300 as pq
+    pq.load(build_if_missing=True)
+    return pq
+
+
+def test_library_exports_every_declared_symbol(pq):
+    names = _declared_functions()
+    assert "pbpqlp_factor" in names and "pbpqlp_plan" in names
+    lib = ctypes.CDLL(pq.lib_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_strerror(pq):
+    assert pq.pbpqlp_version() >= 10000
+    for code in range(0, 9):
+        assert isinstance(pq.strerror(code), str) and pq.strerror(code)
+
+
+@pytest.mark.parametrize("args", [
+    (0, 10, 2, 1, 1),      # m < 1
+    (10, 10, 0, 1, 1),     # k < 1
+    (10, 10, 8, 3, 1),     # l > min(m, n)
+    (10, 10, 2, -1, 1),    # p < 0
+    (10, 10, 2, 1, -1),    # q < 0
+    (500, 500, 200, 30, 1),  # l > 224
+])
+def test_plan_rejects_bad_sizes(pq, args):
+    with pytest.raises(pq.PbpqlpError) as e:
+        pq.pbpqlp_plan(*args, seed=1, mode=pq.PBPQLP_MODE_FP64, stream=0)
+    assert e.value.status == pq.PBPQLP_EINVAL
+
+
+def test_plan_rejects_bad_mode(pq):
+    with pytest.raises(pq.PbpqlpError) as e:
+        pq.pbpqlp_plan(100, 100, 5, 5, 1, seed=1, mode=99, stream=0)
+    assert e.value.status == pq.PBPQLP_EINVAL
+
+
+def test_plan_workspace_is_sized_and_factor_validates(pq):
+    h = pq.pbpqlp_plan(1000, 1000, 20, 5, 1, seed=1, mode=pq.PBPQLP_MODE_FP64, stream=0)
+    try:
+        ws = pq.pbpqlp_workspace_bytes(h)
+        # at least the five panels m x l / n x l in FP64
+        assert ws >= 5 * 1000 * 25 * 8
+        # null pointers / small workspace are rejected before any launch
+        with pytest.raises(pq.PbpqlpError) as e:
+            pq.pbpqlp_factor(h, 0, 1000, pq.PBPQLP_F64, 0, ws, None, 0, 0, 0)
+        assert e.value.status == pq.PBPQLP_EINVAL
+        with pytest.raises(pq.PbpqlpError) as e:
+            pq.pbpqlp_factor(h, 256, 1000, pq.PBPQLP_F64, 512, ws - 1, None, 256, 256, 256)
+        assert e.value.status == pq.PBPQLP_EWORKSPACE
+        with pytest.raises(pq.PbpqlpError) as e:
+            pq.pbpqlp_factor(h, 256, 999, pq.PBPQLP_F64, 512, ws, None, 256, 256, 256)
+        assert e.value.status == pq.PBPQLP_EINVAL
+    finally:
+        pq.pbpqlp_plan_destroy(h)
