@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""PbP-QLP benchmark on GB300: factorizations/s of Algorithm 3.
+
+Default workload (one GPU): plain FP64, A = U diag(exp(-i/40)) V^T with Haar
+U, V, m = n = 8000, k = 100, p = 10, q = 2 — one step is one whole
+factorization (Phi, 2q+2 products with A / A^T, 2q+2 CholeskyQR orths, the
+l x l QR and the basis update).  A (512 MB) is larger than the 129 MB L2, so
+no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on the same workload instead.
+"""
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PbP-QLP factorizations/s & TFLOP/s, mixed vs plain FP64 at equal rel. error"
+UNIT = "factorizations/s"
+
+WORKLOADS = {
+    "fp64_8000": dict(m=8000, n=8000, k=100, p=10, q=2, spectrum="exp", scale=40.0, rank_cap=1500,
+                      mode="FP64", desc="plain FP64, A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
+}
+
+# FP64 issue rate of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def algorithmic_flops(m, n, l, q):
+    """Every A-pass GEMM, CholeskyQR-equivalent orth work, basis update and small QR."""
+    return (2 * q + 2) * 2.0 * m * n * l + 4.0 * (q + 1) * (m + n) * l * l + 2.0 * n * l * l + (8.0 / 3.0) * l ** 3
+
+
+def make_matrix(w, seed, device):
+    import synth
+    sig = synth.spectrum(w["spectrum"], w["rank_cap"], w["scale"])
+    return synth.torch_svd_matrix(seed, w["m"], w["n"], sig, device=device)
+
+
+def read_traffic(kernel_file_tag):
+    """ncu DRAM bytes per launch recorded in profiles/, valid only for the kernel source it was taken on."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file_tag + ".md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mt = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    ms = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    src = os.path.join(ROOT, "paper_2103_07245_gb300", "csrc", "kernels_fp64.cu")
+    if not mt or not ms or not os.path.exists(src):
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return float(mt.group(1)) if cur.startswith(ms.group(1)) else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, w, world, rank):
+    """The FP64 CPU oracle timed on the host cores (reference arm)."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A = make_matrix(w, 1000, dev).cpu().numpy()
+    l = w["k"] + w["p"]
+    for _ in range(args.warmup):
+        oracle.pbpqlp(A, l, w["q"], seed=7)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pbpqlp(A, l, w["q"], seed=7)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / dt
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
+                   "l2": "inputs larger than L2 (A is %d MB)" % (w["m"] * w["n"] * 8 // 2 ** 20)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one full FP64 oracle factorization per step on the same workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "tflops_algorithmic": value * algorithmic_flops(w["m"], w["n"], l, w["q"]) / 1e12,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fp64_8000", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+
+    import numpy as np
+    import torch
+    import paper_2103_07245_gb300 as pq
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pq.load(build_if_missing=True)
+
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    l = k + p
+    A = make_matrix(w, 1000 + rank, dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = pq.Plan(m, n, k, p, q, seed=7 + rank, stream=stream, device=dev)
+    Qa, L, Qb = plan.outputs(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.factor(A, out=(Qa, L, Qb))
+    rc, flags = plan.sync_status()
+    if rc != pq.PBPQLP_OK:
+        raise RuntimeError("device status %d flags %d" % (rc, flags))
+
+    # ---- device-resident timing (inputs already in HBM)
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    pq.pbpqlp_set_timing(plan.handle, True)
+    pq.pbpqlp_read_timing(plan.handle)
+    launches0 = pq.pbpqlp_kernel_launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.factor(A, out=(Qa, L, Qb))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    launches = pq.pbpqlp_kernel_launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    pass_ms, pass_launches = pq.pbpqlp_read_timing(plan.handle)
+    pq.pbpqlp_set_timing(plan.handle, False)
+    rc, flags = plan.sync_status()
+    if rc != pq.PBPQLP_OK:
+        raise RuntimeError("device status %d flags %d" % (rc, flags))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    A_host = A.cpu().pin_memory()
+    A_dev = torch.empty_like(A)
+    out_host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (Qa, L, Qb)]
+    h2d = A_host.numel() * A_host.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in out_host)
+    for _ in range(1):
+        A_dev.copy_(A_host, non_blocking=True)
+        plan.factor(A_dev, out=(Qa, L, Qb))
+        for h, d in zip(out_host, (Qa, L, Qb)):
+            h.copy_(d, non_blocking=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        plan.factor(A_dev, out=(Qa, L, Qb))
+        for h, d in zip(out_host, (Qa, L, Qb)):
+            h.copy_(d, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms_e2e = f0.elapsed_time(f1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    flops = algorithmic_flops(m, n, l, q)
+    pass_flops = 2.0 * m * n * l
+    avg_pass_s = (pass_ms / pass_launches) / 1e3 if pass_launches else None
+    achieved = pass_flops / avg_pass_s / 1e12 if avg_pass_s else None
+    traffic = read_traffic("dgemm_skinny_fp64_8000")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q, "mode": w["mode"],
+                   "l2": "inputs larger than L2 (A is %d MB), no flush" % (m * n * 8 // 2 ** 20),
+                   "parallelism": "independent factorizations per GPU" if world > 1 else "single GPU"},
+        "tflops_algorithmic": value * flops / 1e12,
+        "roofline": {"kernel": "k_dgemm_skinny (A / A^T pass, 2mnl flop per launch)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
+                     "launches_timed": pass_launches, "avg_launch_ms": (pass_ms / pass_launches) if pass_launches else None},
+        "e2e": {"value": world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    # ---- CPU baseline: the oracle, rank 0 at N = 1, and parity of the timed result
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        A_np = A_host.numpy()
+        t0 = time.perf_counter()
+        ref = oracle.pbpqlp(A_np, l, q, seed=7)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "one full FP64 oracle factorization of the same %dx%d matrix (q=%d, l=%d)"
+                                          % (m, n, q, l)}
+        Qa_n, L_n, Qb_n = (t.numpy() for t in out_host)
+        Ag = oracle.reconstruct(Qa_n, L_n, Qb_n, k)
+        Ac = oracle.reconstruct(ref["Q"], ref["L"], ref["P"], k)
+        line["parity"] = {"rel_fro_diff_rank_k": float(np.linalg.norm(Ag - Ac) / np.linalg.norm(A_np)),
+                          "tol": 1e-11}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

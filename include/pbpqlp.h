@@ -157,6 +157,21 @@ int pbpqlp_error(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
  */
 int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
 
+/*
+ * Observability (not part of the paper's method).
+ * pbpqlp_set_timing: when enable != 0, every later pbpqlp_factor on this plan
+ * records a CUDA event pair on the plan's stream around each launch of the
+ * kernel that multiplies by A or A^T (the 2q+2 passes of Algorithm 3).
+ * pbpqlp_read_timing waits for the stream, returns the summed milliseconds
+ * and the number of such launches since the last read, and clears them.
+ * Event pairs are created on first use and kept by the plan.
+ */
+int pbpqlp_set_timing(pbpqlp_plan_t plan, int enable);
+int pbpqlp_read_timing(pbpqlp_plan_t plan, double* pass_ms_total, int64_t* pass_launches);
+
+/* Process-wide count of CUDA kernels this library has launched so far. */
+int64_t pbpqlp_kernel_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,12 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_error.restype = ci
     L.pbpqlp_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.pbpqlp_sync_status.restype = ci
+    L.pbpqlp_set_timing.argtypes = [vp, ci]
+    L.pbpqlp_set_timing.restype = ci
+    L.pbpqlp_read_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.pbpqlp_read_timing.restype = ci
+    L.pbpqlp_kernel_launch_count.argtypes = []
+    L.pbpqlp_kernel_launch_count.restype = ctypes.c_int64
     _lib = L
     return L
 
@@ -158,6 +164,22 @@ def pbpqlp_sync_status(plan):
     f = ctypes.c_uint32(0)
     rc = load().pbpqlp_sync_status(plan, ctypes.byref(f))
     return rc, int(f.value)
+
+
+def pbpqlp_set_timing(plan, enable):
+    _check(load().pbpqlp_set_timing(plan, 1 if enable else 0), "pbpqlp_set_timing")
+
+
+def pbpqlp_read_timing(plan):
+    """Returns (milliseconds summed over timed pass kernels, number of such launches)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().pbpqlp_read_timing(plan, ctypes.byref(ms), ctypes.byref(n)), "pbpqlp_read_timing")
+    return ms.value, int(n.value)
+
+
+def pbpqlp_kernel_launch_count() -> int:
+    return int(load().pbpqlp_kernel_launch_count())
 
 
 # ------------------------------------------------------- torch convenience layer

@@ -16,6 +16,10 @@ constexpr uint32_t kStBreakdown = 2u;  // Cholesky failed even with the shift
 constexpr uint32_t kStNonFinite = 4u;  // NaN/Inf met
 constexpr uint32_t kStTimeout = 8u;    // bounded wait gave up
 
+// Process-wide launch counter (incremented by every launcher below).
+void count_launches(int64_t n);
+int64_t launch_count();
+
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t packed_tri(int l) { return (int64_t)l * (l + 1) / 2; }
 

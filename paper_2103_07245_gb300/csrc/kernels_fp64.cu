@@ -11,7 +11,13 @@
 
 #include "internal.h"
 
+#include <atomic>
+
 namespace pbq {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller.
@@ -54,6 +60,7 @@ cudaError_t launch_gaussian(uint64_t seed, int64_t rows, int l, double* out, int
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     k_gaussian<<<(unsigned)blocks, 256, 0, s>>>(seed, rows, l, out, ld);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -139,6 +146,7 @@ static cudaError_t dispatch_dgemm(int TN, dim3 grid, int64_t M, int N, int64_t K
         default: return cudaErrorInvalidValue;
     }
 #undef PBQ_CASE
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -191,6 +199,7 @@ cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, 
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     k_reduce_partials<<<(unsigned)blocks, 256, 0, s>>>(M, N, S, part, ps, ldp, C, ldc, cond);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -294,6 +303,7 @@ cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rp, ui
     cudaError_t e = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_cholesky<<<1, 1024, smem, s>>>(l, rows, G, Rp, status, ctl, pass);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -360,6 +370,7 @@ cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double
         default: return cudaErrorInvalidValue;
     }
 #undef PBQ_TR
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -457,6 +468,7 @@ k_small_qr(int l, const double* __restrict__ R, double* __restrict__ L, double* 
 
 cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s) {
     k_small_qr<<<1, 1024, 0, s>>>(l, R, L, Ptil, work);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -470,6 +482,7 @@ __global__ void k_triu(int l, double* R) {
 
 cudaError_t launch_triu(int l, double* R, cudaStream_t s) {
     k_triu<<<64, 256, 0, s>>>(l, R);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -548,6 +561,7 @@ cudaError_t launch_dgemm_nt(int64_t M, int64_t N, int K, const double* A, int64_
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
     if (nblocks) *nblocks = (int)(grid.x * grid.y);
     k_dgemm_nt<<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, Aref, aref_f32, ldref, sqpart);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -595,6 +609,7 @@ __global__ void k_sum(int n, const double* __restrict__ part, double* __restrict
 
 cudaError_t launch_sum(int n, const double* part, double* out, cudaStream_t s) {
     k_sum<<<1, 1024, 0, s>>>(n, part, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -603,6 +618,7 @@ cudaError_t launch_sumsq(int64_t rows, int64_t cols, const void* X, int x_f32, i
     int64_t nb = rows < 1024 ? rows : 1024;
     if (nb < 1) nb = 1;
     k_sumsq<<<(unsigned)nb, 256, 0, s>>>(rows, cols, X, x_f32, ldx, Ysub, ldy, part);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_sum((int)nb, part, out, s);

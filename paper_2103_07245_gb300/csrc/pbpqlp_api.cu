@@ -6,6 +6,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "../../include/pbpqlp.h"
 #include "internal.h"
@@ -27,6 +29,13 @@ struct pbpqlp_plan_s {
     size_t off_status = 0, off_ctl = 0, off_scal = 0, off_Xm = 0, off_Ym = 0, off_Dm = 0, off_Xn = 0, off_Yn = 0;
     size_t off_part = 0, off_G = 0, off_Rp = 0, off_R = 0, off_Pt = 0, off_work = 0, off_red = 0, total = 0;
     void* last_ws = nullptr;
+    // observability: CUDA event pairs around each A / A^T pass kernel
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+    ~pbpqlp_plan_s() {
+        for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
 };
 
 namespace {
@@ -84,16 +93,32 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA
 
 #define PBQ_TRY(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
 
-// C (M x l) = op(A) B through the split-K partial buffer when S > 1.
-int gemm_pass(const pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, const double* A, int64_t lda,
-              const double* B, int64_t ldb, double* C, int64_t ldc, int N, int S, int64_t kc) {
+// Event pair for the next timed pass kernel (nullptr pair when timing is off).
+std::pair<cudaEvent_t, cudaEvent_t> next_events(pbpqlp_plan_s* P) {
+    if (!P->timing) return {nullptr, nullptr};
+    if (P->ev_used == P->ev.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return {nullptr, nullptr};
+        P->ev.emplace_back(a, b);
+    }
+    return P->ev[P->ev_used++];
+}
+
+// C (M x l) = op(A) B through the split-K partial buffer when S > 1.  With
+// `timed`, the GEMM kernel launch is bracketed by a plan event pair.
+int gemm_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double* C, int64_t ldc, int N, int S, int64_t kc, bool timed = false) {
     cudaStream_t s = P->stream;
+    const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
+    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
     if (S <= 1) {
         PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, C, ldc, 1, K, 0, nullptr, s));
+        if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
         return PBPQLP_OK;
     }
     const int64_t ps = M * P->ldp;
     PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, w.part, P->ldp, S, kc, ps, nullptr, s));
+    if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
     PBQ_TRY(launch_reduce_partials(M, N, S, w.part, ps, P->ldp, C, ldc, nullptr, s));
     return PBPQLP_OK;
 }
@@ -231,17 +256,17 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
     else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
     // C = A^T Phi (Eq. 3); Pbar = orth(C) (Eq. 4)
-    if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn))) return rc;
+    if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn, true))) return rc;
     if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
     // power iterations with an orth after every product (Section III-B)
     for (int it = 0; it < P->q; ++it) {
-        if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Xm, ldp, l, P->S_nn, P->kc_nn))) return rc;
+        if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Xm, ldp, l, P->S_nn, P->kc_nn, true))) return rc;
         if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
-        if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn))) return rc;
+        if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn, true))) return rc;
         if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
     }
     // D = A Pbar (Eq. 5); [Q, R] = qr(D) (Eq. 6) with R = Q^T D
-    if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Dm, ldp, l, P->S_nn, P->kc_nn))) return rc;
+    if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Dm, ldp, l, P->S_nn, P->kc_nn, true))) return rc;
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
     {
@@ -337,5 +362,28 @@ int pbpqlp_error(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, const
     if (!std::isfinite(*rel_err)) return PBPQLP_ENONFINITE;
     return PBPQLP_OK;
 }
+
+int pbpqlp_set_timing(pbpqlp_plan_t P, int enable) {
+    if (!P) return PBPQLP_EINVAL;
+    P->timing = enable != 0;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_read_timing(pbpqlp_plan_t P, double* ms_total, int64_t* launches) {
+    if (!P || !ms_total || !launches) return PBPQLP_EINVAL;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return PBPQLP_ECUDA;
+    double tot = 0.0;
+    for (size_t i = 0; i < P->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->ev[i].first, P->ev[i].second) != cudaSuccess) return PBPQLP_ECUDA;
+        tot += ms;
+    }
+    *ms_total = tot;
+    *launches = (int64_t)P->ev_used;
+    P->ev_used = 0;
+    return PBPQLP_OK;
+}
+
+int64_t pbpqlp_kernel_launch_count(void) { return launch_count(); }
 
 }  // extern "C"

@@ -106,26 +106,19 @@ def batched_shapes(seed: int, count: int = 512, m_range=(256, 4096), n_lo: int =
 
 
 # ------------------------------------------------------------- torch (device)
-def torch_haar_columns(gen, rows: int, cols: int, device, dtype):
-    import torch
-    g = torch.randn(rows, cols, generator=gen, device=device, dtype=torch.float64)
-    q, r = torch.linalg.qr(g)
-    s = torch.sign(torch.diagonal(r))
-    s[s == 0] = 1.0
-    return (q * s).to(dtype)
-
-
 def torch_svd_matrix(seed: int, m: int, n: int, sigma, device="cuda", dtype=None):
-    """Device version of :func:`svd_matrix` (FP64 build, optional cast)."""
+    """Device version of :func:`svd_matrix`: the Haar factors come from the same
+    numpy stream (QR on the host, LAPACK), the product U diag(sigma) V^T is
+    formed on the device in FP64."""
     import torch
     dtype = dtype or torch.float64
-    gen = torch.Generator(device=device)
-    gen.manual_seed(seed)
-    s = torch.as_tensor(np.asarray(sigma), device=device, dtype=torch.float64)
-    r = s.numel()
-    U = torch_haar_columns(gen, m, r, device, torch.float64)
-    V = torch_haar_columns(gen, n, r, device, torch.float64)
-    return ((U * s) @ V.T).to(dtype).contiguous()
+    rng = np.random.default_rng(seed)
+    s = np.asarray(sigma, dtype=np.float64)
+    r = len(s)
+    U = torch.from_numpy(haar_columns(rng, m, r)).to(device)
+    V = torch.from_numpy(haar_columns(rng, n, r)).to(device)
+    sd = torch.from_numpy(s).to(device)
+    return ((U * sd) @ V.T).to(dtype).contiguous()
 
 
 def torch_xyt_plus_noise(seed: int, m: int, n: int, r: int, eps: float, device="cuda"):
