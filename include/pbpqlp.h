@@ -158,6 +158,33 @@ int pbpqlp_error(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
 int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
 
 /*
+ * pbpqlp_factor_static — the paper has no counterpart; this is a deployment
+ * variant of pbpqlp_factor for callers that cannot allocate device memory
+ * (code whose host framework owns every device allocation, such as an
+ * inference-engine plugin, or a path that must not pay cudaMalloc's implicit
+ * synchronisation).  It takes the same inputs and outputs as pbpqlp_factor
+ * but no workspace: the scratch is a fixed array of
+ * PBPQLP_STATIC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library reserves until the process exits.
+ *   - Plans with pbpqlp_workspace_bytes(plan) > PBPQLP_STATIC_SCRATCH_BYTES
+ *     are rejected with PBPQLP_EWORKSPACE before anything is enqueued.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.  The current device must own the plan's stream and
+ *     the buffers.
+ *   - Every call shares the one array, so calls whose work overlaps on the
+ *     GPU (other streams, other plans, other host threads) race and corrupt
+ *     each other; serialise them.  State that must start at zero is cleared
+ *     by each call.
+ *   - It allocates nothing (no cudaMalloc, cudaFree or allocating library
+ *     call).  pbpqlp_sync_status reports its device status like
+ *     pbpqlp_factor's.
+ */
+#define PBPQLP_STATIC_SCRATCH_BYTES (32u << 20)
+int pbpqlp_factor_static(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
+                         const double* omega, double* Qa, double* L, double* Qb);
+
+/*
  * Observability (not part of the paper's method).
  * pbpqlp_set_timing: when enable != 0, every later pbpqlp_factor on this plan
  * records a CUDA event pair on the plan's stream around each launch of the

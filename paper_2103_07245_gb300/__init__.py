@@ -34,6 +34,8 @@ PBPQLP_ERR_IDENTITY = 0
 PBPQLP_ERR_RESIDUAL = 1
 PBPQLP_ERR_PROBES = 2
 
+PBPQLP_STATIC_SCRATCH_BYTES = 32 << 20
+
 MAX_ELL = 224
 
 _lib = None
@@ -80,6 +82,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_error.restype = ci
     L.pbpqlp_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.pbpqlp_sync_status.restype = ci
+    L.pbpqlp_factor_static.argtypes = [vp, vp, i64, ci, vp, vp, vp, vp]
+    L.pbpqlp_factor_static.restype = ci
     L.pbpqlp_set_timing.argtypes = [vp, ci]
     L.pbpqlp_set_timing.restype = ci
     L.pbpqlp_read_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -164,6 +168,12 @@ def pbpqlp_sync_status(plan):
     f = ctypes.c_uint32(0)
     rc = load().pbpqlp_sync_status(plan, ctypes.byref(f))
     return rc, int(f.value)
+
+
+def pbpqlp_factor_static(plan, A, lda, a_dtype, omega, Qa, L, Qb):
+    """pbpqlp_factor without a workspace argument (the library's fixed device scratch)."""
+    _check(load().pbpqlp_factor_static(plan, _ptr(A), int(lda), int(a_dtype), _ptr(omega), _ptr(Qa), _ptr(L),
+                                       _ptr(Qb)), "pbpqlp_factor_static")
 
 
 def pbpqlp_set_timing(plan, enable):
