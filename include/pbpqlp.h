@@ -114,7 +114,8 @@ int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
  * Algorithm 3: factor A ~= Qa L Qb^T.
  *   A         : device, m x n, row-major, leading dimension lda >= n,
  *               element type a_dtype (PBPQLP_F64 in MODE_FP64; PBPQLP_F32 or
- *               PBPQLP_F64 in the mixed modes).
+ *               PBPQLP_F64 in the mixed modes, which split A into BF16 hi/lo
+ *               copies in the workspace once per call).
  *   workspace : device, >= pbpqlp_workspace_bytes(plan) bytes, 256-aligned;
  *               ws_bytes is its size.  Contents are scratch between calls.
  *   omega     : optional device m x l FP64 test matrix; NULL draws Phi from
@@ -127,6 +128,19 @@ int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
 int pbpqlp_factor(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
                   void* workspace, size_t ws_bytes, const double* omega,
                   double* Qa, double* L, double* Qb);
+
+/*
+ * One product of Algorithm 3 on its own (Eq. 3 / Eq. 5): C = A Y (trans = 0;
+ * Y is n x ncols, C is m x ncols) or C = A^T Y (trans = 1; Y is m x ncols,
+ * C is n x ncols), in the plan's arithmetic mode (FP64 DFMA, or the
+ * tcgen05 BF16 / split-BF16 products with FP32 accumulation).
+ *   Y, C : device FP64, row-major, leading dimensions ldy, ldc >= ncols.
+ *   1 <= ncols <= l.  A and a_dtype as in pbpqlp_factor.
+ * Uses the workspace (same size rule as pbpqlp_factor); asynchronous.
+ */
+int pbpqlp_sketch(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype, int trans,
+                  const double* Y, int64_t ldy, int ncols, double* C, int64_t ldc,
+                  void* workspace, size_t ws_bytes);
 
 /*
  * Rank-r reconstruction Ahat = Qa[:, :r] L[:r, :r] Qb[:, :r]^T (Eq. 8 and its

@@ -76,6 +76,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_generate_omega.restype = ci
     L.pbpqlp_factor.argtypes = [vp, vp, i64, ci, vp, sz, vp, vp, vp, vp]
     L.pbpqlp_factor.restype = ci
+    L.pbpqlp_sketch.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp, sz]
+    L.pbpqlp_sketch.restype = ci
     L.pbpqlp_reconstruct.argtypes = [vp, vp, vp, vp, ci, vp, i64, vp, sz]
     L.pbpqlp_reconstruct.restype = ci
     L.pbpqlp_error.argtypes = [vp, vp, i64, ci, vp, vp, vp, ci, ci, ci, u64, vp, sz, ctypes.POINTER(ctypes.c_double)]
@@ -148,6 +150,11 @@ def pbpqlp_generate_omega(plan, omega):
 def pbpqlp_factor(plan, A, lda, a_dtype, workspace, ws_bytes, omega, Qa, L, Qb):
     _check(load().pbpqlp_factor(plan, _ptr(A), int(lda), int(a_dtype), _ptr(workspace), int(ws_bytes),
                                 _ptr(omega), _ptr(Qa), _ptr(L), _ptr(Qb)), "pbpqlp_factor")
+
+
+def pbpqlp_sketch(plan, A, lda, a_dtype, trans, Y, ldy, ncols, C, ldc, workspace, ws_bytes):
+    _check(load().pbpqlp_sketch(plan, _ptr(A), int(lda), int(a_dtype), int(trans), _ptr(Y), int(ldy), int(ncols),
+                                _ptr(C), int(ldc), _ptr(workspace), int(ws_bytes)), "pbpqlp_sketch")
 
 
 def pbpqlp_reconstruct(plan, Qa, L, Qb, r, Ahat, ldh, workspace, ws_bytes):
@@ -223,6 +230,16 @@ class Plan:
         o = torch.empty(self.m, self.l, dtype=torch.float64, device=device)
         pbpqlp_generate_omega(self.handle, o)
         return o
+
+    def sketch(self, A, Y, trans=False):
+        """C = A Y (or A^T Y) in the plan's mode; Y is FP64 with <= l columns."""
+        import torch
+        a_dtype = PBPQLP_F32 if A.dtype == torch.float32 else PBPQLP_F64
+        rows = self.n if trans else self.m
+        C = torch.empty(rows, Y.shape[1], dtype=torch.float64, device=A.device)
+        pbpqlp_sketch(self.handle, A, A.stride(0), a_dtype, 1 if trans else 0, Y, Y.stride(0), Y.shape[1], C,
+                      C.stride(0), self.workspace, self.ws_bytes)
+        return C
 
     def reconstruct(self, Qa, L, Qb, r=None):
         import torch

@@ -1,0 +1,535 @@
+// Tensor-core (tcgen05 / TMEM / TMA) products with A and A^T for the mixed
+// precision modes of Algorithm 3 (the sketch C = A^T Phi, the power-iteration
+// products and the projection D = A Pbar; Eqs. 3 and 5).
+//
+// C[i][j] = sum_k Aop[i][k] * Bt[j][k]: both operands are K-major BF16 in
+// global memory (A pre-split into row-major and transposed copies, the
+// panels transposed), moved by TMA with the 128-byte swizzle into a ring of
+// shared-memory stages and multiplied by tcgen05.mma (kind::f16, FP32
+// accumulation in TMEM).  The split mode issues three MMAs per k-step,
+// hi*hi + lo*hi + hi*lo, into the same accumulator.
+//
+// Work split: static stream-K over the (row tile, k-block) iterations, so the
+// 152 SMs get equal shares; each contiguous run of k-blocks of one tile is a
+// "segment" whose FP32 partial goes to a partial buffer, and a second kernel
+// adds the partials of each tile in CTA order (deterministic) into the FP64
+// output panel.
+//
+// Roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues
+// MMAs, warps 2-5 drain the double-buffered TMEM accumulator.  Every wait on
+// an mbarrier is bounded by a globaltimer deadline; on expiry the CTA sets a
+// status bit, raises a shared abort flag, drains what it issued and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "internal.h"
+#include "tc_internal.h"
+
+namespace pbq {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false when the deadline passed or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline, volatile int* abort_flag) {
+    uint32_t it = 0;
+    while (!mbar_test(bar, parity)) {
+        if ((++it & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() > deadline) return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major, 128-byte-swizzled tile whose
+// rows are 128 bytes and whose 8-row groups are 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// First iteration owned by CTA c of G over T iterations.
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t c, int64_t T, int64_t G) { return (c * T) / G; }
+
+}  // namespace
+
+constexpr int kTcBM = 128;   // rows per tile (one TMEM lane per row)
+constexpr int kTcBK = 64;    // BF16 elements per k-block (one 128-byte swizzle row)
+
+template <int NPROD, int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+          const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int64_t tiles,
+          int KI, int smax, float* __restrict__ part, uint32_t* __restrict__ status, uint64_t timeout_ns) {
+    constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
+    constexpr uint32_t B_BYTES = BN * kTcBK * 2;
+    constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
+    constexpr uint32_t ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    constexpr uint32_t IDESC = idesc_bf16_f32(kTcBM, BN);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int issued_sh, consumed_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x, c = blockIdx.x;
+    const int64_t T = tiles * (int64_t)KI;
+    const int64_t it_begin = sk_begin(c, T, G), it_end = sk_begin(c + 1, T, G);
+    const uint64_t deadline = globaltimer() + timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        mbar_init(&drain_bar, 1);
+        abort_sh = 0;
+        issued_sh = 0;
+        consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(2 * ACC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    auto stage_ptr = [&](int s, int which) -> unsigned char* {
+        // which: 0 = A hi, 1 = B hi, 2 = A lo, 3 = B lo
+        unsigned char* base = smem + (size_t)s * STAGE_BYTES;
+        switch (which) {
+            case 0: return base;
+            case 1: return base + A_BYTES;
+            case 2: return base + A_BYTES + B_BYTES;
+            default: return base + 2 * A_BYTES + B_BYTES;
+        }
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int li = 0;
+            for (int64_t it = it_begin; it < it_end; ++it, ++li) {
+                const int s = li % STAGES;
+                if (li >= STAGES) {
+                    if (!mbar_wait(&empty_bar[s], (uint32_t)((li / STAGES - 1) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        break;
+                    }
+                }
+                const int64_t tile = it / KI;
+                const int k0 = (int)(it - tile * KI) * kTcBK;
+                const int m0 = (int)(tile * kTcBM);
+                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                tma_load_2d(stage_ptr(s, 0), &tmAhi, &full_bar[s], k0, m0);
+                tma_load_2d(stage_ptr(s, 1), &tmBhi, &full_bar[s], k0, 0);
+                if (NPROD == 3) {
+                    tma_load_2d(stage_ptr(s, 2), &tmAlo, &full_bar[s], k0, m0);
+                    tma_load_2d(stage_ptr(s, 3), &tmBlo, &full_bar[s], k0, 0);
+                }
+                issued_sh = li + 1;
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int li = 0, seg = 0;
+            bool ok = true;
+            int64_t it = it_begin;
+            while (ok && it < it_end) {
+                const int64_t tile = it / KI;
+                const int64_t seg_end = ((tile + 1) * KI < it_end) ? (tile + 1) * KI : it_end;
+                const int b = seg & 1;
+                if (seg >= 2 && !mbar_wait(&acce_bar[b], (uint32_t)((seg / 2 - 1) & 1), deadline, &abort_sh)) {
+                    abort_sh = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)b * ACC_COLS;
+                bool first = true;
+                for (; it < seg_end; ++it, ++li) {
+                    const int s = li % STAGES;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((li / STAGES) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ahi = smem_u32(stage_ptr(s, 0)), bhi = smem_u32(stage_ptr(s, 1));
+                    const uint32_t alo = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along the swizzled row
+                        tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(bhi + off), IDESC,
+                                    (first && kk == 0) ? 0u : 1u);
+                        if (NPROD == 3) {
+                            tc_mma_bf16(dt, sdesc_k_sw128(alo + off), sdesc_k_sw128(bhi + off), IDESC, 1u);
+                            tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(blo + off), IDESC, 1u);
+                        }
+                    }
+                    first = false;
+                    tc_commit(&empty_bar[s]);
+                    consumed_sh = li + 1;
+                }
+                if (!ok) break;
+                tc_commit(&accf_bar[b]);
+                ++seg;
+            }
+            // all MMAs issued by this thread complete before TMEM is released;
+            // this wait ignores the abort flag (bounded by the deadline only)
+            tc_commit(&drain_bar);
+            const uint64_t dl = globaltimer() + timeout_ns;
+            uint32_t spin = 0;
+            while (!mbar_test(&drain_bar, 0)) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) { abort_sh = 1; break; }
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> FP32 partials
+        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;
+        int seg = 0;
+        int64_t it = it_begin;
+        const int64_t first_tile = it_begin / KI;
+        while (it < it_end) {
+            const int64_t tile = it / KI;
+            const int64_t seg_end = ((tile + 1) * KI < it_end) ? (tile + 1) * KI : it_end;
+            const int b = seg & 1;
+            // warp-uniform decision: the TMEM loads below are .sync.aligned
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (uint32_t)((seg / 2) & 1), deadline, &abort_sh));
+            if (!ok) {
+                abort_sh = 1;
+                break;
+            }
+            tc_fence_after();
+            float* slot = part + ((size_t)c * smax + (size_t)(tile - first_tile)) * (size_t)kTcBM * BN;
+            const uint32_t taddr = tmem_base + (uint32_t)b * ACC_COLS + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 16; ++ch) {
+                float v[16];
+                tmem_ld16(taddr + ch * 16, v);
+                float4* dst = (float4*)(slot + ((size_t)ch * kTcBM + row) * 16);
+                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+                dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+            }
+            tc_fence_before();
+            mbar_arrive(&acce_bar[b]);
+            it = seg_end;
+            ++seg;
+        }
+    }
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // wait (bounded) for TMA copies that were issued but never consumed
+        const uint64_t dl = globaltimer() + timeout_ns;
+        for (int li = consumed_sh; li < issued_sh; ++li) {
+            const int s = li % STAGES;
+            uint32_t spin = 0;
+            while (!mbar_test(&full_bar[s], (uint32_t)((li / STAGES) & 1))) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) break;
+            }
+        }
+        if (abort_sh) atomicOr(status, kStTimeout);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * ACC_COLS)
+                     : "memory");
+    }
+}
+
+// Sum the stream-K partials of each tile in CTA order into C (FP64, rows x N, ldc).
+__global__ void k_tc_reduce(int64_t rows, int N, int BN, int64_t tiles, int KI, int64_t G, int smax,
+                            const float* __restrict__ part, double* __restrict__ C, int64_t ldc) {
+    const int64_t T = tiles * (int64_t)KI;
+    const int64_t total = rows * (int64_t)N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / N;
+        const int j = (int)(e - i * N);
+        const int64_t tile = i / kTcBM;
+        const int r = (int)(i - tile * kTcBM);
+        const int64_t it0 = tile * KI, it1 = it0 + KI - 1;
+        int64_t c = (it0 * G) / T;
+        while (c + 1 < G && sk_begin(c + 1, T, G) <= it0) ++c;
+        while (c > 0 && sk_begin(c, T, G) > it0) --c;
+        double acc = 0.0;
+        for (; c < G && sk_begin(c, T, G) <= it1; ++c) {
+            const int64_t b = sk_begin(c, T, G), en = sk_begin(c + 1, T, G);
+            if (en <= it0) continue;
+            const int64_t ft = b / KI;
+            const float* slot = part + ((size_t)c * smax + (size_t)(tile - ft)) * (size_t)kTcBM * BN;
+            acc += (double)slot[((size_t)(j >> 4) * kTcBM + r) * 16 + (j & 15)];
+        }
+        C[i * ldc + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled encode_fn() {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map over a rows x cols row-major matrix (ld elements), box {64, box_rows}.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    PFN_encodeTiled fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NPROD, int BN>
+cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part, uint32_t* status,
+                         uint64_t timeout_ns, cudaStream_t s) {
+    constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2;
+    constexpr uint32_t STAGE = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
+    constexpr int STAGES = (int)((220u * 1024u) / STAGE) > 8 ? 8 : (int)((220u * 1024u) / STAGE);
+    static_assert(STAGES >= 2, "stage ring too small");
+    const size_t smem = (size_t)STAGES * STAGE + 1024;
+    auto kern = k_tc_gemm<NPROD, BN, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<G, 192, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int NPROD>
+cudaError_t launch_tc_nprod(int BN, const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part,
+                            uint32_t* status, uint64_t to, cudaStream_t s) {
+    switch (BN) {
+#define PBQ_BN(X) case X: return launch_tc_bn<NPROD, X>(m, tiles, KI, G, smax, part, status, to, s);
+        PBQ_BN(16) PBQ_BN(32) PBQ_BN(48) PBQ_BN(64) PBQ_BN(80) PBQ_BN(96) PBQ_BN(112) PBQ_BN(128)
+        PBQ_BN(144) PBQ_BN(160) PBQ_BN(176) PBQ_BN(192) PBQ_BN(208) PBQ_BN(224)
+#undef PBQ_BN
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms) {
+    TcGeom g;
+    g.BN = (int)round_up(N, 16);
+    g.tiles = (rows + kTcBM - 1) / kTcBM;
+    g.KI = (int)((K + kTcBK - 1) / kTcBK);
+    const int64_t T = g.tiles * g.KI;
+    g.G = (int)(T < num_sms ? T : num_sms);
+    if (g.G < 1) g.G = 1;
+    // most segments a CTA can touch: its share spans at most ceil(share / KI) + 1 tiles
+    const int64_t share = (T + g.G - 1) / g.G;
+    g.smax = (int)((share + g.KI - 1) / g.KI + 1);
+    g.part_floats = (int64_t)g.G * g.smax * kTcBM * g.BN;
+    return g;
+}
+
+int64_t tc_ld(int64_t K) { return round_up(K, 64); }
+
+cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, float* part, double* C, int64_t ldc,
+                              uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm) {
+    if (op.N < 1 || op.N > kMaxEll || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
+    CUtensorMap maps[4];
+    if (!make_map(&maps[0], op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[1], op.Alo ? op.Alo : op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[2], op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[3], op.Blo ? op.Blo : op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
+    const uint64_t timeout_ns = 2000000000ull;
+    cudaError_t e = nprod == 3 ? launch_tc_nprod<3>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s)
+                               : launch_tc_nprod<1>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s);
+    if (e != cudaSuccess) return e;
+    if (after_gemm && (e = cudaEventRecord(after_gemm, s)) != cudaSuccess) return e;
+    const int64_t total = op.rows * (int64_t)op.N;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_tc_reduce<<<(unsigned)blocks, 256, 0, s>>>(op.rows, op.N, g.BN, g.tiles, g.KI, g.G, g.smax, part, C, ldc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation: BF16 hi/lo splits (row-major and transposed).
+// hi = RN_bf16(x), lo = RN_bf16(x - hi).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_split_a(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo, int64_t ldh, __nv_bfloat16* __restrict__ thi,
+                          __nv_bfloat16* __restrict__ tlo, int64_t ldt) {
+    __shared__ __nv_bfloat16 sh[32][33], sl[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t r = r0 + k, cc = c0 + tx;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
+        if (r < m && cc < n) {
+            const double x = (double)A[r * lda + cc];
+            h = __double2bfloat16(x);
+            l = __double2bfloat16(x - (double)__bfloat162float(h));
+            hi[r * ldh + cc] = h;
+            if (lo) lo[r * ldh + cc] = l;
+        }
+        sh[k][tx] = h;
+        sl[k][tx] = l;
+    }
+    __syncthreads();
+    if (!thi) return;
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t cc = c0 + k, r = r0 + tx;   // transposed: row cc of A^T, column r
+        if (cc < n && r < m) {
+            thi[cc * ldt + r] = sh[tx][k];
+            if (tlo) tlo[cc * ldt + r] = sl[tx][k];
+        }
+    }
+}
+
+cudaError_t launch_split_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, void* hi, void* lo, int64_t ldh,
+                           void* thi, void* tlo, int64_t ldt, cudaStream_t s) {
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
+    if (a_f32)
+        k_split_a<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldh,
+                                               (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+    else
+        k_split_a<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo,
+                                                ldh, (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Panel P (rows x N FP64, ld ldp) -> transposed BF16 hi/lo (N x rows, ld ldt).
+__global__ void k_split_panel_t(int64_t rows, int N, const double* __restrict__ P, int64_t ldp,
+                                __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo, int64_t ldt) {
+    const int64_t total = rows * (int64_t)N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / rows);
+        const int64_t r = e - (int64_t)j * rows;
+        const double x = P[r * ldp + j];
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        thi[(int64_t)j * ldt + r] = h;
+        if (tlo) tlo[(int64_t)j * ldt + r] = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
+}
+
+cudaError_t launch_split_panel_t(int64_t rows, int N, const double* P, int64_t ldp, void* thi, void* tlo, int64_t ldt,
+                                 cudaStream_t s) {
+    const int64_t total = rows * (int64_t)N;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_split_panel_t<<<(unsigned)blocks, 256, 0, s>>>(rows, N, P, ldp, (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pbq

@@ -11,6 +11,7 @@
 
 #include "../../include/pbpqlp.h"
 #include "internal.h"
+#include "tc_internal.h"
 
 using namespace pbq;
 
@@ -28,6 +29,12 @@ struct pbpqlp_plan_s {
     // workspace layout (byte offsets)
     size_t off_status = 0, off_ctl = 0, off_scal = 0, off_Xm = 0, off_Ym = 0, off_Dm = 0, off_Xn = 0, off_Yn = 0;
     size_t off_part = 0, off_G = 0, off_Rp = 0, off_R = 0, off_Pt = 0, off_work = 0, off_red = 0, total = 0;
+    // mixed modes: BF16 copies of A and A^T, transposed panels, stream-K partials
+    int nprod = 0;                      // 1 (BF16) or 3 (split BF16); 0 in FP64 mode
+    TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
+    int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
+    size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
+    size_t off_Bnhi = 0, off_Bnlo = 0, off_Bmhi = 0, off_Bmlo = 0, off_tcpart = 0;
     void* last_ws = nullptr;
     // observability: CUDA event pairs around each A / A^T pass kernel
     bool timing = false;
@@ -45,6 +52,8 @@ struct Ws {
     int* ctl;
     double* scal;
     double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red;
+    void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
+    float* tcpart;
 };
 
 Ws carve(const pbpqlp_plan_s* P, void* base) {
@@ -65,6 +74,16 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.Pt = (double*)(b + P->off_Pt);
     w.work = (double*)(b + P->off_work);
     w.red = (double*)(b + P->off_red);
+    const bool mixed = P->nprod > 0, split = P->nprod == 3;
+    w.Ahi = mixed ? (void*)(b + P->off_Ahi) : nullptr;
+    w.Alo = split ? (void*)(b + P->off_Alo) : nullptr;
+    w.Athi = mixed ? (void*)(b + P->off_Athi) : nullptr;
+    w.Atlo = split ? (void*)(b + P->off_Atlo) : nullptr;
+    w.Bnhi = mixed ? (void*)(b + P->off_Bnhi) : nullptr;
+    w.Bnlo = split ? (void*)(b + P->off_Bnlo) : nullptr;
+    w.Bmhi = mixed ? (void*)(b + P->off_Bmhi) : nullptr;
+    w.Bmlo = split ? (void*)(b + P->off_Bmlo) : nullptr;
+    w.tcpart = mixed ? (float*)(b + P->off_tcpart) : nullptr;
     return w;
 }
 
@@ -123,6 +142,41 @@ int gemm_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, 
     return PBPQLP_OK;
 }
 
+// Mixed-mode product with A (transA = false: C = A Y, Y n x N) or A^T
+// (C = A^T Y, Y m x N): the FP64 panel Y is split into the transposed BF16
+// operand, then one tcgen05 product + deterministic stream-K reduction.
+int tc_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t ldy, int N, double* C, int64_t ldc,
+            bool timed = false) {
+    cudaStream_t s = P->stream;
+    TcOperands op;
+    const TcGeom* g;
+    if (!transA) {
+        PBQ_TRY(launch_split_panel_t(P->n, N, Y, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s));
+        op.Ahi = w.Ahi; op.Alo = w.Alo; op.rows = P->m; op.K = P->n; op.lda = P->ldk_n;
+        op.Bhi = w.Bnhi; op.Blo = w.Bnlo; op.ldb = P->ldk_n;
+        g = &P->g_nn;
+    } else {
+        PBQ_TRY(launch_split_panel_t(P->m, N, Y, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s));
+        op.Ahi = w.Athi; op.Alo = w.Atlo; op.rows = P->n; op.K = P->m; op.lda = P->ldk_m;
+        op.Bhi = w.Bmhi; op.Blo = w.Bmlo; op.ldb = P->ldk_m;
+        g = &P->g_tn;
+    }
+    op.N = N;
+    TcGeom gg = *g;
+    if (N != P->l) gg = tc_geometry(op.rows, op.K, N, P->num_sms);
+    if (gg.part_floats > g->part_floats) return PBPQLP_EINVAL;
+    const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
+    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+    PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, C, ldc, w.status, s, ev.second));
+    return PBPQLP_OK;
+}
+
+// Split A once per factorization into the BF16 operands of both orientations.
+int tc_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, int64_t lda) {
+    PBQ_TRY(launch_split_a(P->m, P->n, A, a_f32, lda, w.Ahi, w.Alo, P->ldk_n, w.Athi, w.Atlo, P->ldk_m, P->stream));
+    return PBPQLP_OK;
+}
+
 // Orthonormalise X (rows x l, ld ldp) in place: CholeskyQR in pass pairs
 // (X -> Y -> X).  Pair 1 is CholeskyQR2; pairs 2 and 3 run on the device
 // only if a pass of the previous pair needed the shifted retry.
@@ -178,7 +232,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
     if (l64 > m || l64 > n || l64 > kMaxEll) return PBPQLP_EINVAL;
     if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_TF32X3) return PBPQLP_EINVAL;
-    if (mode != PBPQLP_MODE_FP64) return PBPQLP_EUNSUPPORTED;
+    if (mode == PBPQLP_MODE_TF32 || mode == PBPQLP_MODE_TF32X3) return PBPQLP_EUNSUPPORTED;
     pbpqlp_plan_s* P = new (std::nothrow) pbpqlp_plan_s();
     if (!P) return PBPQLP_ENOMEM;
     P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
@@ -222,6 +276,25 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->off_Pt = take(sizeof(double) * l * ldp);
     P->off_work = take(sizeof(double) * (3 * l * l + 2 * l));
     P->off_red = take(sizeof(double) * 2048);
+    if (mode == PBPQLP_MODE_BF16 || mode == PBPQLP_MODE_BF16X3) {
+        P->nprod = (mode == PBPQLP_MODE_BF16X3) ? 3 : 1;
+        P->ldk_n = tc_ld(n);
+        P->ldk_m = tc_ld(m);
+        P->g_nn = tc_geometry(m, n, P->l, P->num_sms);
+        P->g_tn = tc_geometry(n, m, P->l, P->num_sms);
+        const int64_t BN = P->g_nn.BN;
+        const bool split = P->nprod == 3;
+        P->off_Ahi = take(2 * (size_t)m * P->ldk_n);
+        if (split) P->off_Alo = take(2 * (size_t)m * P->ldk_n);
+        P->off_Athi = take(2 * (size_t)n * P->ldk_m);
+        if (split) P->off_Atlo = take(2 * (size_t)n * P->ldk_m);
+        P->off_Bnhi = take(2 * (size_t)BN * P->ldk_n);
+        if (split) P->off_Bnlo = take(2 * (size_t)BN * P->ldk_n);
+        P->off_Bmhi = take(2 * (size_t)BN * P->ldk_m);
+        if (split) P->off_Bmlo = take(2 * (size_t)BN * P->ldk_m);
+        const int64_t pf = P->g_nn.part_floats > P->g_tn.part_floats ? P->g_nn.part_floats : P->g_tn.part_floats;
+        P->off_tcpart = take(sizeof(float) * (size_t)pf);
+    }
     P->total = off;
     *out = P;
     return PBPQLP_OK;
@@ -242,7 +315,8 @@ int pbpqlp_generate_omega(pbpqlp_plan_t P, double* omega) {
 int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
                   const double* omega, double* Qa, double* L, double* Qb) {
     if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
-    if (a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    const bool mixed = P->nprod > 0;
+    if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
     P->last_ws = workspace;
@@ -252,21 +326,28 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     const int64_t m = P->m, n = P->n, ldp = P->ldp;
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
+    // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
+    auto product = [&](bool transA, const double* Y, double* C) -> int {
+        if (mixed) return tc_pass(P, w, transA, Y, ldp, l, C, ldp, true);
+        return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
+                      : gemm_pass(P, w, false, m, n, A, lda, Y, ldp, C, ldp, l, P->S_nn, P->kc_nn, true);
+    };
     // Phi (m x l)
     if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
     else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
     // C = A^T Phi (Eq. 3); Pbar = orth(C) (Eq. 4)
-    if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn, true))) return rc;
+    if ((rc = product(true, w.Xm, w.Xn))) return rc;
     if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
     // power iterations with an orth after every product (Section III-B)
     for (int it = 0; it < P->q; ++it) {
-        if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Xm, ldp, l, P->S_nn, P->kc_nn, true))) return rc;
+        if ((rc = product(false, w.Xn, w.Xm))) return rc;
         if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
-        if ((rc = gemm_pass(P, w, true, n, m, A, lda, w.Xm, ldp, w.Xn, ldp, l, P->S_tn, P->kc_tn, true))) return rc;
+        if ((rc = product(true, w.Xm, w.Xn))) return rc;
         if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
     }
     // D = A Pbar (Eq. 5); [Q, R] = qr(D) (Eq. 6) with R = Q^T D
-    if ((rc = gemm_pass(P, w, false, m, n, A, lda, w.Xn, ldp, w.Dm, ldp, l, P->S_nn, P->kc_nn, true))) return rc;
+    if ((rc = product(false, w.Xn, w.Dm))) return rc;
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
     {
@@ -280,6 +361,28 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
     PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
     return PBPQLP_OK;
+}
+
+int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int trans, const double* Y, int64_t ldy,
+                  int ncols, double* C, int64_t ldc, void* workspace, size_t ws_bytes) {
+    if (!P || !A || !Y || !C || ncols < 1 || ncols > P->l || lda < P->n) return PBPQLP_EINVAL;
+    const int64_t rowsY = trans ? P->m : P->n, rowsC = trans ? P->n : P->m;
+    if (ldy < ncols || ldc < ncols) return PBPQLP_EINVAL;
+    const bool mixed = P->nprod > 0;
+    if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    P->last_ws = workspace;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    (void)rowsY;
+    if (mixed) {
+        if ((rc = tc_prepare_a(P, w, A, a_dtype == PBPQLP_F32, lda))) return rc;
+        return tc_pass(P, w, trans != 0, Y, ldy, ncols, C, ldc);
+    }
+    return trans ? gemm_pass(P, w, true, rowsC, P->m, (const double*)A, lda, Y, ldy, C, ldc, ncols, P->S_tn, P->kc_tn)
+                 : gemm_pass(P, w, false, rowsC, P->n, (const double*)A, lda, Y, ldy, C, ldc, ncols, P->S_nn, P->kc_nn);
 }
 
 int pbpqlp_reconstruct(pbpqlp_plan_t P, const double* Qa, const double* L, const double* Qb, int r, double* Ahat,
