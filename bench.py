@@ -30,12 +30,29 @@ METRIC = "PbP-QLP factorizations/s & TFLOP/s, mixed vs plain FP64 at equal rel. 
 UNIT = "factorizations/s"
 
 WORKLOADS = {
-    "fp64_8000": dict(m=8000, n=8000, k=100, p=10, q=2, spectrum="exp", scale=40.0, rank_cap=1500,
-                      mode="FP64", desc="plain FP64, A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
+    "fp64_8000": dict(m=8000, n=8000, k=100, p=10, q=2, gen="svd", spectrum="exp", scale=40.0, rank_cap=1500,
+                      mode="FP64", compare="BF16X3",
+                      desc="plain FP64, A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
+    "bf16x3_20000": dict(m=20000, n=20000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
+                         compare=None,
+                         desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 20000x20000, k=200 p=20 q=2"),
+    "bf16x3_10000": dict(m=10000, n=10000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
+                         compare=None,
+                         desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 10000x10000, k=200 p=20 q=2 (profiling size)"),
 }
 
 # FP64 issue rate of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, 1700.0, "fallback"
 
 
 def algorithmic_flops(m, n, l, q):
@@ -45,8 +62,36 @@ def algorithmic_flops(m, n, l, q):
 
 def make_matrix(w, seed, device):
     import synth
+    if w["gen"] == "xyt":
+        return synth.torch_xyt_plus_noise(seed, w["m"], w["n"], w["rank"], w["eps"], device=device)
     sig = synth.spectrum(w["spectrum"], w["rank_cap"], w["scale"])
     return synth.torch_svd_matrix(seed, w["m"], w["n"], sig, device=device)
+
+
+def tc_roofline(rows, K, l, nprod, avg_ms, hbm_peak, tc_peak):
+    """Roofline of one tensor-core product launch (rows x K operand, l columns).
+
+    Bytes: the BF16 operand copies of A (hi and lo for the split mode, i.e. the
+    same 4 bytes per element as an FP32 A), the BF16 panel, the FP32 partials.
+    Flops: the MMAs the tensor pipe executes (three per split product, N padded
+    to a multiple of 16)."""
+    bn = (l + 15) // 16 * 16
+    t = avg_ms / 1e3
+    eb = 4.0 if nprod == 3 else 2.0
+    hw_flops = nprod * 2.0 * rows * K * bn
+    nbytes = eb * rows * K + eb * K * bn + 4.0 * rows * bn
+    t_tensor = hw_flops / (tc_peak * 1e12)
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    tensor = t_tensor >= t_hbm
+    ach = hw_flops / t / 1e12 if tensor else nbytes / t / 1e9
+    peak = tc_peak if tensor else hbm_peak
+    return {"kernel": "k_tc_gemm (tcgen05 product with A, %s)" % ("split BF16 x3" if nprod == 3 else "BF16"),
+            "bound": "tensor" if tensor else "hbm", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak,
+            "achieved_basis": "tensor-pipe MMA flops (%d MMAs per product, N padded to %d)" % (nprod, bn)
+            if tensor else "bytes of the BF16 operand copies + panel + partials",
+            "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
+            "avg_launch_ms": avg_ms}
 
 
 def read_traffic(kernel_file_tag):
@@ -132,7 +177,7 @@ def run_reference(args, w, world, rank):
     import oracle
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    A = make_matrix(w, 1000, dev).cpu().numpy()
+    A = make_matrix(w, 1000, dev).cpu().numpy().astype(np.float64)
     l = w["k"] + w["p"]
     for _ in range(args.warmup):
         oracle.pbpqlp(A, l, w["q"], seed=7)
@@ -147,7 +192,7 @@ def run_reference(args, w, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
-                   "l2": "inputs larger than L2 (A is %d MB)" % (w["m"] * w["n"] * 8 // 2 ** 20)},
+                   "mode": w["mode"], "l2": "inputs larger than L2 (A is %d MB)" % (w["m"] * w["n"] * 8 // 2 ** 20)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle factorization per step on the same workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -186,15 +231,43 @@ def main():
 
     m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
     l = k + p
+    hbm_peak, bf16_peak, bf16_sus, peak_src = measured_peaks()
     A = make_matrix(w, 1000 + rank, dev)
     stream = torch.cuda.current_stream(dev)
-    plan = pq.Plan(m, n, k, p, q, seed=7 + rank, stream=stream, device=dev)
+    mode = getattr(pq, "PBPQLP_MODE_" + w["mode"])
+    plan = pq.Plan(m, n, k, p, q, seed=7 + rank, mode=mode, stream=stream, device=dev)
     Qa, L, Qb = plan.outputs(dev)
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    def timed_run(pl, outs, steps, sampler=None):
+        """K factorizations bracketed by barrier + synchronize; returns (ms/step, pass ms, passes, launches, clocks)."""
+        pq.pbpqlp_set_timing(pl.handle, True)
+        pq.pbpqlp_read_timing(pl.handle)
+        l0 = pq.pbpqlp_kernel_launch_count()
+        barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            pl.factor(A, out=outs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        clk = sampler.stop() if sampler else None
+        launches = pq.pbpqlp_kernel_launch_count() - l0
+        pms, pn = pq.pbpqlp_read_timing(pl.handle)
+        pq.pbpqlp_set_timing(pl.handle, False)
+        rc, flags = pl.sync_status()
+        if rc != pq.PBPQLP_OK:
+            raise RuntimeError("device status %d flags %d" % (rc, flags))
+        return e0.elapsed_time(e1) / steps, pms, pn, launches, clk
 
     for _ in range(args.warmup):
         plan.factor(A, out=(Qa, L, Qb))
@@ -203,36 +276,16 @@ def main():
         raise RuntimeError("device status %d flags %d" % (rc, flags))
 
     # ---- device-resident timing (inputs already in HBM)
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
-    pq.pbpqlp_set_timing(plan.handle, True)
-    pq.pbpqlp_read_timing(plan.handle)
-    launches0 = pq.pbpqlp_kernel_launch_count()
-    barrier()
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.factor(A, out=(Qa, L, Qb))
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    clocks = sampler.stop()
-    launches = pq.pbpqlp_kernel_launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
-    pass_ms, pass_launches = pq.pbpqlp_read_timing(plan.handle)
-    pq.pbpqlp_set_timing(plan.handle, False)
-    rc, flags = plan.sync_status()
-    if rc != pq.PBPQLP_OK:
-        raise RuntimeError("device status %d flags %d" % (rc, flags))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(vis) if vis.isdigit() else local)
+    ms, pass_ms, pass_launches, launches, clocks = timed_run(plan, (Qa, L, Qb), args.steps, sampler)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world / (ms / 1e3)
+    err_main = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_RESIDUAL)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     A_host = A.cpu().pin_memory()
@@ -240,21 +293,20 @@ def main():
     out_host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (Qa, L, Qb)]
     h2d = A_host.numel() * A_host.element_size()
     d2h = sum(t.numel() * t.element_size() for t in out_host)
-    for _ in range(1):
+
+    def e2e_step():
         A_dev.copy_(A_host, non_blocking=True)
         plan.factor(A_dev, out=(Qa, L, Qb))
         for h, d in zip(out_host, (Qa, L, Qb)):
             h.copy_(d, non_blocking=True)
+    e2e_step()
     barrier()
     torch.cuda.synchronize(dev)
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
-        A_dev.copy_(A_host, non_blocking=True)
-        plan.factor(A_dev, out=(Qa, L, Qb))
-        for h, d in zip(out_host, (Qa, L, Qb)):
-            h.copy_(d, non_blocking=True)
+        e2e_step()
     f1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -266,33 +318,61 @@ def main():
         ms_e2e = float(t.item())
 
     flops = algorithmic_flops(m, n, l, q)
-    pass_flops = 2.0 * m * n * l
-    avg_pass_s = (pass_ms / pass_launches) / 1e3 if pass_launches else None
-    achieved = pass_flops / avg_pass_s / 1e12 if avg_pass_s else None
-    traffic = read_traffic("dgemm_skinny_fp64_8000")
+    avg_pass_ms = (pass_ms / pass_launches) if pass_launches else None
+    if w["mode"] == "FP64":
+        achieved = 2.0 * m * n * l / (avg_pass_ms / 1e3) / 1e12 if avg_pass_ms else None
+        roofline = {"kernel": "k_dgemm_skinny (A / A^T pass, 2mnl flop per launch)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                    "traffic": read_traffic("dgemm_skinny_fp64_8000"),
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
+                    "launches_timed": pass_launches, "avg_launch_ms": avg_pass_ms}
+        dtype = "f64"
+    else:
+        nprod = 3 if w["mode"] == "BF16X3" else 1
+        roofline = tc_roofline(max(m, n), min(m, n), l, nprod, avg_pass_ms, hbm_peak, bf16_sus)
+        roofline["traffic"] = None
+        roofline["peak_source"] = "%s (MEASURED_PEAKS.json: HBM copy GB/s, bf16 sustained TFLOP/s)" % peak_src
+        roofline["launches_timed"] = pass_launches
+        dtype = "bf16x3" if nprod == 3 else "bf16"
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q, "mode": w["mode"],
-                   "l2": "inputs larger than L2 (A is %d MB), no flush" % (m * n * 8 // 2 ** 20),
+                   "l2": "inputs larger than L2 (A is %d MB), no flush" % (A.numel() * A.element_size() // 2 ** 20),
                    "parallelism": "independent factorizations per GPU" if world > 1 else "single GPU"},
         "tflops_algorithmic": value * flops / 1e12,
-        "roofline": {"kernel": "k_dgemm_skinny (A / A^T pass, 2mnl flop per launch)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
-                     "launches_timed": pass_launches, "avg_launch_ms": (pass_ms / pass_launches) if pass_launches else None},
+        "rel_err_rank_k": err_main,
+        "roofline": roofline,
         "e2e": {"value": world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
     }
 
+    # ---- the same matrix in the mixed mode: speed at (near) equal relative error
+    if w.get("compare"):
+        cmode = getattr(pq, "PBPQLP_MODE_" + w["compare"])
+        cplan = pq.Plan(m, n, k, p, q, seed=7 + rank, mode=cmode, stream=stream, device=dev)
+        couts = cplan.outputs(dev)
+        for _ in range(args.warmup):
+            cplan.factor(A, out=couts)
+        cms, cpms, cpn, _, _ = timed_run(cplan, couts, args.steps)
+        err_c = cplan.error(A, *couts, k, method=pq.PBPQLP_ERR_RESIDUAL)
+        nprod = 3 if w["compare"] == "BF16X3" else 1
+        line["mixed"] = {"mode": w["compare"], "value": world / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
+                         "tflops_algorithmic": world / (cms / 1e3) * flops / 1e12,
+                         "rel_err_rank_k": err_c, "rel_err_rank_k_fp64": err_main,
+                         "error_ratio_vs_fp64": err_c / err_main, "speedup_vs_fp64": ms / cms,
+                         "roofline": tc_roofline(max(m, n), min(m, n), l, nprod, cpms / cpn if cpn else None,
+                                                 hbm_peak, bf16_sus) if cpn else None}
+        del cplan
+
     # ---- CPU baseline: the oracle, rank 0 at N = 1, and parity of the timed result
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        A_np = A_host.numpy()
+        A_np = A_host.numpy().astype(np.float64)
         t0 = time.perf_counter()
         ref = oracle.pbpqlp(A_np, l, q, seed=7)
         dt = time.perf_counter() - t0
@@ -302,8 +382,14 @@ def main():
         Qa_n, L_n, Qb_n = (t.numpy() for t in out_host)
         Ag = oracle.reconstruct(Qa_n, L_n, Qb_n, k)
         Ac = oracle.reconstruct(ref["Q"], ref["L"], ref["P"], k)
-        line["parity"] = {"rel_fro_diff_rank_k": float(np.linalg.norm(Ag - Ac) / np.linalg.norm(A_np)),
-                          "tol": 1e-11}
+        if w["mode"] == "FP64":
+            line["parity"] = {"rel_fro_diff_rank_k": float(np.linalg.norm(Ag - Ac) / np.linalg.norm(A_np)),
+                              "tol": 1e-11}
+        else:
+            e_gpu = float(np.linalg.norm(A_np - Ag) / np.linalg.norm(A_np))
+            e_orc = float(np.linalg.norm(A_np - Ac) / np.linalg.norm(A_np))
+            line["parity"] = {"rel_err_rank_k": e_gpu, "rel_err_rank_k_oracle": e_orc,
+                              "error_ratio": e_gpu / e_orc, "tol_ratio": 1.1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

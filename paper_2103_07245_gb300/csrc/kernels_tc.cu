@@ -15,8 +15,14 @@
 // adds the partials of each tile in CTA order (deterministic) into the FP64
 // output panel.
 //
-// Roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues
-// MMAs, warps 2-5 drain the double-buffered TMEM accumulator.  Every wait on
+// Accumulation: the tensor pipe's FP32 accumulation drifts toward zero by an
+// amount that grows with the depth of the sum, so each segment is cut into
+// chunks of kTcKC k-blocks; a chunk accumulates in TMEM and is then added
+// (round-to-nearest, CUDA cores) into FP32 registers of the epilogue warps.
+//
+// Roles (320 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues
+// MMAs, warps 2-9 drain the double-buffered TMEM chunk accumulator (two warps
+// per TMEM lane quarter, each owning half of the tile's columns).  Every wait on
 // an mbarrier is bounded by a globaltimer deadline; on expiry the CTA sets a
 // status bit, raises a shared abort flag, drains what it issued and returns.
 #include <cuda.h>
@@ -136,9 +142,11 @@ __host__ __device__ __forceinline__ int64_t sk_begin(int64_t c, int64_t T, int64
 
 constexpr int kTcBM = 128;   // rows per tile (one TMEM lane per row)
 constexpr int kTcBK = 64;    // BF16 elements per k-block (one 128-byte swizzle row)
+constexpr int kTcKC = 16;    // k-blocks per TMEM accumulation chunk (1024-deep sums)
+constexpr int kTcThreads = 320;
 
 template <int NPROD, int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int64_t tiles,
           int KI, int smax, float* __restrict__ part, uint32_t* __restrict__ status, uint64_t timeout_ns) {
@@ -163,7 +171,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 128); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf_bar[b], 1); mbar_init(&acce_bar[b], 256); }
         mbar_init(&drain_bar, 1);
         abort_sh = 0;
         issued_sh = 0;
@@ -220,48 +228,52 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int li = 0, seg = 0;
+            int li = 0, chunk = 0;
             bool ok = true;
             int64_t it = it_begin;
             while (ok && it < it_end) {
                 const int64_t tile = it / KI;
                 const int64_t seg_end = ((tile + 1) * KI < it_end) ? (tile + 1) * KI : it_end;
-                const int b = seg & 1;
-                if (seg >= 2 && !mbar_wait(&acce_bar[b], (uint32_t)((seg / 2 - 1) & 1), deadline, &abort_sh)) {
-                    abort_sh = 1;
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)b * ACC_COLS;
-                bool first = true;
-                for (; it < seg_end; ++it, ++li) {
-                    const int s = li % STAGES;
-                    if (!mbar_wait(&full_bar[s], (uint32_t)((li / STAGES) & 1), deadline, &abort_sh)) {
+                while (ok && it < seg_end) {
+                    const int64_t ch_end = (it + kTcKC < seg_end) ? it + kTcKC : seg_end;
+                    const int b = chunk & 1;
+                    if (chunk >= 2 &&
+                        !mbar_wait(&acce_bar[b], (uint32_t)((chunk / 2 - 1) & 1), deadline, &abort_sh)) {
                         abort_sh = 1;
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t ahi = smem_u32(stage_ptr(s, 0)), bhi = smem_u32(stage_ptr(s, 1));
-                    const uint32_t alo = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
-#pragma unroll
-                    for (int kk = 0; kk < kTcBK / 16; ++kk) {
-                        const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along the swizzled row
-                        tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(bhi + off), IDESC,
-                                    (first && kk == 0) ? 0u : 1u);
-                        if (NPROD == 3) {
-                            tc_mma_bf16(dt, sdesc_k_sw128(alo + off), sdesc_k_sw128(bhi + off), IDESC, 1u);
-                            tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(blo + off), IDESC, 1u);
+                    const uint32_t dt = tmem_base + (uint32_t)b * ACC_COLS;
+                    bool first = true;
+                    for (; it < ch_end; ++it, ++li) {
+                        const int s = li % STAGES;
+                        if (!mbar_wait(&full_bar[s], (uint32_t)((li / STAGES) & 1), deadline, &abort_sh)) {
+                            abort_sh = 1;
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t ahi = smem_u32(stage_ptr(s, 0)), bhi = smem_u32(stage_ptr(s, 1));
+                        const uint32_t alo = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+                        for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                            const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along the swizzled row
+                            tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(bhi + off), IDESC,
+                                        (first && kk == 0) ? 0u : 1u);
+                            if (NPROD == 3) {
+                                tc_mma_bf16(dt, sdesc_k_sw128(alo + off), sdesc_k_sw128(bhi + off), IDESC, 1u);
+                                tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(blo + off), IDESC, 1u);
+                            }
+                        }
+                        first = false;
+                        tc_commit(&empty_bar[s]);
+                        consumed_sh = li + 1;
                     }
-                    first = false;
-                    tc_commit(&empty_bar[s]);
-                    consumed_sh = li + 1;
+                    if (!ok) break;
+                    tc_commit(&accf_bar[b]);
+                    ++chunk;
                 }
-                if (!ok) break;
-                tc_commit(&accf_bar[b]);
-                ++seg;
             }
             // all MMAs issued by this thread complete before TMEM is released;
             // this wait ignores the abort flag (bounded by the deadline only)
@@ -273,39 +285,63 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
             }
         }
     } else {
-        // ---------------- epilogue: TMEM -> FP32 partials
-        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        // ---------------- epilogue: TMEM chunks -> FP32 registers -> FP32 partials
+        constexpr int NCH = BN / 16;              // 16-column groups of the tile
+        constexpr int HCH = (NCH + 1) / 2;        // groups owned by one of the two warps of a quarter
+        const int q = warp & 3;                   // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;            // which half of the column groups
         const int row = q * 32 + lane;
-        int seg = 0;
+        float acc[HCH][16];
+        int chunk = 0;
         int64_t it = it_begin;
         const int64_t first_tile = it_begin / KI;
-        while (it < it_end) {
+        bool ok = true;
+        while (ok && it < it_end) {
             const int64_t tile = it / KI;
             const int64_t seg_end = ((tile + 1) * KI < it_end) ? (tile + 1) * KI : it_end;
-            const int b = seg & 1;
-            // warp-uniform decision: the TMEM loads below are .sync.aligned
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (uint32_t)((seg / 2) & 1), deadline, &abort_sh));
-            if (!ok) {
-                abort_sh = 1;
-                break;
+#pragma unroll
+            for (int g = 0; g < HCH; ++g)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[g][i] = 0.f;
+            while (it < seg_end) {
+                const int64_t ch_end = (it + kTcKC < seg_end) ? it + kTcKC : seg_end;
+                const int b = chunk & 1;
+                // warp-uniform decision: the TMEM loads below are .sync.aligned
+                ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (uint32_t)((chunk / 2) & 1), deadline, &abort_sh));
+                if (!ok) {
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + (uint32_t)b * ACC_COLS + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+                for (int g = 0; g < HCH; ++g) {
+                    const int grp = h * HCH + g;
+                    if (grp < NCH) {
+                        float v[16];
+                        tmem_ld16(taddr + grp * 16, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) acc[g][i] += v[i];
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce_bar[b]);
+                it = ch_end;
+                ++chunk;
             }
-            tc_fence_after();
+            if (!ok) break;
             float* slot = part + ((size_t)c * smax + (size_t)(tile - first_tile)) * (size_t)kTcBM * BN;
-            const uint32_t taddr = tmem_base + (uint32_t)b * ACC_COLS + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-            for (int ch = 0; ch < BN / 16; ++ch) {
-                float v[16];
-                tmem_ld16(taddr + ch * 16, v);
-                float4* dst = (float4*)(slot + ((size_t)ch * kTcBM + row) * 16);
-                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-                dst[2] = make_float4(v[8], v[9], v[10], v[11]);
-                dst[3] = make_float4(v[12], v[13], v[14], v[15]);
+#pragma unroll
+            for (int g = 0; g < HCH; ++g) {
+                const int grp = h * HCH + g;
+                if (grp < NCH) {
+                    float4* dst = (float4*)(slot + ((size_t)grp * kTcBM + row) * 16);
+                    dst[0] = make_float4(acc[g][0], acc[g][1], acc[g][2], acc[g][3]);
+                    dst[1] = make_float4(acc[g][4], acc[g][5], acc[g][6], acc[g][7]);
+                    dst[2] = make_float4(acc[g][8], acc[g][9], acc[g][10], acc[g][11]);
+                    dst[3] = make_float4(acc[g][12], acc[g][13], acc[g][14], acc[g][15]);
+                }
             }
-            tc_fence_before();
-            mbar_arrive(&acce_bar[b]);
-            it = seg_end;
-            ++seg;
         }
     }
 
@@ -402,7 +438,7 @@ cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int
     auto kern = k_tc_gemm<NPROD, BN, STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<G, 192, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns);
+    kern<<<G, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns);
     count_launches(1);
     return cudaGetLastError();
 }
