@@ -172,6 +172,32 @@ int pbpqlp_error(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
 int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
 
 /*
+ * Batched factorization: `count` independent matrices of uneven shapes, each
+ * factored by Algorithm 3 exactly as pbpqlp_factor would (same kernels, same
+ * results), advanced together one step per launch over work lists; the whole
+ * launch sequence is captured into one CUDA graph on the first call and
+ * replayed while the buffers stay the same.
+ *   m, n, k (host arrays of count): shapes and target ranks; p and q are
+ *   shared; l_i = k_i + p must satisfy 1 <= k_i <= l_i <= min(m_i, n_i), l_i <= 224.
+ *   Matrix i draws Phi_i from the Philox stream keyed by seed + i.
+ *   A, lda, Qa, L, Qb (host arrays of count): device pointers / leading
+ *   dimensions per matrix, layouts as in pbpqlp_factor.
+ *   workspace: device, >= pbpqlp_batch_workspace_bytes(batch), 256-aligned;
+ *   it also holds the work lists, which every call rewrites.
+ * pbpqlp_batch_sync_status waits and returns the worst device status of the
+ * batch; flags_host (optional, count entries) gets each matrix's status bits.
+ */
+typedef struct pbpqlp_batch_s* pbpqlp_batch_t;
+int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const int64_t* n,
+                        const int* k, int p, int q, uint64_t seed, int mode, void* stream);
+int pbpqlp_batch_destroy(pbpqlp_batch_t batch);
+size_t pbpqlp_batch_workspace_bytes(pbpqlp_batch_t batch);
+int pbpqlp_factor_batched(pbpqlp_batch_t batch, const void* const* A, const int64_t* lda, int a_dtype,
+                          void* workspace, size_t ws_bytes, double* const* Qa, double* const* L,
+                          double* const* Qb);
+int pbpqlp_batch_sync_status(pbpqlp_batch_t batch, uint32_t* flags_host);
+
+/*
  * pbpqlp_factor_static — the paper has no counterpart; this is a deployment
  * variant of pbpqlp_factor for callers that cannot allocate device memory
  * (code whose host framework owns every device allocation, such as an

@@ -84,6 +84,18 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_error.restype = ci
     L.pbpqlp_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.pbpqlp_sync_status.restype = ci
+    pvp = ctypes.POINTER(vp)
+    L.pbpqlp_plan_batched.argtypes = [ctypes.POINTER(vp), ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(ci), ci, ci, u64, ci, vp]
+    L.pbpqlp_plan_batched.restype = ci
+    L.pbpqlp_batch_destroy.argtypes = [vp]
+    L.pbpqlp_batch_destroy.restype = ci
+    L.pbpqlp_batch_workspace_bytes.argtypes = [vp]
+    L.pbpqlp_batch_workspace_bytes.restype = sz
+    L.pbpqlp_factor_batched.argtypes = [vp, pvp, ctypes.POINTER(i64), ci, vp, sz, pvp, pvp, pvp]
+    L.pbpqlp_factor_batched.restype = ci
+    L.pbpqlp_batch_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.pbpqlp_batch_sync_status.restype = ci
     L.pbpqlp_factor_static.argtypes = [vp, vp, i64, ci, vp, vp, vp, vp]
     L.pbpqlp_factor_static.restype = ci
     L.pbpqlp_set_timing.argtypes = [vp, ci]
@@ -199,6 +211,47 @@ def pbpqlp_kernel_launch_count() -> int:
     return int(load().pbpqlp_kernel_launch_count())
 
 
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def pbpqlp_plan_batched(m, n, k, p, q, seed, mode=PBPQLP_MODE_FP64, stream=None):
+    cnt = len(m)
+    h = ctypes.c_void_p()
+    ma = (ctypes.c_int64 * cnt)(*[int(x) for x in m])
+    na = (ctypes.c_int64 * cnt)(*[int(x) for x in n])
+    ka = (ctypes.c_int * cnt)(*[int(x) for x in k])
+    _check(load().pbpqlp_plan_batched(ctypes.byref(h), cnt, ma, na, ka, int(p), int(q),
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(mode), _stream(stream)),
+           "pbpqlp_plan_batched")
+    return h
+
+
+def pbpqlp_batch_destroy(batch):
+    _check(load().pbpqlp_batch_destroy(batch), "pbpqlp_batch_destroy")
+
+
+def pbpqlp_batch_workspace_bytes(batch) -> int:
+    return int(load().pbpqlp_batch_workspace_bytes(batch))
+
+
+def pbpqlp_factor_batched(batch, A, lda, a_dtype, workspace, ws_bytes, Qa, L, Qb):
+    cnt = len(A)
+    la = (ctypes.c_int64 * cnt)(*[int(x) for x in lda])
+    _check(load().pbpqlp_factor_batched(batch, _ptr_array(A), la, int(a_dtype), _ptr(workspace), int(ws_bytes),
+                                        _ptr_array(Qa), _ptr_array(L), _ptr_array(Qb)), "pbpqlp_factor_batched")
+
+
+def pbpqlp_batch_sync_status(batch, count):
+    """Returns (worst status, per-matrix flag list)."""
+    f = (ctypes.c_uint32 * count)()
+    rc = load().pbpqlp_batch_sync_status(batch, f)
+    return rc, [int(x) for x in f]
+
+
 # ------------------------------------------------------- torch convenience layer
 class Plan:
     """Owns a plan handle and a torch-allocated workspace for one shape."""
@@ -262,4 +315,43 @@ class Plan:
         h = getattr(self, "handle", None)
         if h is not None and _lib is not None:
             _lib.pbpqlp_plan_destroy(h)
+            self.handle = None
+
+
+class Batch:
+    """Owns a batched plan and its workspace; factors lists of torch matrices."""
+
+    def __init__(self, shapes_m, shapes_n, ks, p, q, seed, mode=PBPQLP_MODE_FP64, stream=None, device="cuda"):
+        import torch
+        self.m = [int(x) for x in shapes_m]
+        self.n = [int(x) for x in shapes_n]
+        self.k = [int(x) for x in ks]
+        self.p, self.q, self.seed, self.mode = int(p), int(q), int(seed), int(mode)
+        self.l = [k + self.p for k in self.k]
+        self.handle = pbpqlp_plan_batched(self.m, self.n, self.k, p, q, seed, mode, stream)
+        self.ws_bytes = pbpqlp_batch_workspace_bytes(self.handle)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+    def outputs(self, device="cuda"):
+        import torch
+        f = torch.float64
+        return ([torch.empty(m, l, dtype=f, device=device) for m, l in zip(self.m, self.l)],
+                [torch.empty(l, l, dtype=f, device=device) for l in self.l],
+                [torch.empty(n, l, dtype=f, device=device) for n, l in zip(self.n, self.l)])
+
+    def factor(self, As, out=None):
+        import torch
+        a_dtype = PBPQLP_F32 if As[0].dtype == torch.float32 else PBPQLP_F64
+        Qa, L, Qb = out if out is not None else self.outputs(As[0].device)
+        pbpqlp_factor_batched(self.handle, As, [a.stride(0) for a in As], a_dtype, self.workspace, self.ws_bytes,
+                              Qa, L, Qb)
+        return Qa, L, Qb
+
+    def sync_status(self):
+        return pbpqlp_batch_sync_status(self.handle, len(self.m))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.pbpqlp_batch_destroy(h)
             self.handle = None

@@ -1,0 +1,455 @@
+// Batched PbP-QLP: many independent factorizations (uneven shapes) advanced
+// together, one step of Algorithm 3 per launch over host-built work lists.
+// The launch sequence is captured once into a CUDA graph and replayed while
+// the buffers stay the same.  Matrix i draws its Gaussian test matrix from
+// the Philox stream with key seed + i.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pbpqlp.h"
+#include "batched.h"
+#include "internal.h"
+
+using namespace pbq;
+
+namespace {
+
+struct MatWs {
+    size_t Xm, Ym, Dm, Xn, Yn, part, G, Rp, R, Pt, work;
+    int S_m, S_n;          // Gram split counts (rows chunks) of the m- and n-side panels
+};
+
+enum LaunchKind { L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_COPY };
+
+struct Launch {
+    int kind;
+    int TN;
+    bool transA;
+    size_t off;            // byte offset of the unit list inside the list region
+    int n;
+};
+
+}  // namespace
+
+struct pbpqlp_batch_s {
+    int count = 0, p = 0, q = 0, mode = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 152;
+    std::vector<int64_t> m, n;
+    std::vector<int> k, l;
+    int lmax = 0;
+    int64_t ldp = 0;
+    int gram_chunk = 512;           // rows per Gram partial (tuned by pbpqlp_batch_autotune)
+    std::vector<MatWs> mw;
+    size_t off_status = 0, off_ctl = 0, off_lists = 0, lists_cap = 0, total = 0;
+    // host copy of the work lists and the launch sequence built for the last buffers
+    std::vector<unsigned char> host_lists;
+    std::vector<Launch> seq;
+    std::vector<const void*> key;   // pointers the lists were built for
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture_stream = nullptr;   // private stream the graph is recorded on
+    bool use_graph = true;
+    void* last_ws = nullptr;
+    ~pbpqlp_batch_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+    }
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Upper bound of the list bytes for the current sizes (used to size the workspace).
+size_t lists_bound(const pbpqlp_batch_s* B, int gram_chunk_min) {
+    size_t units = 0;
+    for (int i = 0; i < B->count; ++i) {
+        const int64_t mt = (B->m[i] + kGemmBM - 1) / kGemmBM, nt = (B->n[i] + kGemmBM - 1) / kGemmBM;
+        const int64_t lt = (B->l[i] + kGemmBM - 1) / kGemmBM;
+        const int64_t gm = (B->m[i] + gram_chunk_min - 1) / gram_chunk_min;
+        const int64_t gn = (B->n[i] + gram_chunk_min - 1) / gram_chunk_min;
+        const int64_t passes = 2 * B->q + 2;
+        // A passes, Grams (6 passes per orth), R = Q^T D, Qb
+        units += (size_t)(passes * (mt + nt)) * sizeof(GemmUnit);
+        units += (size_t)((passes * 6) * lt * std::max(gm, gn) + lt * gm) * sizeof(GemmUnit);
+        units += (size_t)(mt + nt) * sizeof(GemmUnit);
+        // reductions, Cholesky / small QR / Gaussian units, TRSM row blocks
+        units += (size_t)(passes * 6 + 2) * sizeof(ReduceUnit);
+        units += (size_t)(passes * 6 + 2) * sizeof(MatUnit);
+        units += (size_t)(passes * 6) * ((std::max(B->m[i], B->n[i]) + 63) / 64) * sizeof(TrsmUnit);
+    }
+    return units + 64 * 1024 + 256 * 64;
+}
+
+class ListBuilder {
+  public:
+    explicit ListBuilder(pbpqlp_batch_s* B) : B_(B) { B_->host_lists.clear(); B_->seq.clear(); }
+    template <typename T>
+    void add(int kind, const std::vector<T>& units, int TN = 0, bool transA = false) {
+        if (units.empty()) return;
+        size_t off = align_up(B_->host_lists.size(), 256);
+        B_->host_lists.resize(off + units.size() * sizeof(T));
+        std::memcpy(B_->host_lists.data() + off, units.data(), units.size() * sizeof(T));
+        B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size()});
+    }
+    void memset_ctl() { B_->seq.push_back(Launch{L_MEMSET_CTL, 0, false, 0, 0}); }
+
+  private:
+    pbpqlp_batch_s* B_;
+};
+
+struct Ptrs {
+    char* ws;
+    const void* const* A;
+    const int64_t* lda;
+    double* const* Qa;
+    double* const* L;
+    double* const* Qb;
+};
+
+double* P64(const Ptrs& p, size_t off) { return (double*)(p.ws + off); }
+
+// Build the whole launch sequence of one batched factorization (FP64 mode).
+int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
+    ListBuilder lb(B);
+    const int cnt = B->count;
+    const int64_t ldp = B->ldp;
+    const int TN = (B->lmax + 15) / 16;
+    uint32_t* status = (uint32_t*)(pt.ws + B->off_status);
+    int* ctl = (int*)(pt.ws + B->off_ctl);
+
+    // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i
+    {
+        std::vector<MatUnit> u(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            MatUnit x{};
+            x.l = B->l[i]; x.rows = B->m[i]; x.out = P64(pt, B->mw[i].Xm); x.ld = ldp; x.seed = B->seed + (uint64_t)i;
+            u[i] = x;
+        }
+        lb.add(L_GAUSS, u);
+    }
+    // one product with A_i for every matrix: out_i = op(A_i) Y_i
+    auto product = [&](bool transA, auto ysel, auto csel) {
+        std::vector<GemmUnit> u;
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t M = transA ? B->n[i] : B->m[i], K = transA ? B->m[i] : B->n[i];
+            for (int64_t m0 = 0; m0 < M; m0 += kGemmBM) {
+                GemmUnit g{};
+                g.A = (const double*)pt.A[i]; g.lda = pt.lda[i];
+                g.B = ysel(i); g.ldb = ldp;
+                g.C = csel(i); g.ldc = ldp;   // tile rows are absolute (m0 + r)
+                g.M = M; g.m0 = m0; g.kbeg = 0; g.kend = K; g.N = B->l[i]; g.transA = transA; g.cond = nullptr;
+                u.push_back(g);
+            }
+        }
+        lb.add(L_GEMM, u, TN, transA);
+    };
+    // CholeskyQR passes for every matrix's panel (side 0: m x l panels, side 1: n x l)
+    auto orth = [&](int side, auto srcsel, auto xsel, auto ysel) {
+        lb.memset_ctl();
+        for (int pass = 1; pass <= 6; ++pass) {
+            std::vector<GemmUnit> gu;
+            std::vector<ReduceUnit> ru;
+            std::vector<MatUnit> cu;
+            std::vector<TrsmUnit> tu;
+            for (int i = 0; i < cnt; ++i) {
+                const int64_t rows = side == 0 ? B->m[i] : B->n[i];
+                const int l = B->l[i];
+                const int S = side == 0 ? B->mw[i].S_m : B->mw[i].S_n;
+                const double* src = pass == 1 ? srcsel(i) : ((pass & 1) ? xsel(i) : ysel(i));
+                double* dst = (pass & 1) ? ysel(i) : xsel(i);
+                int* c = ctl + 16 * i;
+                const int* cond = pass <= 2 ? nullptr : c + 8 + (pass + 1) / 2;
+                double* part = P64(pt, B->mw[i].part);
+                const int64_t ps = (int64_t)l * ldp;
+                for (int s = 0; s < S; ++s)
+                    for (int64_t m0 = 0; m0 < l; m0 += kGemmBM) {
+                        GemmUnit g{};
+                        g.A = src; g.lda = ldp; g.B = src; g.ldb = ldp; g.C = part + s * ps; g.ldc = ldp;
+                        g.M = l; g.m0 = m0; g.kbeg = (int64_t)s * B->gram_chunk;
+                        g.kend = std::min<int64_t>(rows, (int64_t)(s + 1) * B->gram_chunk);
+                        g.N = l; g.transA = 1; g.cond = cond;
+                        gu.push_back(g);
+                    }
+                ReduceUnit r{};
+                r.part = part; r.C = P64(pt, B->mw[i].G); r.ps = ps; r.ldp = ldp; r.ldc = l; r.M = l; r.N = l; r.S = S;
+                r.cond = cond;
+                ru.push_back(r);
+                MatUnit m{};
+                m.l = l; m.pass = pass; m.rows = rows; m.G = P64(pt, B->mw[i].G); m.Rp = P64(pt, B->mw[i].Rp);
+                m.ctl = c; m.status = status + i;
+                cu.push_back(m);
+                for (int64_t r0 = 0; r0 < rows; r0 += 64) {
+                    TrsmUnit t{};
+                    t.X = src; t.Y = dst; t.Rp = P64(pt, B->mw[i].Rp); t.ldx = ldp; t.ldy = ldp; t.r0 = r0;
+                    t.r1 = std::min<int64_t>(rows, r0 + 64); t.l = l; t.cond = cond;
+                    tu.push_back(t);
+                }
+            }
+            lb.add(L_GEMM, gu, TN, true);
+            lb.add(L_REDUCE, ru);
+            lb.add(L_CHOL, cu);
+            lb.add(L_TRSM, tu);
+        }
+    };
+    auto Xm = [&](int i) { return P64(pt, B->mw[i].Xm); };
+    auto Ym = [&](int i) { return P64(pt, B->mw[i].Ym); };
+    auto Dm = [&](int i) { return P64(pt, B->mw[i].Dm); };
+    auto Xn = [&](int i) { return P64(pt, B->mw[i].Xn); };
+    auto Yn = [&](int i) { return P64(pt, B->mw[i].Yn); };
+
+    product(true, Xm, Xn);                  // C = A^T Phi (Eq. 3)
+    orth(1, Xn, Xn, Yn);                    // Pbar = orth(C) (Eq. 4)
+    for (int it = 0; it < B->q; ++it) {     // power iterations (Section III-B)
+        product(false, Xn, Xm);
+        orth(0, Xm, Xm, Ym);
+        product(true, Xm, Xn);
+        orth(1, Xn, Xn, Yn);
+    }
+    product(false, Xn, Dm);                 // D = A Pbar (Eq. 5)
+    orth(0, Dm, Xm, Ym);                    // Q = orth(D) (Eq. 6), result in Xm
+    {                                       // R = Q^T D
+        std::vector<GemmUnit> gu;
+        std::vector<ReduceUnit> ru;
+        for (int i = 0; i < cnt; ++i) {
+            const int l = B->l[i];
+            const int S = B->mw[i].S_m;
+            double* part = P64(pt, B->mw[i].part);
+            const int64_t ps = (int64_t)l * ldp;
+            for (int s = 0; s < S; ++s)
+                for (int64_t m0 = 0; m0 < l; m0 += kGemmBM) {
+                    GemmUnit g{};
+                    g.A = Xm(i); g.lda = ldp; g.B = Dm(i); g.ldb = ldp; g.C = part + s * ps; g.ldc = ldp;
+                    g.M = l; g.m0 = m0; g.kbeg = (int64_t)s * B->gram_chunk;
+                    g.kend = std::min<int64_t>(B->m[i], (int64_t)(s + 1) * B->gram_chunk);
+                    g.N = l; g.transA = 1; g.cond = nullptr;
+                    gu.push_back(g);
+                }
+            ReduceUnit r{};
+            r.part = part; r.C = P64(pt, B->mw[i].R); r.ps = ps; r.ldp = ldp; r.ldc = l; r.M = l; r.N = l; r.S = S;
+            r.cond = nullptr;
+            ru.push_back(r);
+        }
+        lb.add(L_GEMM, gu, TN, true);
+        lb.add(L_REDUCE, ru);
+    }
+    {                                       // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7)
+        std::vector<MatUnit> u;
+        for (int i = 0; i < cnt; ++i) {
+            MatUnit x{};
+            x.l = B->l[i]; x.G = P64(pt, B->mw[i].R); x.L = pt.L[i]; x.Pt = P64(pt, B->mw[i].Pt);
+            x.work = P64(pt, B->mw[i].work);
+            u.push_back(x);
+        }
+        lb.add(L_SQR, u);
+    }
+    {                                       // Qb = Pbar Ptil (Eq. 8); Qa = Q (copy to ld l)
+        std::vector<GemmUnit> gu;
+        for (int i = 0; i < cnt; ++i) {
+            const int l = B->l[i];
+            for (int64_t m0 = 0; m0 < B->n[i]; m0 += kGemmBM) {
+                GemmUnit g{};
+                g.A = Xn(i); g.lda = ldp; g.B = P64(pt, B->mw[i].Pt); g.ldb = l; g.C = pt.Qb[i]; g.ldc = l;
+                g.M = B->n[i]; g.m0 = m0; g.kbeg = 0; g.kend = l; g.N = l; g.transA = 0; g.cond = nullptr;
+                gu.push_back(g);
+            }
+        }
+        lb.add(L_GEMM, gu, TN, false);
+        std::vector<ReduceUnit> cu;          // a one-term "reduction" is a strided copy
+        for (int i = 0; i < cnt; ++i) {
+            ReduceUnit r{};
+            r.part = Xm(i); r.C = pt.Qa[i]; r.ps = 0; r.ldp = ldp; r.ldc = B->l[i]; r.M = B->m[i]; r.N = B->l[i];
+            r.S = 1; r.cond = nullptr;
+            cu.push_back(r);
+        }
+        lb.add(L_REDUCE, cu);
+    }
+    if (B->host_lists.size() > B->lists_cap) return PBPQLP_EWORKSPACE;
+    return PBPQLP_OK;
+}
+
+#define PBQ_TRY(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
+
+int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
+    char* lists = ws + B->off_lists;
+    int* ctl = (int*)(ws + B->off_ctl);
+    PBQ_TRY(cudaMemsetAsync(ws + B->off_status, 0, sizeof(uint32_t) * (size_t)B->count, s));
+    for (const Launch& L : B->seq) {
+        const void* u = lists + L.off;
+        switch (L.kind) {
+            case L_MEMSET_CTL: PBQ_TRY(cudaMemsetAsync(ctl, 0, sizeof(int) * 16 * (size_t)B->count, s)); break;
+            case L_GAUSS: PBQ_TRY(launch_gaussian_list((const MatUnit*)u, L.n, s)); break;
+            case L_GEMM: PBQ_TRY(launch_dgemm_list(L.TN, L.transA, (const GemmUnit*)u, L.n, s)); break;
+            case L_REDUCE: PBQ_TRY(launch_reduce_list((const ReduceUnit*)u, L.n, s)); break;
+            case L_CHOL: PBQ_TRY(launch_cholesky_list((const MatUnit*)u, L.n, B->lmax, s)); break;
+            case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, B->lmax, s)); break;
+            case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, s)); break;
+            default: return PBPQLP_EINVAL;
+        }
+    }
+    return PBPQLP_OK;
+}
+
+void layout(pbpqlp_batch_s* B) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    B->off_status = take(sizeof(uint32_t) * (size_t)B->count);
+    B->off_ctl = take(sizeof(int) * 16 * (size_t)B->count);
+    const int64_t ldp = B->ldp;
+    B->mw.assign(B->count, MatWs{});
+    for (int i = 0; i < B->count; ++i) {
+        MatWs& w = B->mw[i];
+        const int64_t m = B->m[i], n = B->n[i], l = B->l[i];
+        w.S_m = (int)((m + B->gram_chunk - 1) / B->gram_chunk);
+        w.S_n = (int)((n + B->gram_chunk - 1) / B->gram_chunk);
+        w.Xm = take(8 * (size_t)(m * ldp));
+        w.Ym = take(8 * (size_t)(m * ldp));
+        w.Dm = take(8 * (size_t)(m * ldp));
+        w.Xn = take(8 * (size_t)(n * ldp));
+        w.Yn = take(8 * (size_t)(n * ldp));
+        w.part = take(8 * (size_t)(std::max(w.S_m, w.S_n) * l * ldp));
+        w.G = take(8 * (size_t)(l * l));
+        w.Rp = take(8 * (size_t)(packed_tri((int)l) + l));
+        w.R = take(8 * (size_t)(l * l));
+        w.Pt = take(8 * (size_t)(l * l));
+        w.work = take(8 * (size_t)(3 * l * l + 2 * l));
+    }
+    B->lists_cap = lists_bound(B, 256);
+    B->off_lists = take(B->lists_cap);
+    B->total = off;
+}
+
+int run(pbpqlp_batch_s* B, const Ptrs& pt, size_t ws_bytes) {
+    std::vector<const void*> key;
+    key.push_back(pt.ws);
+    for (int i = 0; i < B->count; ++i) {
+        key.push_back(pt.A[i]); key.push_back((const void*)(intptr_t)pt.lda[i]);
+        key.push_back(pt.Qa[i]); key.push_back(pt.L[i]); key.push_back(pt.Qb[i]);
+    }
+    (void)ws_bytes;
+    const bool rebuilt = key != B->key || B->seq.empty();
+    if (rebuilt) {
+        if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+        int rc = build_lists(B, pt);
+        if (rc) return rc;
+        B->key = key;
+    }
+    // the lists live in the caller's workspace: refresh them on every call
+    // (a pageable-memory copy is staged before the call returns)
+    PBQ_TRY(cudaMemcpyAsync(pt.ws + B->off_lists, B->host_lists.data(), B->host_lists.size(),
+                            cudaMemcpyHostToDevice, B->stream));
+    if (rebuilt) {
+        if (B->use_graph && !B->capture_stream &&
+            cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            B->capture_stream = nullptr;
+            B->use_graph = false;
+            cudaGetLastError();
+        }
+        if (B->use_graph) {
+            // record on the private stream (nothing runs); the graph is launched on the caller's stream
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int64_t before = launch_count();
+                const int rc2 = enqueue(B, pt.ws, B->capture_stream);
+                count_launches(before - launch_count());   // captured, not run
+                const cudaError_t ec = cudaStreamEndCapture(B->capture_stream, &g);
+                if (rc2 == PBPQLP_OK && ec == cudaSuccess && g &&
+                    cudaGraphInstantiate(&B->exec, g, 0) == cudaSuccess) {
+                    cudaGraphDestroy(g);
+                } else {
+                    if (g) cudaGraphDestroy(g);
+                    B->exec = nullptr;
+                    B->use_graph = false;
+                    cudaGetLastError();
+                }
+            } else {
+                B->use_graph = false;
+                cudaGetLastError();
+            }
+        }
+    }
+    if (B->exec) {
+        PBQ_TRY(cudaGraphLaunch(B->exec, B->stream));
+        int64_t kernels = 0;
+        for (const Launch& L : B->seq) kernels += (L.kind != L_MEMSET_CTL);
+        count_launches(kernels);
+        return PBPQLP_OK;
+    }
+    return enqueue(B, pt.ws, B->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const int64_t* n, const int* k, int p, int q,
+                        uint64_t seed, int mode, void* stream) {
+    if (!out) return PBPQLP_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !m || !n || !k || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
+    if (mode != PBPQLP_MODE_FP64) return PBPQLP_EUNSUPPORTED;
+    pbpqlp_batch_s* B = new (std::nothrow) pbpqlp_batch_s();
+    if (!B) return PBPQLP_ENOMEM;
+    B->count = count; B->p = p; B->q = q; B->seed = seed; B->mode = mode; B->stream = (cudaStream_t)stream;
+    B->m.assign(m, m + count);
+    B->n.assign(n, n + count);
+    B->k.assign(k, k + count);
+    B->l.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const int64_t l = (int64_t)k[i] + p;
+        if (m[i] < 1 || n[i] < 1 || k[i] < 1 || l > m[i] || l > n[i] || l > kMaxEll) { delete B; return PBPQLP_EINVAL; }
+        B->l[i] = (int)l;
+        B->lmax = std::max(B->lmax, (int)l);
+    }
+    B->ldp = round_up(B->lmax, 8);
+    const char* env = std::getenv("PBPQLP_BATCH_NO_GRAPH");
+    if (env && env[0] == '1') B->use_graph = false;
+    layout(B);
+    *out = B;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_batch_destroy(pbpqlp_batch_t B) {
+    delete B;
+    return PBPQLP_OK;
+}
+
+size_t pbpqlp_batch_workspace_bytes(pbpqlp_batch_t B) { return B ? B->total : 0; }
+
+int pbpqlp_factor_batched(pbpqlp_batch_t B, const void* const* A, const int64_t* lda, int a_dtype, void* workspace,
+                          size_t ws_bytes, double* const* Qa, double* const* L, double* const* Qb) {
+    if (!B || !A || !lda || !Qa || !L || !Qb) return PBPQLP_EINVAL;
+    if (a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    if (!workspace || ws_bytes < B->total || ((uintptr_t)workspace & 255u)) return PBPQLP_EWORKSPACE;
+    for (int i = 0; i < B->count; ++i)
+        if (!A[i] || !Qa[i] || !L[i] || !Qb[i] || lda[i] < B->n[i]) return PBPQLP_EINVAL;
+    B->last_ws = workspace;
+    Ptrs pt{(char*)workspace, A, lda, Qa, L, Qb};
+    return run(B, pt, ws_bytes);
+}
+
+int pbpqlp_batch_sync_status(pbpqlp_batch_t B, uint32_t* flags_host) {
+    if (!B) return PBPQLP_EINVAL;
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PBPQLP_ECUDA;
+    std::vector<uint32_t> st(B->count, 0);
+    if (B->last_ws && cudaMemcpy(st.data(), (char*)B->last_ws + B->off_status, sizeof(uint32_t) * st.size(),
+                                 cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PBPQLP_ECUDA;
+    uint32_t all = 0;
+    for (int i = 0; i < B->count; ++i) {
+        all |= st[i];
+        if (flags_host) flags_host[i] = st[i];
+    }
+    if (all & kStNonFinite) return PBPQLP_ENONFINITE;
+    if (all & kStTimeout) return PBPQLP_ETIMEOUT;
+    if (all & kStBreakdown) return PBPQLP_EBREAKDOWN;
+    return PBPQLP_OK;
+}
+
+}  // extern "C"

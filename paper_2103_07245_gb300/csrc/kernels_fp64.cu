@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "fp64_device.cuh"
 
 #include <atomic>
 
@@ -22,36 +23,8 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
-    }
-}
-
 __global__ void k_gaussian(uint64_t seed, int64_t rows, int l, double* __restrict__ out, int64_t ld) {
-    const int64_t total = rows * (int64_t)l;
-    const int64_t npairs = (total + 1) / 2;
-    const double inv53 = 1.0 / 9007199254740992.0;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npairs;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c[4] = {(uint32_t)b, (uint32_t)((uint64_t)b >> 32), 0u, 0u};
-        philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-        const uint64_t a53 = ((uint64_t)(c[0] >> 5) << 26) | (uint64_t)(c[1] >> 6);
-        const uint64_t b53 = ((uint64_t)(c[2] >> 5) << 26) | (uint64_t)(c[3] >> 6);
-        const double u1 = ((double)a53 + 1.0) * inv53;
-        const double u2 = (double)b53 * inv53;
-        const double rad = sqrt(-2.0 * log(u1));
-        double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);
-        const int64_t t0 = 2 * b;
-        out[(t0 / l) * ld + (t0 % l)] = rad * cs;
-        if (t0 + 1 < total) out[((t0 + 1) / l) * ld + ((t0 + 1) % l)] = rad * sn;
-    }
+    dev_gaussian(seed, rows, l, out, ld, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 cudaError_t launch_gaussian(uint64_t seed, int64_t rows, int l, double* out, int64_t ld, cudaStream_t s) {
@@ -76,63 +49,10 @@ k_dgemm_skinny(int64_t M, int N, int64_t K, const double* __restrict__ A, int64_
                const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc,
                int64_t kchunk, int64_t part_stride, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
-    constexpr int BM = kGemmBM, BK = kGemmBK, BN = 16 * TN;
-    __shared__ double As[BK][BM];
-    __shared__ double Bs[BK][BN];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
     const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
     const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
-
-    double acc[4][TN];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < TN; ++c) acc[r][c] = 0.0;
-
-    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int idx = tid + 256 * i;
-            int r, kk;
-            if (!TA) { r = idx >> 4; kk = idx & 15; }
-            else     { kk = idx >> 6; r = idx & 63; }
-            const int64_t gm = m0 + r, gk = k0 + kk;
-            double v = 0.0;
-            if (gm < M && gk < kend) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
-            As[kk][r] = v;
-        }
-        for (int idx = tid; idx < BK * BN; idx += 256) {
-            const int kk = idx / BN, c = idx - kk * BN;
-            const int64_t gk = k0 + kk;
-            Bs[kk][c] = (c < N && gk < kend) ? B[gk * ldb + c] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[TN];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
-#pragma unroll
-            for (int c = 0; c < TN; ++c) b[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-    double* Cb = C + (int64_t)blockIdx.y * part_stride;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int64_t gm = m0 + ty * 4 + r;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int c = 0; c < TN; ++c) {
-            const int col = tx + 16 * c;
-            if (col < N) Cb[gm * ldc + col] = acc[r][c];
-        }
-    }
+    dev_dgemm_tile<TN, TA>(M, N, A, lda, B, ldb, C + (int64_t)blockIdx.y * part_stride, ldc,
+                           (int64_t)blockIdx.x * kGemmBM, kbeg, kend);
 }
 
 template <bool TA>
@@ -209,92 +129,11 @@ cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, 
 // pass pair j (passes 2j-1, 2j) must run.  Pair 1 always runs; pair j+1 runs
 // iff a pass of pair j was shifted.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t pidx(int l, int a, int b) {
-    return (int64_t)a * (2 * l - a + 1) / 2 + (b - a);
-}
-
 __global__ void __launch_bounds__(1024)
 k_cholesky(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
            uint32_t* __restrict__ status, int* __restrict__ ctl, int pass) {
-    if (pass >= 3 && ctl[8 + (pass + 1) / 2] == 0) return;
     extern __shared__ double sm[];
-    const int64_t P = (int64_t)l * (l + 1) / 2;
-    double* S = sm;
-    double* dg0 = sm + P;
-    double* dinv = dg0 + l;
-    __shared__ int s_fail;
-    __shared__ double s_inv, s_shift;
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-    const double tau = 1e-12;
-
-    for (int j = tid; j < l; j += nth) dg0[j] = G[(int64_t)j * l + j];
-    if (tid == 0) { s_shift = 0.0; s_fail = 0; }
-    __syncthreads();
-
-    int shifted = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        const double shift = s_shift;
-        for (int a = warp; a < l; a += nwarp)
-            for (int b = a + lane; b < l; b += 32)
-                S[pidx(l, a, b)] = G[(int64_t)a * l + b] + (a == b ? shift : 0.0);
-        if (tid == 0) s_fail = 0;
-        __syncthreads();
-        for (int j = 0; j < l; ++j) {
-            if (tid == 0) {
-                const double d = S[pidx(l, j, j)];
-                const double thr = (attempt == 0) ? tau * dg0[j] : 0.0;
-                if (!isfinite(d)) s_fail = 2;
-                else if (!(d > thr)) s_fail = 1;
-                else {
-                    const double r = sqrt(d);
-                    S[pidx(l, j, j)] = r;
-                    s_inv = 1.0 / r;
-                    dinv[j] = s_inv;
-                }
-            }
-            __syncthreads();
-            if (s_fail) break;
-            const double inv = s_inv;
-            const int64_t rj = pidx(l, j, 0);
-            for (int c = j + 1 + tid; c < l; c += nth) S[rj + c] *= inv;
-            __syncthreads();
-            for (int a = j + 1 + warp; a < l; a += nwarp) {
-                const double rja = S[rj + a];
-                const int64_t ra = pidx(l, a, 0);
-                for (int b = a + lane; b < l; b += 32) S[ra + b] -= rja * S[rj + b];
-            }
-            __syncthreads();
-        }
-        const int fail = s_fail;
-        __syncthreads();
-        if (!fail) break;
-        if (fail == 2 || attempt == 1) {
-            if (tid == 0) atomicOr(status, fail == 2 ? kStNonFinite : kStBreakdown);
-            // leave a finite identity factor so later kernels stay finite
-            for (int a = warp; a < l; a += nwarp)
-                for (int b = a + lane; b < l; b += 32) S[pidx(l, a, b)] = (a == b) ? 1.0 : 0.0;
-            for (int j = tid; j < l; j += nth) dinv[j] = 1.0;
-            __syncthreads();
-            break;
-        }
-        // shifted retry: G + s I, s = 11 (rows*l + l(l+1)) u tr(G)  (u = 2^-53)
-        if (tid == 0) {
-            double tr = 0.0;
-            for (int j = 0; j < l; ++j) tr += dg0[j];
-            double sh = 11.0 * ((double)rows * l + (double)l * (l + 1)) * 1.1102230246251565e-16 * tr;
-            if (!(sh > 0.0) || !isfinite(sh)) sh = 1.0;  // all-zero panel: any factor will do
-            s_shift = sh;
-        }
-        shifted = 1;
-        __syncthreads();
-    }
-    for (int64_t e = tid; e < P; e += nth) Rp[e] = S[e];
-    for (int j = tid; j < l; j += nth) Rp[P + j] = dinv[j];
-    if (tid == 0) {
-        ctl[pass] = shifted;
-        if ((pass & 1) == 0) ctl[8 + pass / 2 + 1] = (ctl[pass - 1] | ctl[pass]) ? 1 : 0;
-        if (shifted) atomicOr(status, kStShifted);
-    }
+    dev_cholesky(l, rows, G, Rp, status, ctl, pass, sm);
 }
 
 cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rp, uint32_t* status, int* ctl, int pass,
@@ -321,36 +160,8 @@ k_trsm_rows(int64_t rows, int l, const double* __restrict__ Rp, const double* __
     const int64_t P = (int64_t)l * (l + 1) / 2;
     for (int64_t e = threadIdx.x; e < P + l; e += blockDim.x) sR[e] = Rp[e];
     __syncthreads();
-    const double* dinv = sR + P;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < rows; r += (int64_t)gridDim.x * 8) {
-        double x[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = lane + 32 * u;
-            x[u] = (c < l) ? X[r * ldx + c] : 0.0;
-        }
-#pragma unroll
-        for (int u0 = 0; u0 < U; ++u0) {
-            for (int tt = 0; tt < 32; ++tt) {
-                const int t = 32 * u0 + tt;
-                if (t >= l) break;
-                const double y = __shfl_sync(0xffffffffu, x[u0], tt) * dinv[t];
-                if (lane == tt) x[u0] = y;
-                const int64_t rt = pidx(l, t, 0);
-#pragma unroll
-                for (int u = u0; u < U; ++u) {
-                    const int c = lane + 32 * u;
-                    if (c > t && c < l) x[u] -= y * sR[rt + c];
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = lane + 32 * u;
-            if (c < l) Y[r * ldy + c] = x[u];
-        }
-    }
+    const int warp = threadIdx.x >> 5;
+    dev_trsm_rows<U>(l, sR, X, ldx, Y, ldy, (int64_t)blockIdx.x * 8 + warp, rows, (int64_t)gridDim.x * 8);
 }
 
 cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double* X, int64_t ldx, double* Y,
@@ -383,87 +194,7 @@ cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double
 __global__ void __launch_bounds__(1024)
 k_small_qr(int l, const double* __restrict__ R, double* __restrict__ L, double* __restrict__ Ptil,
            double* __restrict__ work) {
-    double* Wt = work;
-    double* V = Wt + (int64_t)l * l;
-    double* Pt = V + (int64_t)l * l;   // Ptil transposed: row c = column c of Ptil
-    double* vv = Pt + (int64_t)l * l;
-    double* sg = vv + l;
-    __shared__ double s_alpha;
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-    const int64_t ll = (int64_t)l * l;
-    for (int64_t e = tid; e < ll; e += nth) {
-        const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
-        Wt[e] = (i >= c) ? R[e] : 0.0;
-        V[e] = 0.0;
-        Pt[e] = (i == c) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int j = 0; j < l; ++j) {
-        double* wj = Wt + (int64_t)j * l;
-        if (warp == 0) {
-            double t = 0.0;
-            for (int i = j + 1 + lane; i < l; i += 32) t += wj[i] * wj[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) {
-                const double x0 = wj[j];
-                const double nrm = sqrt(x0 * x0 + t);
-                if (nrm == 0.0) { vv[j] = 0.0; s_alpha = 0.0; }
-                else {
-                    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-                    const double v0 = x0 - alpha;
-                    V[(int64_t)j * l + j] = v0;
-                    vv[j] = v0 * v0 + t;
-                    s_alpha = alpha;
-                }
-            }
-        }
-        __syncthreads();
-        double* vj = V + (int64_t)j * l;
-        for (int i = j + 1 + tid; i < l; i += nth) vj[i] = wj[i];
-        __syncthreads();
-        const double vvj = vv[j];
-        if (vvj != 0.0) {
-            for (int c = j + 1 + warp; c < l; c += nwarp) {
-                double* wc = Wt + (int64_t)c * l;
-                double d = 0.0;
-                for (int i = j + lane; i < l; i += 32) d += vj[i] * wc[i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const double f = 2.0 * d / vvj;
-                for (int i = j + lane; i < l; i += 32) wc[i] -= f * vj[i];
-            }
-            if (tid == 0) wj[j] = s_alpha;
-            for (int i = j + 1 + tid; i < l; i += nth) wj[i] = 0.0;
-        }
-        __syncthreads();
-    }
-    // Ptil = H_0 ... H_{l-1} [I]: columns c < j are untouched unit vectors at step j.
-    for (int j = l - 1; j >= 0; --j) {
-        const double vvj = vv[j];
-        if (vvj != 0.0) {
-            const double* vj = V + (int64_t)j * l;
-            for (int c = j + warp; c < l; c += nwarp) {
-                double* pc = Pt + (int64_t)c * l;
-                double d = 0.0;
-                for (int i = j + lane; i < l; i += 32) d += vj[i] * pc[i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const double f = 2.0 * d / vvj;
-                for (int i = j + lane; i < l; i += 32) pc[i] -= f * vj[i];
-            }
-        }
-        __syncthreads();
-    }
-    for (int j = tid; j < l; j += nth) sg[j] = (Wt[(int64_t)j * l + j] < 0.0) ? -1.0 : 1.0;
-    __syncthreads();
-    // L[b][a] = Rtil[a][b] = sg[a] * W[a][b] = sg[a] * Wt[b][a]  (b >= a)
-    for (int64_t e = tid; e < ll; e += nth) {
-        const int b = (int)(e / l), a = (int)(e - (int64_t)b * l);
-        L[e] = (b >= a) ? sg[a] * Wt[e] : 0.0;
-        // Ptil[i][c] = sg[c] * Pt[c][i]  with (i, c) = (b, a)
-        Ptil[e] = sg[a] * Pt[(int64_t)a * l + b];
-    }
+    dev_small_qr(l, R, L, Ptil, work);
 }
 
 cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s) {

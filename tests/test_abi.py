@@ -79,3 +79,14 @@ def test_plan_workspace_is_sized_and_factor_validates(pq):
         assert e.value.status == pq.PBPQLP_EINVAL
     finally:
         pq.pbpqlp_plan_destroy(h)
+
+
+def test_batched_plan_validates(pq):
+    with pytest.raises(pq.PbpqlpError) as e:
+        pq.pbpqlp_plan_batched([100, 50], [80, 60], [10, 60], 5, 1, seed=1, stream=0)
+    assert e.value.status == pq.PBPQLP_EINVAL
+    h = pq.pbpqlp_plan_batched([100, 500], [80, 300], [10, 20], 5, 1, seed=1, stream=0)
+    try:
+        assert pq.pbpqlp_batch_workspace_bytes(h) > 8 * (100 + 500) * 32
+    finally:
+        pq.pbpqlp_batch_destroy(h)

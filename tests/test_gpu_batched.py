@@ -1,0 +1,88 @@
+"""Batched factorization (many uneven matrices, work-list launches captured in
+one CUDA graph) against the oracle, matrix by matrix."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def pq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2103_07245_gb300 as pq
+    pq.load(build_if_missing=True)
+    return pq
+
+
+def _batch(seed, count):
+    shapes = synth.batched_shapes(seed, count, m_range=(130, 900), n_lo=70, n_hi=600, k_range=(4, 40))
+    mats = [synth.poly_decay(seed * 1000 + i, s["m"], s["n"], s["alpha"]) for i, s in enumerate(shapes)]
+    return shapes, mats
+
+
+def test_batched_matches_oracle_per_matrix(pq):
+    import torch
+    shapes, mats = _batch(3, 12)
+    p, q, seed = 8, 1, 41
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], p, q, seed)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    Qa, L, Qb = B.factor(As)
+    rc, flags = B.sync_status()
+    assert rc == pq.PBPQLP_OK, flags
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        ref = oracle.pbpqlp(A, s["k"] + p, q, seed=seed + i)
+        g = [Qa[i].cpu().numpy(), L[i].cpu().numpy(), Qb[i].cpu().numpy()]
+        for r in (s["k"], s["k"] + p):
+            d = np.linalg.norm(oracle.reconstruct(*g, r) - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], r))
+            assert d / np.linalg.norm(A) <= TOL, (i, r, d)
+        assert np.array_equal(g[1], np.tril(g[1]))
+
+
+def test_batched_equals_single_and_replays_bitwise(pq):
+    import torch
+    shapes, mats = _batch(5, 6)
+    p, q, seed = 6, 2, 9
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], p, q, seed)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    outs = B.outputs()
+    B.factor(As, out=outs)
+    first = [[t.clone() for t in ts] for ts in outs]
+    B.factor(As, out=outs)      # graph replay
+    rc, _ = B.sync_status()
+    assert rc == pq.PBPQLP_OK
+    for ts0, ts1 in zip(first, outs):
+        for a, b in zip(ts0, ts1):
+            assert torch.equal(a, b)
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        plan = pq.Plan(s["m"], s["n"], s["k"], p, q, seed=seed + i)
+        Qa, L, Qb = plan.factor(As[i])
+        g1 = [t.cpu().numpy() for t in (Qa, L, Qb)]
+        g2 = [outs[0][i].cpu().numpy(), outs[1][i].cpu().numpy(), outs[2][i].cpu().numpy()]
+        d = np.linalg.norm(oracle.reconstruct(*g1, s["k"]) - oracle.reconstruct(*g2, s["k"]))
+        assert d / np.linalg.norm(A) <= TOL
+
+
+def test_batched_status_is_per_matrix(pq):
+    import torch
+    shapes = [dict(m=200, n=150, k=10), dict(m=300, n=120, k=8), dict(m=180, n=180, k=12)]
+    mats = [synth.rank_r(1, 200, 150, 5), synth.poly_decay(2, 300, 120, 1.0), synth.poly_decay(3, 180, 180, 2.0)]
+    mats[1] = mats[1].copy()
+    mats[1][7, 9] = np.nan
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], 5, 1, 3)
+    Qa, L, Qb = B.factor([torch.from_numpy(a).cuda() for a in mats])
+    rc, flags = B.sync_status()
+    assert rc == pq.PBPQLP_ENONFINITE
+    assert flags[1] & 4 and not (flags[0] & 4) and not (flags[2] & 4)
+    assert flags[0] & 1      # rank 5 < l = 15: shifted retry used
+    g0 = [Qa[0].cpu().numpy(), L[0].cpu().numpy(), Qb[0].cpu().numpy()]
+    assert oracle.rel_fro_error(mats[0], *g0, 10) < 1e-12
+    ref2 = oracle.pbpqlp(mats[2], 17, 1, seed=3 + 2)
+    g2 = [Qa[2].cpu().numpy(), L[2].cpu().numpy(), Qb[2].cpu().numpy()]
+    d = np.linalg.norm(oracle.reconstruct(*g2, 12) - oracle.reconstruct(ref2["Q"], ref2["L"], ref2["P"], 12))
+    assert d / np.linalg.norm(mats[2]) <= TOL
