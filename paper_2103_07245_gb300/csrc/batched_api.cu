@@ -3,6 +3,8 @@
 // The launch sequence is captured once into a CUDA graph and replayed while
 // the buffers stay the same.  Matrix i draws its Gaussian test matrix from
 // the Philox stream with key seed + i.
+#include <cuda.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -14,6 +16,7 @@
 #include "../../include/pbpqlp.h"
 #include "batched.h"
 #include "internal.h"
+#include "tc_internal.h"
 
 using namespace pbq;
 
@@ -22,9 +25,12 @@ namespace {
 struct MatWs {
     size_t Xm, Ym, Dm, Xn, Yn, part, G, Rp, R, Pt, work;
     int S_m, S_n;          // Gram split counts (rows chunks) of the m- and n-side panels
+    // TF32 modes: split copies of A and A^T, transposed panels
+    size_t Ahi, Alo, Athi, Atlo, Bnhi, Bnlo, Bmhi, Bmlo;
+    int64_t ldn, ldm;      // their leading dimensions (n, m rounded up to 32)
 };
 
-enum LaunchKind { L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_COPY };
+enum LaunchKind { L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_SPLIT, L_PSPLIT, L_TC };
 
 struct Launch {
     int kind;
@@ -46,8 +52,11 @@ struct pbpqlp_batch_s {
     int lmax = 0;
     int64_t ldp = 0;
     int gram_chunk = 512;           // rows per Gram partial (tuned by pbpqlp_batch_autotune)
+    int nprod = 0;                  // TF32 modes: 1 (TF32) or 3 (split TF32); 0 in FP64 mode
+    int a_f32 = 0;                  // element type of the A pointers the lists were built for
     std::vector<MatWs> mw;
     size_t off_status = 0, off_ctl = 0, off_lists = 0, lists_cap = 0, total = 0;
+    size_t maps_off = 0;            // tensor-map table inside the list region
     // host copy of the work lists and the launch sequence built for the last buffers
     std::vector<unsigned char> host_lists;
     std::vector<Launch> seq;
@@ -83,6 +92,11 @@ size_t lists_bound(const pbpqlp_batch_s* B, int gram_chunk_min) {
         units += (size_t)(passes * 6 + 2) * sizeof(ReduceUnit);
         units += (size_t)(passes * 6 + 2) * sizeof(MatUnit);
         units += (size_t)(passes * 6) * ((std::max(B->m[i], B->n[i]) + 63) / 64) * sizeof(TrsmUnit);
+        if (B->nprod) {
+            units += 8 * 128;                                                   // tensor maps
+            units += (size_t)(passes * ((B->m[i] + 127) / 128 + (B->n[i] + 127) / 128)) * sizeof(TcUnit);
+            units += (size_t)((B->m[i] + 31) / 32) * sizeof(SplitUnit) + (size_t)passes * sizeof(PanelUnit);
+        }
     }
     return units + 64 * 1024 + 256 * 64;
 }
@@ -99,6 +113,13 @@ class ListBuilder {
         B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size()});
     }
     void memset_ctl() { B_->seq.push_back(Launch{L_MEMSET_CTL, 0, false, 0, 0}); }
+    // raw table at the start of the list region (the tensor maps)
+    size_t raw(const void* data, size_t bytes) {
+        size_t off = align_up(B_->host_lists.size(), 256);
+        B_->host_lists.resize(off + bytes);
+        std::memcpy(B_->host_lists.data() + off, data, bytes);
+        return off;
+    }
 
   private:
     pbpqlp_batch_s* B_;
@@ -114,6 +135,7 @@ struct Ptrs {
 };
 
 double* P64(const Ptrs& p, size_t off) { return (double*)(p.ws + off); }
+float* P32(const Ptrs& p, size_t off) { return (float*)(p.ws + off); }
 
 // Build the whole launch sequence of one batched factorization (FP64 mode).
 int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
@@ -124,6 +146,36 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     uint32_t* status = (uint32_t*)(pt.ws + B->off_status);
     int* ctl = (int*)(pt.ws + B->off_ctl);
 
+    // TF32 modes: the tensor-map table (8 maps per matrix) and the split of every A_i
+    if (B->nprod) {
+        std::vector<CUtensorMap> maps((size_t)8 * cnt);
+        for (int i = 0; i < cnt; ++i) {
+            const MatWs& w = B->mw[i];
+            const int npad = (int)round_up(B->l[i], 16);
+            const void* bases[8] = {P32(pt, w.Ahi), P32(pt, w.Alo ? w.Alo : w.Ahi), P32(pt, w.Athi),
+                                    P32(pt, w.Atlo ? w.Atlo : w.Athi), P32(pt, w.Bnhi), P32(pt, w.Bnlo ? w.Bnlo : w.Bnhi),
+                                    P32(pt, w.Bmhi), P32(pt, w.Bmlo ? w.Bmlo : w.Bmhi)};
+            const int64_t rows[8] = {B->m[i], B->m[i], B->n[i], B->n[i], B->l[i], B->l[i], B->l[i], B->l[i]};
+            const int64_t cols[8] = {B->n[i], B->n[i], B->m[i], B->m[i], B->n[i], B->n[i], B->m[i], B->m[i]};
+            const int64_t lds[8] = {w.ldn, w.ldn, w.ldm, w.ldm, w.ldn, w.ldn, w.ldm, w.ldm};
+            for (int t = 0; t < 8; ++t)
+                if (!make_map_f32(&maps[(size_t)8 * i + t], bases[t], rows[t], cols[t], lds[t], t < 4 ? 128 : npad))
+                    return PBPQLP_EINVAL;
+        }
+        B->maps_off = lb.raw(maps.data(), maps.size() * sizeof(CUtensorMap));
+        std::vector<SplitUnit> su;
+        for (int i = 0; i < cnt; ++i) {
+            const MatWs& w = B->mw[i];
+            for (int64_t r0 = 0; r0 < B->m[i]; r0 += 32) {
+                SplitUnit x{};
+                x.A = pt.A[i]; x.lda = pt.lda[i]; x.a_f32 = B->a_f32; x.m = B->m[i]; x.n = B->n[i]; x.r0 = r0;
+                x.hi = P32(pt, w.Ahi); x.lo = w.Alo ? P32(pt, w.Alo) : nullptr; x.ldh = w.ldn;
+                x.thi = P32(pt, w.Athi); x.tlo = w.Atlo ? P32(pt, w.Atlo) : nullptr; x.ldt = w.ldm;
+                su.push_back(x);
+            }
+        }
+        lb.add(L_SPLIT, su);
+    }
     // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i
     {
         std::vector<MatUnit> u(cnt);
@@ -136,6 +188,35 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     }
     // one product with A_i for every matrix: out_i = op(A_i) Y_i
     auto product = [&](bool transA, auto ysel, auto csel) {
+        if (B->nprod) {
+            std::vector<PanelUnit> pu;
+            std::vector<TcUnit> tu;
+            for (int i = 0; i < cnt; ++i) {
+                const MatWs& w = B->mw[i];
+                PanelUnit x{};
+                x.Y = ysel(i); x.ldy = ldp; x.N = B->l[i];
+                x.rows = transA ? B->m[i] : B->n[i];
+                x.thi = P32(pt, transA ? w.Bmhi : w.Bnhi);
+                const size_t lo = transA ? w.Bmlo : w.Bnlo;
+                x.tlo = lo ? P32(pt, lo) : nullptr;
+                x.ldt = transA ? w.ldm : w.ldn;
+                pu.push_back(x);
+                const int64_t M = transA ? B->n[i] : B->m[i], K = transA ? B->m[i] : B->n[i];
+                for (int64_t m0 = 0; m0 < M; m0 += 128) {
+                    TcUnit t{};
+                    t.amap_hi = 8 * i + (transA ? 2 : 0); t.amap_lo = t.amap_hi + 1;
+                    t.bmap_hi = 8 * i + (transA ? 6 : 4); t.bmap_lo = t.bmap_hi + 1;
+                    t.m0 = (int)m0; t.N = B->l[i]; t.npad = (int)round_up(B->l[i], 16); t.KI = (int)((K + 31) / 32);
+                    t.C = csel(i); t.ldc = ldp; t.rows = M;
+                    tu.push_back(t);
+                }
+            }
+            // longest contraction first, then dealt round-robin to the persistent CTAs
+            std::stable_sort(tu.begin(), tu.end(), [](const TcUnit& a, const TcUnit& b) { return a.KI > b.KI; });
+            lb.add(L_PSPLIT, pu);
+            lb.add(L_TC, tu);
+            return;
+        }
         std::vector<GemmUnit> u;
         for (int i = 0; i < cnt; ++i) {
             const int64_t M = transA ? B->n[i] : B->m[i], K = transA ? B->m[i] : B->n[i];
@@ -290,6 +371,12 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
             case L_CHOL: PBQ_TRY(launch_cholesky_list((const MatUnit*)u, L.n, B->lmax, s)); break;
             case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, B->lmax, s)); break;
             case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, s)); break;
+            case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, s)); break;
+            case L_PSPLIT: PBQ_TRY(launch_split_panel_tf32_list((const PanelUnit*)u, L.n, s)); break;
+            case L_TC:
+                PBQ_TRY(launch_tc_list(B->nprod, lists + B->maps_off, (const TcUnit*)u, L.n, B->num_sms,
+                                       (uint32_t*)(ws + B->off_status), s));
+                break;
             default: return PBPQLP_EINVAL;
         }
     }
@@ -319,6 +406,20 @@ void layout(pbpqlp_batch_s* B) {
         w.R = take(8 * (size_t)(l * l));
         w.Pt = take(8 * (size_t)(l * l));
         w.work = take(8 * (size_t)(3 * l * l + 2 * l));
+        if (B->nprod) {
+            const bool split = B->nprod == 3;
+            const int64_t npad = round_up(l, 16);
+            w.ldn = round_up(n, 32);
+            w.ldm = round_up(m, 32);
+            w.Ahi = take(4 * (size_t)(m * w.ldn));
+            w.Alo = split ? take(4 * (size_t)(m * w.ldn)) : 0;
+            w.Athi = take(4 * (size_t)(n * w.ldm));
+            w.Atlo = split ? take(4 * (size_t)(n * w.ldm)) : 0;
+            w.Bnhi = take(4 * (size_t)(npad * w.ldn));
+            w.Bnlo = split ? take(4 * (size_t)(npad * w.ldn)) : 0;
+            w.Bmhi = take(4 * (size_t)(npad * w.ldm));
+            w.Bmlo = split ? take(4 * (size_t)(npad * w.ldm)) : 0;
+        }
     }
     B->lists_cap = lists_bound(B, 256);
     B->off_lists = take(B->lists_cap);
@@ -393,7 +494,7 @@ int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const 
     if (!out) return PBPQLP_EINVAL;
     *out = nullptr;
     if (count < 1 || !m || !n || !k || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
-    if (mode != PBPQLP_MODE_FP64) return PBPQLP_EUNSUPPORTED;
+    if (mode != PBPQLP_MODE_FP64 && mode != PBPQLP_MODE_TF32 && mode != PBPQLP_MODE_TF32X3) return PBPQLP_EUNSUPPORTED;
     pbpqlp_batch_s* B = new (std::nothrow) pbpqlp_batch_s();
     if (!B) return PBPQLP_ENOMEM;
     B->count = count; B->p = p; B->q = q; B->seed = seed; B->mode = mode; B->stream = (cudaStream_t)stream;
@@ -406,6 +507,15 @@ int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const 
         if (m[i] < 1 || n[i] < 1 || k[i] < 1 || l > m[i] || l > n[i] || l > kMaxEll) { delete B; return PBPQLP_EINVAL; }
         B->l[i] = (int)l;
         B->lmax = std::max(B->lmax, (int)l);
+    }
+    B->nprod = mode == PBPQLP_MODE_TF32X3 ? 3 : mode == PBPQLP_MODE_TF32 ? 1 : 0;
+    if (B->nprod && B->lmax > kTcListBNMax) { delete B; return PBPQLP_EUNSUPPORTED; }
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            B->num_sms = sms;
+        cudaGetLastError();
     }
     B->ldp = round_up(B->lmax, 8);
     const char* env = std::getenv("PBPQLP_BATCH_NO_GRAPH");
@@ -425,11 +535,12 @@ size_t pbpqlp_batch_workspace_bytes(pbpqlp_batch_t B) { return B ? B->total : 0;
 int pbpqlp_factor_batched(pbpqlp_batch_t B, const void* const* A, const int64_t* lda, int a_dtype, void* workspace,
                           size_t ws_bytes, double* const* Qa, double* const* L, double* const* Qb) {
     if (!B || !A || !lda || !Qa || !L || !Qb) return PBPQLP_EINVAL;
-    if (a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    if (B->nprod ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
     if (!workspace || ws_bytes < B->total || ((uintptr_t)workspace & 255u)) return PBPQLP_EWORKSPACE;
     for (int i = 0; i < B->count; ++i)
         if (!A[i] || !Qa[i] || !L[i] || !Qb[i] || lda[i] < B->n[i]) return PBPQLP_EINVAL;
     B->last_ws = workspace;
+    if (B->a_f32 != (a_dtype == PBPQLP_F32)) { B->a_f32 = a_dtype == PBPQLP_F32; B->key.clear(); }
     Ptrs pt{(char*)workspace, A, lda, Qa, L, Qb};
     return run(B, pt, ws_bytes);
 }

@@ -43,4 +43,38 @@ cudaError_t launch_split_a(int64_t m, int64_t n, const void* A, int a_f32, int64
 cudaError_t launch_split_panel_t(int64_t rows, int N, const double* P, int64_t ldp, void* thi, void* tlo, int64_t ldt,
                                  cudaStream_t s);
 
+// ---- grouped TF32 products of the batched path (kernels_tc_list.cu) ----------
+// One unit: C[m0 .. m0+127, 0 .. N) = Aop Bt^T over the full contraction
+// (KI k-blocks of 32 FP32 elements), operands given by tensor-map indices.
+struct TcUnit {
+    int amap_hi, amap_lo, bmap_hi, bmap_lo;
+    int m0, N, npad, KI;
+    double* C;
+    int64_t ldc, rows;
+};
+constexpr int kTcListBNMax = 128;   // largest padded N of the grouped kernel
+// nprod 1 (TF32) or 3 (split TF32); units should be sorted by cost (largest first).
+cudaError_t launch_tc_list(int nprod, const void* maps, const TcUnit* units, int nunits, int num_sms, uint32_t* status,
+                           cudaStream_t s);
+// Host: encode a 2-D FP32 tensor map (rows x cols, ld elements, box {32, box_rows}, 128-byte swizzle).
+bool make_map_f32(void* map128, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+
+// A strip of one matrix for the TF32 split: rows [r0, r0+32) of A (m x n) into
+// hi/lo (ld ldh) and transposed hi/lo (ld ldt).
+struct SplitUnit {
+    const void* A;
+    float *hi, *lo, *thi, *tlo;
+    int64_t lda, ldh, ldt, m, n, r0;
+    int a_f32;
+};
+cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, cudaStream_t s);
+// One panel: Y (rows x N FP64, ld ldy) into transposed TF32 hi/lo (N x rows, ld ldt).
+struct PanelUnit {
+    const double* Y;
+    float *thi, *tlo;
+    int64_t rows, ldy, ldt;
+    int N;
+};
+cudaError_t launch_split_panel_tf32_list(const PanelUnit* units, int nunits, cudaStream_t s);
+
 }  // namespace pbq

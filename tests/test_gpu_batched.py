@@ -86,3 +86,49 @@ def test_batched_status_is_per_matrix(pq):
     g2 = [Qa[2].cpu().numpy(), L[2].cpu().numpy(), Qb[2].cpu().numpy()]
     d = np.linalg.norm(oracle.reconstruct(*g2, 12) - oracle.reconstruct(ref2["Q"], ref2["L"], ref2["P"], 12))
     assert d / np.linalg.norm(mats[2]) <= TOL
+
+
+def _errors(A64, g, ref, k):
+    e_gpu = oracle.rel_fro_error(A64, *g, k)
+    e_orc = oracle.rel_fro_error(A64, ref["Q"], ref["L"], ref["P"], k)
+    return e_gpu, e_orc
+
+
+@pytest.mark.parametrize("a32", [True, False])
+def test_batched_split_tf32_within_1p1_of_oracle(pq, a32):
+    """TF32 x3 tensor-core products, FP64 Gram / Cholesky / small QR: each
+    matrix's rank-k error is within 1.1x of the oracle's on the same data."""
+    import torch
+    shapes = synth.batched_shapes(11, 10, m_range=(200, 1200), n_lo=100, n_hi=700, k_range=(8, 48))
+    mats = [synth.poly_decay(500 + i, s["m"], s["n"], s["alpha"]).astype(np.float32).astype(np.float64)
+            for i, s in enumerate(shapes)]
+    p, q, seed = 8, 1, 77
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], p, q, seed,
+                 mode=pq.PBPQLP_MODE_TF32X3)
+    As = [torch.from_numpy(a.astype(np.float32) if a32 else a).cuda() for a in mats]
+    Qa, L, Qb = B.factor(As)
+    rc, flags = B.sync_status()
+    assert rc == pq.PBPQLP_OK, flags
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        ref = oracle.pbpqlp(A, s["k"] + p, q, seed=seed + i)
+        g = [Qa[i].cpu().numpy(), L[i].cpu().numpy(), Qb[i].cpu().numpy()]
+        e_gpu, e_orc = _errors(A, g, ref, s["k"])
+        assert e_gpu <= 1.1 * e_orc, (i, s, e_gpu, e_orc)
+        assert np.array_equal(g[1], np.tril(g[1]))
+
+
+def test_batched_tf32_single_term_runs(pq):
+    import torch
+    shapes = synth.batched_shapes(12, 6, m_range=(200, 900), n_lo=100, n_hi=600, k_range=(8, 32))
+    mats = [synth.poly_decay(700 + i, s["m"], s["n"], 1.0).astype(np.float32) for i, s in enumerate(shapes)]
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], 8, 1, 5,
+                 mode=pq.PBPQLP_MODE_TF32)
+    Qa, L, Qb = B.factor([torch.from_numpy(a).cuda() for a in mats])
+    rc, flags = B.sync_status()
+    assert rc == pq.PBPQLP_OK, flags
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        A64 = A.astype(np.float64)
+        ref = oracle.pbpqlp(A64, s["k"] + 8, 1, seed=5 + i)
+        g = [Qa[i].cpu().numpy(), L[i].cpu().numpy(), Qb[i].cpu().numpy()]
+        e_gpu, e_orc = _errors(A64, g, ref, s["k"])
+        assert np.isfinite(e_gpu) and e_gpu <= 2.0 * e_orc, (i, e_gpu, e_orc)
