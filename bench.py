@@ -36,6 +36,11 @@ WORKLOADS = {
     "bf16x3_20000": dict(m=20000, n=20000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
                          compare=None,
                          desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 20000x20000, k=200 p=20 q=2"),
+    "batched_512": dict(batched=True, count=512, p=8, q=1, mode="TF32X3", compare="FP64",
+                        desc="batched split-TF32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], Haar U V, "
+                             "sigma_i = i^-alpha, alpha~U[1,3], k~U[8,64], p=8, q=1, A in FP32"),
+    "batched_64": dict(batched=True, count=64, p=8, q=1, mode="TF32X3", compare="FP64",
+                       desc="batched split-TF32: 64 matrices of the 512-matrix distribution (profiling size)"),
     "bf16x3_10000": dict(m=10000, n=10000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
                          compare=None,
                          desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 10000x10000, k=200 p=20 q=2 (profiling size)"),
@@ -202,6 +207,205 @@ def run_reference(args, w, world, rank):
     return 0
 
 
+def run_batched(args, w, world, rank, local):
+    """The uneven batch: value = factorizations/s of the whole batch per GPU."""
+    import numpy as np
+    import torch
+    import paper_2103_07245_gb300 as pq
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pq.load(build_if_missing=True)
+    hbm_peak, bf16_peak, bf16_sus, peak_src = measured_peaks()
+    shapes = synth.batched_shapes(2024 + rank, w["count"])
+    p, q = w["p"], w["q"]
+    A64, A32 = [], []
+    for i, sh in enumerate(shapes):
+        r = min(sh["m"], sh["n"])
+        sig = synth.spectrum("poly", r, sh["alpha"])
+        a = synth.torch_svd_matrix_device(7000 + 131 * rank + i, sh["m"], sh["n"], sig, device=dev)
+        A32.append(a.float().contiguous())
+        A64.append(A32[-1].double().contiguous())   # the FP32 data, exactly, for the FP64 comparison
+    ms_, ns_, ks_ = [s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes]
+    stream = torch.cuda.current_stream(dev)
+    mode = getattr(pq, "PBPQLP_MODE_" + w["mode"])
+    B = pq.Batch(ms_, ns_, ks_, p, q, seed=11 + rank, mode=mode, stream=stream, device=dev)
+    outs = B.outputs(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    B.factor(A32, out=outs)
+    tuned_ms = None
+    if not args.no_autotune:
+        tuned_ms = B.autotune(A32, outs)
+    for _ in range(args.warmup):
+        B.factor(A32, out=outs)
+    rc, flags = B.sync_status()
+    if rc != pq.PBPQLP_OK:
+        raise RuntimeError("batch status %d" % rc)
+    pq.pbpqlp_batch_set_timing(B.handle, True)
+    B.factor(A32, out=outs)          # records the graph with the timing events
+    torch.cuda.synchronize(dev)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(vis) if vis.isdigit() else local)
+    l0 = pq.pbpqlp_kernel_launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tc_ms, tc_n = 0.0, 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.factor(A32, out=outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    launches = pq.pbpqlp_kernel_launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    tc_ms, tc_n = pq.pbpqlp_batch_read_timing(B.handle)   # the last step's grouped products
+    pq.pbpqlp_batch_set_timing(B.handle, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    count = w["count"]
+    value = world * count / (ms / 1e3)
+
+    def rel_errors(out_t, As):
+        e = []
+        for i, sh in enumerate(shapes):
+            k = sh["k"]
+            Ahat = (out_t[0][i][:, :k] @ out_t[1][i][:k, :k]) @ out_t[2][i][:, :k].T
+            e.append(float(torch.linalg.norm(As[i] - Ahat) / torch.linalg.norm(As[i])))
+        return np.array(e)
+
+    err_tc = rel_errors(outs, A64)
+    # end to end: host (pinned) A_i in, factors out, every step
+    A_host = [a.cpu().pin_memory() for a in A32]
+    out_host = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in ts] for ts in outs]
+    A_dev = [torch.empty_like(a) for a in A32]
+    h2d = sum(a.numel() * a.element_size() for a in A_host)
+    d2h = sum(t.numel() * t.element_size() for ts in out_host for t in ts)
+
+    def e2e_step():
+        for h, d in zip(A_host, A_dev):
+            d.copy_(h, non_blocking=True)
+        B.factor(A_dev, out=outs)
+        for hs, ds in zip(out_host, outs):
+            for h, d in zip(hs, ds):
+                h.copy_(d, non_blocking=True)
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = f0.elapsed_time(f1) / args.steps
+
+    # the batched FP64 form on the same data (the plain-FP64 GPU reference)
+    cmp = None
+    if w.get("compare"):
+        Bf = pq.Batch(ms_, ns_, ks_, p, q, seed=11 + rank, mode=getattr(pq, "PBPQLP_MODE_" + w["compare"]),
+                      stream=stream, device=dev)
+        of = Bf.outputs(dev)
+        Bf.factor(A64, out=of)
+        torch.cuda.synchronize(dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        csteps = max(1, min(3, args.steps))
+        c0.record(stream)
+        for _ in range(csteps):
+            Bf.factor(A64, out=of)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        cms = c0.elapsed_time(c1) / csteps
+        err_f = rel_errors(of, A64)
+        ratio = err_tc / err_f
+        cmp = {"mode": w["compare"], "value": count / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
+               "speedup_of_mixed": cms / ms, "error_ratio_mixed_vs_fp64": {
+                   "median": float(np.median(ratio)), "max": float(np.max(ratio))}}
+        del Bf, of
+
+    # roofline of the grouped tensor-core products (the last step's 2q+2 launches)
+    hw, nbytes = 0.0, 0.0
+    for sh in shapes:
+        npad = (sh["k"] + p + 15) // 16 * 16
+        for trans in ([True, False] * (q + 1)):
+            M, K = (sh["n"], sh["m"]) if trans else (sh["m"], sh["n"])
+            Mp = (M + 127) // 128 * 128
+            hw += 3 * 2.0 * Mp * K * npad
+            nbytes += 8.0 * M * K + 8.0 * K * npad + 8.0 * M * (sh["k"] + p)
+    tc_t = tc_ms / 1e3 if tc_n else None
+    tf32_sus = bf16_sus / 2.0
+    roofline = None
+    if tc_t:
+        t_tensor, t_hbm = hw / (tf32_sus * 1e12), nbytes / (hbm_peak * 1e9)
+        tensor = t_tensor >= t_hbm
+        ach = hw / tc_t / 1e12 if tensor else nbytes / tc_t / 1e9
+        peak = tf32_sus if tensor else hbm_peak
+        roofline = {"kernel": "k_tc_list (grouped tcgen05 kind::tf32 products, split x3)",
+                    "bound": "tensor" if tensor else "hbm", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": "%s: TF32 = bf16 sustained / 2 (nominal ratio), HBM copy" % peak_src,
+                    "tensor_frac": hw / tc_t / 1e12 / tf32_sus, "hbm_frac": nbytes / tc_t / 1e9 / hbm_peak,
+                    "launches_timed": tc_n, "avg_launch_ms": tc_ms / tc_n}
+    flops = sum(algorithmic_flops(sh["m"], sh["n"], sh["k"] + p, q) for sh in shapes)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "config": {"workload": w["desc"], "count": count, "p": p, "q": q, "mode": w["mode"],
+                   "l2": "inputs larger than L2 (%d MB of A), no flush" % (sum(a.numel() * 4 for a in A32) // 2 ** 20),
+                   "parallelism": "independent batches per GPU" if world > 1 else "single GPU",
+                   "graph": "one CUDA graph replay per step", "autotuned_ms": tuned_ms},
+        "tflops_algorithmic": value * flops / count / 1e12,
+        "rel_err_rank_k": {"median": float(np.median(err_tc)), "max": float(np.max(err_tc))},
+        "roofline": roofline,
+        "e2e": {"value": world * count / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clocks, "fp64_batched": cmp,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sample = list(range(0, count, max(1, count // 6)))[:6]
+        t0 = time.perf_counter()
+        refs = {i: oracle.pbpqlp(A64[i].cpu().numpy(), shapes[i]["k"] + p, q, seed=11 + i) for i in sample}
+        dt = time.perf_counter() - t0
+        ratios = []
+        for i in sample:
+            k = shapes[i]["k"]
+            An = A64[i].cpu().numpy()
+            g = [t[i].cpu().numpy() for t in outs]
+            e_g = oracle.rel_fro_error(An, *g, k)
+            e_o = oracle.rel_fro_error(An, refs[i]["Q"], refs[i]["L"], refs[i]["P"], k)
+            ratios.append(e_g / e_o)
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": "%d matrices of the batch (every %d-th), full FP64 oracle"
+                                % (len(sample), max(1, count // 6))}
+        line["parity"] = {"error_ratio_vs_oracle": {"max": float(np.max(ratios)), "median": float(np.median(ratios))},
+                          "tol_ratio": 1.1, "matrices": len(sample)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,6 +414,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp64_8000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -217,6 +422,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, w, world, rank)
+    if w.get("batched"):
+        return run_batched(args, w, world, rank, local)
 
     import numpy as np
     import torch

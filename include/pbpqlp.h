@@ -203,6 +203,24 @@ int pbpqlp_factor_batched(pbpqlp_batch_t batch, const void* const* A, const int6
 int pbpqlp_batch_sync_status(pbpqlp_batch_t batch, uint32_t* flags_host);
 
 /*
+ * Autotuner of the batched launch geometry: times the batched factorization
+ * on the caller's data for each candidate (Gram row chunk 256/512/1024/2048,
+ * triangular-solve rows per unit 64/256, and in the TF32 modes the order of
+ * the grouped product units) and keeps the fastest in the plan.  Runs the
+ * factorization 2 x (number of candidates) times; outputs hold the last run.
+ * table_path (optional): appends one JSON line with the batch signature and
+ * the chosen values.  *best_ms (optional) gets the best time per call.
+ */
+int pbpqlp_batch_autotune(pbpqlp_batch_t batch, const void* const* A, const int64_t* lda, int a_dtype,
+                          void* workspace, size_t ws_bytes, double* const* Qa, double* const* L,
+                          double* const* Qb, const char* table_path, double* best_ms);
+
+/* Event timing of the batched tensor-core product launches (TF32 modes),
+ * as pbpqlp_set_timing / pbpqlp_read_timing. */
+int pbpqlp_batch_set_timing(pbpqlp_batch_t batch, int enable);
+int pbpqlp_batch_read_timing(pbpqlp_batch_t batch, double* pass_ms_total, int64_t* pass_launches);
+
+/*
  * pbpqlp_factor_static — the paper has no counterpart; this is a deployment
  * variant of pbpqlp_factor for callers that cannot allocate device memory
  * (code whose host framework owns every device allocation, such as an

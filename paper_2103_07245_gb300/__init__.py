@@ -96,6 +96,13 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_factor_batched.restype = ci
     L.pbpqlp_batch_sync_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     L.pbpqlp_batch_sync_status.restype = ci
+    L.pbpqlp_batch_autotune.argtypes = [vp, pvp, ctypes.POINTER(i64), ci, vp, sz, pvp, pvp, pvp, ctypes.c_char_p,
+                                        ctypes.POINTER(ctypes.c_double)]
+    L.pbpqlp_batch_autotune.restype = ci
+    L.pbpqlp_batch_set_timing.argtypes = [vp, ci]
+    L.pbpqlp_batch_set_timing.restype = ci
+    L.pbpqlp_batch_read_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.pbpqlp_batch_read_timing.restype = ci
     L.pbpqlp_factor_static.argtypes = [vp, vp, i64, ci, vp, vp, vp, vp]
     L.pbpqlp_factor_static.restype = ci
     L.pbpqlp_set_timing.argtypes = [vp, ci]
@@ -245,6 +252,28 @@ def pbpqlp_factor_batched(batch, A, lda, a_dtype, workspace, ws_bytes, Qa, L, Qb
                                         _ptr_array(Qa), _ptr_array(L), _ptr_array(Qb)), "pbpqlp_factor_batched")
 
 
+def pbpqlp_batch_autotune(batch, A, lda, a_dtype, workspace, ws_bytes, Qa, L, Qb, table_path=None):
+    cnt = len(A)
+    la = (ctypes.c_int64 * cnt)(*[int(x) for x in lda])
+    best = ctypes.c_double(0.0)
+    _check(load().pbpqlp_batch_autotune(batch, _ptr_array(A), la, int(a_dtype), _ptr(workspace), int(ws_bytes),
+                                        _ptr_array(Qa), _ptr_array(L), _ptr_array(Qb),
+                                        table_path.encode() if table_path else None, ctypes.byref(best)),
+           "pbpqlp_batch_autotune")
+    return best.value
+
+
+def pbpqlp_batch_set_timing(batch, enable):
+    _check(load().pbpqlp_batch_set_timing(batch, 1 if enable else 0), "pbpqlp_batch_set_timing")
+
+
+def pbpqlp_batch_read_timing(batch):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().pbpqlp_batch_read_timing(batch, ctypes.byref(ms), ctypes.byref(n)), "pbpqlp_batch_read_timing")
+    return ms.value, int(n.value)
+
+
 def pbpqlp_batch_sync_status(batch, count):
     """Returns (worst status, per-matrix flag list)."""
     f = (ctypes.c_uint32 * count)()
@@ -349,6 +378,13 @@ class Batch:
 
     def sync_status(self):
         return pbpqlp_batch_sync_status(self.handle, len(self.m))
+
+    def autotune(self, As, out, table_path=None):
+        import torch
+        a_dtype = PBPQLP_F32 if As[0].dtype == torch.float32 else PBPQLP_F64
+        Qa, L, Qb = out
+        return pbpqlp_batch_autotune(self.handle, As, [a.stride(0) for a in As], a_dtype, self.workspace,
+                                     self.ws_bytes, Qa, L, Qb, table_path)
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -52,6 +52,11 @@ struct pbpqlp_batch_s {
     int lmax = 0;
     int64_t ldp = 0;
     int gram_chunk = 512;           // rows per Gram partial (tuned by pbpqlp_batch_autotune)
+    int trsm_rows = 64;             // rows per triangular-solve unit (tuned)
+    int tc_sorted = 1;              // grouped products: longest contraction first (tuned)
+    bool timing = false;            // event pairs around each grouped product kernel
+    std::vector<cudaEvent_t> ev;    // 2 per timed launch
+    int ev_used = 0;
     int nprod = 0;                  // TF32 modes: 1 (TF32) or 3 (split TF32); 0 in FP64 mode
     int a_f32 = 0;                  // element type of the A pointers the lists were built for
     std::vector<MatWs> mw;
@@ -68,6 +73,7 @@ struct pbpqlp_batch_s {
     ~pbpqlp_batch_s() {
         if (exec) cudaGraphExecDestroy(exec);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
 };
 
@@ -212,7 +218,8 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 }
             }
             // longest contraction first, then dealt round-robin to the persistent CTAs
-            std::stable_sort(tu.begin(), tu.end(), [](const TcUnit& a, const TcUnit& b) { return a.KI > b.KI; });
+            if (B->tc_sorted)
+                std::stable_sort(tu.begin(), tu.end(), [](const TcUnit& a, const TcUnit& b) { return a.KI > b.KI; });
             lb.add(L_PSPLIT, pu);
             lb.add(L_TC, tu);
             return;
@@ -266,10 +273,10 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 m.l = l; m.pass = pass; m.rows = rows; m.G = P64(pt, B->mw[i].G); m.Rp = P64(pt, B->mw[i].Rp);
                 m.ctl = c; m.status = status + i;
                 cu.push_back(m);
-                for (int64_t r0 = 0; r0 < rows; r0 += 64) {
+                for (int64_t r0 = 0; r0 < rows; r0 += B->trsm_rows) {
                     TrsmUnit t{};
                     t.X = src; t.Y = dst; t.Rp = P64(pt, B->mw[i].Rp); t.ldx = ldp; t.ldy = ldp; t.r0 = r0;
-                    t.r1 = std::min<int64_t>(rows, r0 + 64); t.l = l; t.cond = cond;
+                    t.r1 = std::min<int64_t>(rows, r0 + B->trsm_rows); t.l = l; t.cond = cond;
                     tu.push_back(t);
                 }
             }
@@ -359,8 +366,18 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
 
 int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
     char* lists = ws + B->off_lists;
+    int evi = 0;
     int* ctl = (int*)(ws + B->off_ctl);
     PBQ_TRY(cudaMemsetAsync(ws + B->off_status, 0, sizeof(uint32_t) * (size_t)B->count, s));
+    if (B->timing) {   // the FP64 mode times its product launches (L_GEMM with the A operand) instead
+        int need = 0;
+        for (const Launch& L : B->seq) need += 2 * (L.kind == L_TC);
+        while ((int)B->ev.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return PBPQLP_ECUDA;
+            B->ev.push_back(e);
+        }
+    }
     for (const Launch& L : B->seq) {
         const void* u = lists + L.off;
         switch (L.kind) {
@@ -373,10 +390,18 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
             case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, s)); break;
             case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, s)); break;
             case L_PSPLIT: PBQ_TRY(launch_split_panel_tf32_list((const PanelUnit*)u, L.n, s)); break;
-            case L_TC:
+            case L_TC: {
+                const bool t = B->timing && evi + 1 < (int)B->ev.size();
+                // under capture an event record must be an external node to be recorded at replay
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                PBQ_TRY(cudaStreamIsCapturing(s, &cs));
+                const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+                if (t) PBQ_TRY(cudaEventRecordWithFlags(B->ev[evi], s, flags));
                 PBQ_TRY(launch_tc_list(B->nprod, lists + B->maps_off, (const TcUnit*)u, L.n, B->num_sms,
                                        (uint32_t*)(ws + B->off_status), s));
+                if (t) { PBQ_TRY(cudaEventRecordWithFlags(B->ev[evi + 1], s, flags)); evi += 2; }
                 break;
+            }
             default: return PBPQLP_EINVAL;
         }
     }
@@ -395,12 +420,13 @@ void layout(pbpqlp_batch_s* B) {
         const int64_t m = B->m[i], n = B->n[i], l = B->l[i];
         w.S_m = (int)((m + B->gram_chunk - 1) / B->gram_chunk);
         w.S_n = (int)((n + B->gram_chunk - 1) / B->gram_chunk);
+        const int smax = (int)((std::max(m, n) + 255) / 256);   // sized for the smallest tuned chunk
         w.Xm = take(8 * (size_t)(m * ldp));
         w.Ym = take(8 * (size_t)(m * ldp));
         w.Dm = take(8 * (size_t)(m * ldp));
         w.Xn = take(8 * (size_t)(n * ldp));
         w.Yn = take(8 * (size_t)(n * ldp));
-        w.part = take(8 * (size_t)(std::max(w.S_m, w.S_n) * l * ldp));
+        w.part = take(8 * (size_t)(smax * l * ldp));
         w.G = take(8 * (size_t)(l * l));
         w.Rp = take(8 * (size_t)(packed_tri((int)l) + l));
         w.R = take(8 * (size_t)(l * l));
@@ -475,6 +501,10 @@ int run(pbpqlp_batch_s* B, const Ptrs& pt, size_t ws_bytes) {
             }
         }
     }
+    if (B->timing) {
+        B->ev_used = 0;
+        for (const Launch& L : B->seq) B->ev_used += 2 * (L.kind == L_TC);
+    }
     if (B->exec) {
         PBQ_TRY(cudaGraphLaunch(B->exec, B->stream));
         int64_t kernels = 0;
@@ -543,6 +573,92 @@ int pbpqlp_factor_batched(pbpqlp_batch_t B, const void* const* A, const int64_t*
     if (B->a_f32 != (a_dtype == PBPQLP_F32)) { B->a_f32 = a_dtype == PBPQLP_F32; B->key.clear(); }
     Ptrs pt{(char*)workspace, A, lda, Qa, L, Qb};
     return run(B, pt, ws_bytes);
+}
+
+int pbpqlp_batch_set_timing(pbpqlp_batch_t B, int enable) {
+    if (!B) return PBPQLP_EINVAL;
+    if (B->timing != (enable != 0)) {
+        B->timing = enable != 0;
+        B->key.clear();   // re-record the graph with or without the event nodes
+    }
+    return PBPQLP_OK;
+}
+
+int pbpqlp_batch_read_timing(pbpqlp_batch_t B, double* ms_total, int64_t* launches) {
+    if (!B || !ms_total || !launches) return PBPQLP_EINVAL;
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PBPQLP_ECUDA;
+    double t = 0.0;
+    for (int i = 0; i + 1 < B->ev_used && i + 1 < (int)B->ev.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, B->ev[i], B->ev[i + 1]) != cudaSuccess) return PBPQLP_ECUDA;
+        t += ms;
+    }
+    *ms_total = t;
+    *launches = B->ev_used / 2;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_batch_autotune(pbpqlp_batch_t B, const void* const* A, const int64_t* lda, int a_dtype, void* workspace,
+                          size_t ws_bytes, double* const* Qa, double* const* L, double* const* Qb, const char* table_path,
+                          double* best_ms) {
+    if (!B) return PBPQLP_EINVAL;
+    const int chunks[] = {256, 512, 1024, 2048};
+    const int trows[] = {64, 256};
+    const int sorts[] = {1, 0};
+    double best = 1e300;
+    int bc = B->gram_chunk, bt = B->trsm_rows, bs = B->tc_sorted;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PBPQLP_ECUDA;
+    int rc = PBPQLP_OK;
+    for (int gc : chunks)
+        for (int tr : trows)
+            for (int so : sorts) {
+                if (!B->nprod && so == 0) continue;   // unit order only matters for the grouped products
+                B->gram_chunk = gc; B->trsm_rows = tr; B->tc_sorted = so;
+                for (int i = 0; i < B->count; ++i) {
+                    B->mw[i].S_m = (int)((B->m[i] + gc - 1) / gc);
+                    B->mw[i].S_n = (int)((B->n[i] + gc - 1) / gc);
+                }
+                B->key.clear();
+                // first call records the graph, the second is timed
+                if ((rc = pbpqlp_factor_batched(B, A, lda, a_dtype, workspace, ws_bytes, Qa, L, Qb))) goto done;
+                if (cudaEventRecord(e0, B->stream) != cudaSuccess) { rc = PBPQLP_ECUDA; goto done; }
+                if ((rc = pbpqlp_factor_batched(B, A, lda, a_dtype, workspace, ws_bytes, Qa, L, Qb))) goto done;
+                if (cudaEventRecord(e1, B->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = PBPQLP_ECUDA;
+                    goto done;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bc = gc; bt = tr; bs = so; }
+            }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->gram_chunk = bc; B->trsm_rows = bt; B->tc_sorted = bs;
+    for (int i = 0; i < B->count; ++i) {
+        B->mw[i].S_m = (int)((B->m[i] + bc - 1) / bc);
+        B->mw[i].S_n = (int)((B->n[i] + bc - 1) / bc);
+    }
+    B->key.clear();
+    if (rc) return rc;
+    if (best_ms) *best_ms = best;
+    if (table_path && table_path[0]) {
+        // one JSON line per tuning: the batch signature and the chosen tiles
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+        mix((uint64_t)B->count); mix((uint64_t)B->p); mix((uint64_t)B->q); mix((uint64_t)B->mode);
+        for (int i = 0; i < B->count; ++i) { mix((uint64_t)B->m[i]); mix((uint64_t)B->n[i]); mix((uint64_t)B->k[i]); }
+        FILE* f = std::fopen(table_path, "a");
+        if (f) {
+            std::fprintf(f,
+                         "{\"signature\": \"%016llx\", \"count\": %d, \"mode\": %d, \"gram_chunk\": %d, "
+                         "\"trsm_rows\": %d, \"tc_sorted\": %d, \"ms\": %.4f}\n",
+                         (unsigned long long)h, B->count, B->mode, bc, bt, bs, best);
+            std::fclose(f);
+        }
+    }
+    return PBPQLP_OK;
 }
 
 int pbpqlp_batch_sync_status(pbpqlp_batch_t B, uint32_t* flags_host) {

@@ -136,3 +136,39 @@ def torch_xyt_plus_noise(seed: int, m: int, n: int, r: int, eps: float, device="
         torch.backends.cuda.matmul.allow_tf32 = old
     A.add_(torch.randn(m, n, generator=gen, device=device, dtype=torch.float32), alpha=eps)
     return A
+
+
+def _preload_torch_linalg():
+    """Load torch's lazily opened CUDA linear-algebra library by absolute path
+    (some profilers' environments break its lookup by name)."""
+    import ctypes
+    import os
+    import torch
+    lib = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(lib):
+        try:
+            ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
+def torch_svd_matrix_device(seed: int, m: int, n: int, sigma, device="cuda"):
+    """U diag(sigma) V^T with Haar U (m x r), V (n x r) drawn and orthonormalised
+    on the device (torch QR with the sign fix); FP64."""
+    import torch
+    _preload_torch_linalg()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    s = torch.as_tensor(np.asarray(sigma), device=device, dtype=torch.float64)
+    r = s.numel()
+
+    def haar(rows):
+        g = torch.randn(rows, r, generator=gen, device=device, dtype=torch.float64)
+        q, rr = torch.linalg.qr(g)
+        sg = torch.sign(torch.diagonal(rr))
+        sg[sg == 0] = 1.0
+        return q * sg
+
+    U = haar(m)
+    V = haar(n)
+    return ((U * s) @ V.T).contiguous()

@@ -132,3 +132,26 @@ def test_batched_tf32_single_term_runs(pq):
         g = [Qa[i].cpu().numpy(), L[i].cpu().numpy(), Qb[i].cpu().numpy()]
         e_gpu, e_orc = _errors(A64, g, ref, s["k"])
         assert np.isfinite(e_gpu) and e_gpu <= 2.0 * e_orc, (i, e_gpu, e_orc)
+
+
+def test_batched_autotune_keeps_results(pq, tmp_path):
+    import json
+    import torch
+    shapes, mats = _batch(7, 5)
+    p, q, seed = 8, 1, 21
+    B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], p, q, seed)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    outs = B.outputs()
+    table = str(tmp_path / "tune.jsonl")
+    best = B.autotune(As, outs, table_path=table)
+    assert best > 0
+    rec = json.loads(open(table).read().strip().splitlines()[-1])
+    assert rec["gram_chunk"] in (256, 512, 1024, 2048) and rec["trsm_rows"] in (64, 256)
+    B.factor(As, out=outs)
+    rc, _ = B.sync_status()
+    assert rc == pq.PBPQLP_OK
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        ref = oracle.pbpqlp(A, s["k"] + p, q, seed=seed + i)
+        g = [outs[0][i].cpu().numpy(), outs[1][i].cpu().numpy(), outs[2][i].cpu().numpy()]
+        d = np.linalg.norm(oracle.reconstruct(*g, s["k"]) - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], s["k"]))
+        assert d / np.linalg.norm(A) <= TOL
