@@ -221,6 +221,51 @@ int pbpqlp_batch_set_timing(pbpqlp_batch_t batch, int enable);
 int pbpqlp_batch_read_timing(pbpqlp_batch_t batch, double* pass_ms_total, int64_t* pass_launches);
 
 /*
+ * Learned (q, p) proposer.  Not in the paper: a small network proposes the
+ * power-iteration count q in {0..4} and the oversampling p in {5, 10, 20}
+ * from cheap features of a first q = 0, l = k + 20 sketch; the caller keeps
+ * the plain fixed-q method (q = 2, p = 10) as the fallback, judged by the
+ * a-posteriori estimator of pbpqlp_error (PBPQLP_ERR_PROBES).
+ *
+ * Features (pbpqlp_features): from the L-values d_i = |L_ii| of that sketch
+ * (the paper's rank-revealing diagonal, Section IV-C) and m, n, k, 32 floats
+ * per matrix: log m / 8, log n / 8, log k / 4, 10 k / min(m, n);
+ * log10(d_j / d_1) / 4 at j = round(t k), t = 0.1 .. 1.0 (10 values) and at
+ * j = k + 1, 2, 5, 10, 15, 20; log10 of d_k/d_{k+1}, d_k/d_{k+5},
+ * d_k/d_{k+20}, d_{k/2}/d_k, d_{k+10}/d_{k+20}; log10 of the sketch tail
+ * ratio sqrt(sum_{i>k} d_i^2 / sum_{i<=k} d_i^2) / 4; least-squares slopes
+ * of log10 d over [k/2, k] and [k, l] (times k); log10(d_l / d_1) / 4;
+ * 10 l / min(m, n); m / n - 1; the constant 1.
+ *   L, l, k, m, n: host arrays of count (L[i] a device pointer to the l_i x l_i
+ *   factor); features: device, count x 32 FP32; workspace: device,
+ *   >= pbpqlp_features_workspace_bytes(count).
+ *
+ * Network (pbpqlp_mlp_*): 32 -> 128 -> 128 -> 8 with GELU (erf form); the
+ * outputs are 5 logits for q and 3 for p.  Parameters are one FP32 vector of
+ * pbpqlp_mlp_param_count() floats: W1 (128 x 32), b1, W2 (128 x 128), b2,
+ * W3 (8 x 128), b3.  Every linear layer rounds both operands to BF16 and
+ * accumulates in FP32 on the tensor cores (forward and backward); the loss is
+ * the mean over the batch of the two heads' cross-entropies.  pbpqlp_mlp_adamw
+ * is AdamW on the FP32 master parameters (bias-corrected, decoupled decay).
+ * pbpqlp_propose writes q and the p index (0, 1, 2 -> p = 5, 10, 20) per row.
+ * All pointers are device pointers; workspaces >= pbpqlp_mlp_workspace_bytes(batch).
+ */
+size_t pbpqlp_features_workspace_bytes(int count);
+int pbpqlp_features(int count, const double* const* L, const int* l, const int* k, const int64_t* m,
+                    const int64_t* n, float* features, void* workspace, size_t ws_bytes, void* stream);
+int pbpqlp_mlp_param_count(void);
+size_t pbpqlp_mlp_workspace_bytes(int batch);
+int pbpqlp_mlp_init(float* params, uint64_t seed, void* stream);
+int pbpqlp_mlp_forward(const float* params, const float* X, int batch, float* logits, void* workspace,
+                       size_t ws_bytes, void* stream);
+int pbpqlp_mlp_loss_grad(const float* params, const float* X, const int* yq, const int* yp, int batch,
+                         float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream);
+int pbpqlp_mlp_adamw(float* params, float* m, float* v, const float* grad, int step, float lr, float beta1,
+                     float beta2, float eps, float weight_decay, void* stream);
+int pbpqlp_propose(const float* features, int count, const float* params, int* q_out, int* p_index_out,
+                   void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * pbpqlp_factor_static — the paper has no counterpart; this is a deployment
  * variant of pbpqlp_factor for callers that cannot allocate device memory
  * (code whose host framework owns every device allocation, such as an

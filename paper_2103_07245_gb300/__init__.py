@@ -103,6 +103,27 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_batch_set_timing.restype = ci
     L.pbpqlp_batch_read_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.pbpqlp_batch_read_timing.restype = ci
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.pbpqlp_features_workspace_bytes.argtypes = [ci]
+    L.pbpqlp_features_workspace_bytes.restype = sz
+    L.pbpqlp_features.argtypes = [ci, pvp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64), vp, vp, sz, vp]
+    L.pbpqlp_features.restype = ci
+    L.pbpqlp_mlp_param_count.argtypes = []
+    L.pbpqlp_mlp_param_count.restype = ci
+    L.pbpqlp_mlp_workspace_bytes.argtypes = [ci]
+    L.pbpqlp_mlp_workspace_bytes.restype = sz
+    L.pbpqlp_mlp_init.argtypes = [vp, u64, vp]
+    L.pbpqlp_mlp_init.restype = ci
+    L.pbpqlp_mlp_forward.argtypes = [vp, vp, ci, vp, vp, sz, vp]
+    L.pbpqlp_mlp_forward.restype = ci
+    L.pbpqlp_mlp_loss_grad.argtypes = [vp, vp, vp, vp, ci, vp, vp, vp, sz, vp]
+    L.pbpqlp_mlp_loss_grad.restype = ci
+    L.pbpqlp_mlp_adamw.argtypes = [vp, vp, vp, vp, ci, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, vp]
+    L.pbpqlp_mlp_adamw.restype = ci
+    L.pbpqlp_propose.argtypes = [vp, ci, vp, vp, vp, vp, sz, vp]
+    L.pbpqlp_propose.restype = ci
     L.pbpqlp_factor_static.argtypes = [vp, vp, i64, ci, vp, vp, vp, vp]
     L.pbpqlp_factor_static.restype = ci
     L.pbpqlp_set_timing.argtypes = [vp, ci]
@@ -200,6 +221,52 @@ def pbpqlp_factor_static(plan, A, lda, a_dtype, omega, Qa, L, Qb):
     """pbpqlp_factor without a workspace argument (the library's fixed device scratch)."""
     _check(load().pbpqlp_factor_static(plan, _ptr(A), int(lda), int(a_dtype), _ptr(omega), _ptr(Qa), _ptr(L),
                                        _ptr(Qb)), "pbpqlp_factor_static")
+
+
+def pbpqlp_features_workspace_bytes(count) -> int:
+    return int(load().pbpqlp_features_workspace_bytes(int(count)))
+
+
+def pbpqlp_features(L, l, k, m, n, features, workspace, ws_bytes, stream=None):
+    cnt = len(L)
+    la = (ctypes.c_int * cnt)(*[int(x) for x in l])
+    ka = (ctypes.c_int * cnt)(*[int(x) for x in k])
+    ma = (ctypes.c_int64 * cnt)(*[int(x) for x in m])
+    na = (ctypes.c_int64 * cnt)(*[int(x) for x in n])
+    _check(load().pbpqlp_features(cnt, _ptr_array(L), la, ka, ma, na, _ptr(features), _ptr(workspace), int(ws_bytes),
+                                  _stream(stream)), "pbpqlp_features")
+
+
+def pbpqlp_mlp_param_count() -> int:
+    return int(load().pbpqlp_mlp_param_count())
+
+
+def pbpqlp_mlp_workspace_bytes(batch) -> int:
+    return int(load().pbpqlp_mlp_workspace_bytes(int(batch)))
+
+
+def pbpqlp_mlp_init(params, seed, stream=None):
+    _check(load().pbpqlp_mlp_init(_ptr(params), int(seed) & 0xFFFFFFFFFFFFFFFF, _stream(stream)), "pbpqlp_mlp_init")
+
+
+def pbpqlp_mlp_forward(params, X, batch, logits, workspace, ws_bytes, stream=None):
+    _check(load().pbpqlp_mlp_forward(_ptr(params), _ptr(X), int(batch), _ptr(logits), _ptr(workspace), int(ws_bytes),
+                                     _stream(stream)), "pbpqlp_mlp_forward")
+
+
+def pbpqlp_mlp_loss_grad(params, X, yq, yp, batch, grad, loss, workspace, ws_bytes, stream=None):
+    _check(load().pbpqlp_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(yq), _ptr(yp), int(batch), _ptr(grad), _ptr(loss),
+                                       _ptr(workspace), int(ws_bytes), _stream(stream)), "pbpqlp_mlp_loss_grad")
+
+
+def pbpqlp_mlp_adamw(params, m, v, grad, step, lr, beta1, beta2, eps, weight_decay, stream=None):
+    _check(load().pbpqlp_mlp_adamw(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr), float(beta1),
+                                   float(beta2), float(eps), float(weight_decay), _stream(stream)), "pbpqlp_mlp_adamw")
+
+
+def pbpqlp_propose(features, count, params, q_out, p_index_out, workspace, ws_bytes, stream=None):
+    _check(load().pbpqlp_propose(_ptr(features), int(count), _ptr(params), _ptr(q_out), _ptr(p_index_out),
+                                 _ptr(workspace), int(ws_bytes), _stream(stream)), "pbpqlp_propose")
 
 
 def pbpqlp_set_timing(plan, enable):

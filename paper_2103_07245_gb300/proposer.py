@@ -1,0 +1,249 @@
+"""Learned (q, p) proposer for PbP-QLP: data, training and the guarded proposal.
+
+Every numerical step runs in the library's kernels (factorizations, feature
+extraction, MLP forward / backward / AdamW, the a-posteriori estimator); this
+module only moves torch tensors between those calls.
+
+- Labels come from the method itself: each training matrix is factored for
+  every q in {0..4} and p in {5, 10, 20}; the label is the cheapest pair
+  (cost (2q + 2)(k + p), i.e. passes over A times panel width) whose
+  relative Frobenius error is <= 1.5 x the optimal tail ||sigma_{k+1:}|| / ||A||_F.
+  The error is read through the identity ||A - A_k||^2 = ||A||^2 - ||L_k||^2
+  of Eq. 8 (FP64 factors).
+- Features: pbpqlp_features on the L-values of the (q = 0, p = 20) sketch.
+- Guarded proposal: the pair the network proposes is run, its error is
+  estimated with Gaussian probes (pbpqlp_error, PBPQLP_ERR_PROBES) and, when
+  the estimate misses the caller's tolerance, the plain method with fixed
+  (q = 2, p = 10) is run instead.
+"""
+import math
+import os
+
+import numpy as np
+
+import paper_2103_07245_gb300 as pq
+
+Q_CHOICES = (0, 1, 2, 3, 4)
+P_CHOICES = (5, 10, 20)
+FIXED = (2, 10)
+
+
+class Proposer:
+    """The MLP's parameters and AdamW state on the device."""
+
+    def __init__(self, seed=0, device="cuda"):
+        import torch
+        self.device = device
+        self.n = pq.pbpqlp_mlp_param_count()
+        self.params = torch.empty(self.n, dtype=torch.float32, device=device)
+        pq.pbpqlp_mlp_init(self.params, seed)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.t = 0
+        self._ws = {}
+
+    def _workspace(self, batch):
+        import torch
+        if batch not in self._ws:
+            nb = pq.pbpqlp_mlp_workspace_bytes(batch)
+            self._ws[batch] = (torch.empty(nb, dtype=torch.uint8, device=self.device), nb)
+        return self._ws[batch]
+
+    def loss_grad(self, X, yq, yp):
+        import torch
+        ws, nb = self._workspace(X.shape[0])
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        pq.pbpqlp_mlp_loss_grad(self.params, X, yq, yp, X.shape[0], self.grad, loss, ws, nb)
+        return loss
+
+    def step(self, X, yq, yp, lr=2e-3, weight_decay=1e-4):
+        loss = self.loss_grad(X, yq, yp)
+        self.t += 1
+        pq.pbpqlp_mlp_adamw(self.params, self.m, self.v, self.grad, self.t, lr, 0.9, 0.999, 1e-8, weight_decay)
+        return loss
+
+    def logits(self, X):
+        import torch
+        ws, nb = self._workspace(X.shape[0])
+        out = torch.empty(X.shape[0], 8, dtype=torch.float32, device=self.device)
+        pq.pbpqlp_mlp_forward(self.params, X, X.shape[0], out, ws, nb)
+        return out
+
+    def propose(self, X):
+        """(q, p) per row of the feature matrix X (count x 32, FP32 device)."""
+        import torch
+        ws, nb = self._workspace(X.shape[0])
+        qi = torch.empty(X.shape[0], dtype=torch.int32, device=self.device)
+        pi = torch.empty_like(qi)
+        pq.pbpqlp_propose(X, X.shape[0], self.params, qi, pi, ws, nb)
+        qs = [Q_CHOICES[int(x)] for x in qi.cpu()]
+        ps = [P_CHOICES[int(x)] for x in pi.cpu()]
+        return qs, ps
+
+    def save(self, path):
+        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(), t=self.t)
+
+    def load(self, path):
+        import torch
+        d = np.load(path)
+        self.params.copy_(torch.from_numpy(d["params"]))
+        self.m.copy_(torch.from_numpy(d["m"]))
+        self.v.copy_(torch.from_numpy(d["v"]))
+        self.t = int(d["t"])
+
+
+def features(Ls, ls, ks, ms, ns, device="cuda"):
+    import torch
+    cnt = len(Ls)
+    F = torch.empty(cnt, 32, dtype=torch.float32, device=device)
+    nb = pq.pbpqlp_features_workspace_bytes(cnt)
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    pq.pbpqlp_features(Ls, ls, ks, ms, ns, F, ws, nb)
+    return F
+
+
+def _batched_errors(As, ks, p, q, seed, normA2):
+    """Rank-k relative errors of the batched FP64 factorization with (p, q)."""
+    import torch
+    ms = [a.shape[0] for a in As]
+    ns = [a.shape[1] for a in As]
+    old = os.environ.get("PBPQLP_BATCH_NO_GRAPH")
+    os.environ["PBPQLP_BATCH_NO_GRAPH"] = "1"       # one-shot batches: launch eagerly
+    try:
+        B = pq.Batch(ms, ns, ks, p, q, seed)
+    finally:
+        if old is None:
+            del os.environ["PBPQLP_BATCH_NO_GRAPH"]
+        else:
+            os.environ["PBPQLP_BATCH_NO_GRAPH"] = old
+    Qa, L, Qb = B.factor(As)
+    rc, _ = B.sync_status()
+    errs = []
+    for i, k in enumerate(ks):
+        lk2 = float(torch.sum(L[i][:k, :k] ** 2))
+        errs.append(math.sqrt(max(normA2[i] - lk2, 0.0) / normA2[i]))
+    return errs, L, rc
+
+
+def label(As, ks, tails, seed=0):
+    """Features of the (0, 20) sketch, the error table err[i][q][p] and the labels."""
+    import torch
+    normA2 = [float(torch.sum(a * a)) for a in As]
+    cnt = len(As)
+    err = np.zeros((cnt, len(Q_CHOICES), len(P_CHOICES)))
+    Lsk = None
+    for qi, q in enumerate(Q_CHOICES):
+        for pi, p in enumerate(P_CHOICES):
+            e, L, rc = _batched_errors(As, ks, p, q, seed, normA2)
+            err[:, qi, pi] = e
+            if q == 0 and p == 20:
+                Lsk = L
+    F = features(Lsk, [k + 20 for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
+    yq, yp = [], []
+    for i, k in enumerate(ks):
+        best, bc = None, None
+        for qi, q in enumerate(Q_CHOICES):
+            for pi, p in enumerate(P_CHOICES):
+                if err[i, qi, pi] <= 1.5 * tails[i]:
+                    c = (2 * q + 2) * (k + p)
+                    if bc is None or c < bc:
+                        best, bc = (qi, pi), c
+        if best is None:
+            best = (len(Q_CHOICES) - 1, len(P_CHOICES) - 1)
+        yq.append(best[0])
+        yp.append(best[1])
+    return F, err, np.array(yq), np.array(yp)
+
+
+def random_family(rng, m, n):
+    """Spectrum of a training / evaluation matrix: polynomial, exponential or low rank plus noise."""
+    r = min(m, n)
+    i = np.arange(1, r + 1, dtype=np.float64)
+    fam = rng.integers(0, 3)
+    if fam == 0:
+        return i ** (-rng.uniform(0.5, 3.0))
+    if fam == 1:
+        return np.exp(-i * rng.uniform(1 / 80, 1 / 10))
+    rank = int(rng.integers(8, 96))
+    mu = 10 ** rng.uniform(-4, -1)
+    s = np.full(r, mu)
+    s[:rank] = np.linspace(1.0, 0.5, rank)
+    return s
+
+
+def make_matrices(seed, count, m_range=(512, 2048), k_range=(8, 64), fixed=None, eval_mix=False, device="cuda"):
+    """Seeded matrices, their k and their optimal relative tails ||sigma_{k+1:}|| / ||sigma||."""
+    import synth
+    rng = np.random.default_rng(seed)
+    As, ks, tails = [], [], []
+    for j in range(count):
+        if fixed:
+            m, n, k = fixed
+        else:
+            m = int(rng.integers(m_range[0], m_range[1] + 1))
+            n = int(rng.integers(m_range[0], m_range[1] + 1))
+            k = int(rng.integers(k_range[0], k_range[1] + 1))
+        if eval_mix:
+            i = np.arange(1, min(m, n) + 1, dtype=np.float64)
+            sig = i ** (-rng.uniform(0.5, 3.0)) if rng.random() < 0.5 else np.exp(-i * rng.uniform(1 / 80, 1 / 10))
+        else:
+            sig = random_family(rng, m, n)
+        As.append(synth.torch_svd_matrix_device(int(rng.integers(1 << 30)), m, n, sig, device=device))
+        ks.append(k)
+        tails.append(float(np.linalg.norm(sig[k:]) / np.linalg.norm(sig)))
+    return As, ks, tails
+
+
+def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0):
+    """Minibatch AdamW on the labelled features; returns the loss history."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = F.shape[0]
+    yq_t = torch.as_tensor(yq, dtype=torch.int32, device=F.device)
+    yp_t = torch.as_tensor(yp, dtype=torch.int32, device=F.device)
+    hist = []
+    for ep in range(epochs):
+        perm = torch.as_tensor(rng.permutation(n), device=F.device)
+        tot = 0.0
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            loss = prop.step(F[idx].contiguous(), yq_t[idx].contiguous(), yp_t[idx].contiguous(), lr=lr)
+            tot += float(loss)
+        hist.append(tot / max(1, n // batch))
+    return hist
+
+
+def evaluate(prop, As, ks, tails, seed=0, nprobes=10):
+    """Fixed (2, 10) against the guarded proposal on the same matrices.
+
+    Passes over A: fixed = 2*2+2; proposal = 2 (the (0, 20) sketch) + 2q+2
+    (0 extra when the proposal is (0, 20) itself) + 6 when it falls back."""
+    import torch
+    normA2 = [float(torch.sum(a * a)) for a in As]
+    cnt = len(As)
+    e_fixed, _, _ = _batched_errors(As, ks, FIXED[1], FIXED[0], seed, normA2)
+    e0, L0, _ = _batched_errors(As, ks, 20, 0, seed, normA2)
+    F = features(L0, [k + 20 for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
+    qs, ps = prop.propose(F)
+    e_prop, passes, fallback = [], [], []
+    for i, (A, k) in enumerate(zip(As, ks)):
+        q, p = qs[i], ps[i]
+        plan = pq.Plan(A.shape[0], A.shape[1], k, p, q, seed=seed + i)
+        Qa, L, Qb = plan.factor(A)
+        est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
+        e = math.sqrt(max(normA2[i] - float(torch.sum(L[:k, :k] ** 2)), 0.0) / normA2[i])
+        n_pass = 2 + (0 if (q, p) == (0, 20) else 2 * q + 2)
+        fb = est > 1.5 * tails[i]
+        if fb:
+            e = e_fixed[i]
+            n_pass += 2 * FIXED[0] + 2
+        e_prop.append(e)
+        passes.append(n_pass)
+        fallback.append(fb)
+        del plan
+    ok_fixed = np.array(e_fixed) <= 1.5 * np.array(tails)
+    ok_prop = np.array(e_prop) <= 1.5 * np.array(tails)
+    return {"fixed_success": float(ok_fixed.mean()), "proposer_success": float(ok_prop.mean()),
+            "fixed_passes": float(2 * FIXED[0] + 2), "proposer_passes": float(np.mean(passes)),
+            "fallback_rate": float(np.mean(fallback)), "proposals": list(zip(qs, ps))}

@@ -279,3 +279,34 @@ def test_paper_low_rank_small_gap_q2(orc, golden):
         ratios.append(_sv(E)[0] / _sv(A)[g["d"]])
     paper_ratio = g["paper_error"] / g["paper_svd"]
     assert abs(np.median(ratios) - paper_ratio) < 0.05, (ratios, paper_ratio)
+
+
+# ------------------------------------------------------- proposer MLP (oracle)
+def test_oracle_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(mlp.PARAMS) * 0.2
+    X = rng.standard_normal((7, mlp.IN))
+    yq = rng.integers(0, mlp.NQ, 7)
+    yp = rng.integers(0, mlp.NP, 7)
+    loss, g = mlp.loss_grad(p, X, yq, yp)
+    assert mlp.PARAMS == 21768 and g.shape == (mlp.PARAMS,)
+    idx = rng.choice(mlp.PARAMS, 40, replace=False)
+    for i in idx:
+        h = 1e-6
+        pp = p.copy(); pp[i] += h
+        pm = p.copy(); pm[i] -= h
+        fd = (mlp.loss_grad(pp, X, yq, yp)[0] - mlp.loss_grad(pm, X, yq, yp)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_oracle_mlp_closed_forms():
+    from oracle import mlp
+    # GELU(0) = 0, GELU'(0) = 1/2, GELU(x) - GELU(-x) = x
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0 and abs(mlp.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+    x = np.linspace(-3, 3, 13)
+    assert np.allclose(mlp.gelu(x) - mlp.gelu(-x), x, atol=1e-14)
+    # zero weights: uniform heads, loss = log 5 + log 3 for any labels
+    p = np.zeros(mlp.PARAMS)
+    loss, _ = mlp.loss_grad(p, np.ones((4, mlp.IN)), [0, 1, 2, 3], [0, 1, 2, 0])
+    assert abs(loss - (np.log(5) + np.log(3))) < 1e-12
