@@ -108,3 +108,29 @@ def test_training_on_gpu_fits_a_rule(pq):
     acc_q = np.mean(np.array(qs) == yq)
     acc_p = np.mean(np.array([{5: 0, 10: 1, 20: 2}[x] for x in ps]) == yp)
     assert acc_q > 0.8 and acc_p > 0.85, (acc_q, acc_p)
+
+
+@pytest.mark.slow
+def test_trained_proposer_gains_over_fixed_q2_p10(pq):
+    """Train on labelled matrices the method generates, then compare the guarded
+    proposal with the plain fixed (q = 2, p = 10) method on held-out 2048 x 2048
+    matrices (k = 64, polynomial or exponential decay): at least the same share
+    meets 1.5 x the optimal tail, with fewer passes over A."""
+    import torch
+    from paper_2103_07245_gb300 import proposer as P
+    F_all, yq_all, yp_all = [], [], []
+    for chunk in range(4):
+        As, ks, tails = P.make_matrices(100 + chunk, 96, m_range=(512, 2048))
+        F, err, yq, yp = P.label(As, ks, tails, seed=chunk)
+        F_all.append(F)
+        yq_all.append(yq)
+        yp_all.append(yp)
+        del As
+    F = torch.cat(F_all)
+    prop = P.Proposer(seed=1)
+    hist = P.train(prop, F, np.concatenate(yq_all), np.concatenate(yp_all), epochs=200, batch=128, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    As, ks, tails = P.make_matrices(999, 32, fixed=(2048, 2048, 64), eval_mix=True)
+    res = P.evaluate(prop, As, ks, tails)
+    assert res["proposer_success"] >= res["fixed_success"], res
+    assert res["proposer_passes"] < res["fixed_passes"], res
