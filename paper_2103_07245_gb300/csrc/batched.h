@@ -56,8 +56,8 @@ struct TrsmUnit {
 cudaError_t launch_dgemm_list(int TN, bool transA, const GemmUnit* units, int nunits, cudaStream_t s);
 cudaError_t launch_reduce_list(const ReduceUnit* units, int nunits, cudaStream_t s);
 cudaError_t launch_cholesky_list(const MatUnit* units, int nunits, int lmax, cudaStream_t s);
-cudaError_t launch_trsm_list(const TrsmUnit* units, int nunits, int lmax, cudaStream_t s);
-cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, cudaStream_t s);
+cudaError_t launch_trsm_list(const TrsmUnit* units, int nunits, int lmax, cudaStream_t s, bool f32 = false);
+cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, int lmax, cudaStream_t s);
 cudaError_t launch_gaussian_list(const MatUnit* units, int nunits, cudaStream_t s);
 
 }  // namespace pbq

@@ -386,8 +386,8 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
             case L_GEMM: PBQ_TRY(launch_dgemm_list(L.TN, L.transA, (const GemmUnit*)u, L.n, s)); break;
             case L_REDUCE: PBQ_TRY(launch_reduce_list((const ReduceUnit*)u, L.n, s)); break;
             case L_CHOL: PBQ_TRY(launch_cholesky_list((const MatUnit*)u, L.n, B->lmax, s)); break;
-            case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, B->lmax, s)); break;
-            case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, s)); break;
+            case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, B->lmax, s, B->nprod > 0)); break;
+            case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, B->lmax, s)); break;
             case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, s)); break;
             case L_PSPLIT: PBQ_TRY(launch_split_panel_tf32_list((const PanelUnit*)u, L.n, s)); break;
             case L_TC: {

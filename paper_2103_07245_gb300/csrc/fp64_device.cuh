@@ -118,7 +118,7 @@ __device__ __forceinline__ void dev_cholesky(int l, int64_t rows, const double* 
     double* dg0 = sm + P;
     double* dinv = dg0 + l;
     __shared__ int s_fail;
-    __shared__ double s_inv, s_shift;
+    __shared__ double s_shift;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const double tau = 1e-12;
 
@@ -134,29 +134,47 @@ __device__ __forceinline__ void dev_cholesky(int l, int64_t rows, const double* 
                 S[pidx(l, a, b)] = G[(int64_t)a * l + b] + (a == b ? shift : 0.0);
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        for (int j = 0; j < l; ++j) {
-            if (tid == 0) {
-                const double d = S[pidx(l, j, j)];
-                const double thr = (attempt == 0) ? tau * dg0[j] : 0.0;
-                if (!isfinite(d)) s_fail = 2;
-                else if (!(d > thr)) s_fail = 1;
+        // right-looking, one barrier per column.  Warp 0 owns row j + 1 of the
+        // update of step j: right after updating it, its lane 0 takes the pivot
+        // (checks it, sqrt and one reciprocal) and the warp scales the row, so
+        // the next step starts from a finished row and all scalar FP64 work
+        // runs on one thread (GB300 issues 2 FP64 lanes per SM per clock).
+        auto pivot_row = [&](int i) {   // warp 0 only, row i already updated
+            double inv = 0.0;
+            int f = 0;
+            if (lane == 0) {
+                const double d = S[pidx(l, i, i)];
+                const double thr = (attempt == 0) ? tau * dg0[i] : 0.0;
+                f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
+                if (f) s_fail = f;
                 else {
                     const double r = sqrt(d);
-                    S[pidx(l, j, j)] = r;
-                    s_inv = 1.0 / r;
-                    dinv[j] = s_inv;
+                    S[pidx(l, i, i)] = r;
+                    inv = 1.0 / r;
+                    dinv[i] = inv;
                 }
             }
-            __syncthreads();
-            if (s_fail) break;
-            const double inv = s_inv;
+            f = __shfl_sync(0xffffffffu, f, 0);
+            inv = __shfl_sync(0xffffffffu, inv, 0);
+            if (!f) {
+                const int64_t ri = pidx(l, i, 0);
+                for (int c = i + 1 + lane; c < l; c += 32) S[ri + c] *= inv;
+            }
+            __syncwarp();
+        };
+        if (warp == 0) pivot_row(0);
+        __syncthreads();
+        for (int j = 0; j < l; ++j) {
+            if (s_fail) break;   // uniform: read after a barrier
             const int64_t rj = pidx(l, j, 0);
-            for (int c = j + 1 + tid; c < l; c += nth) S[rj + c] *= inv;
-            __syncthreads();
             for (int a = j + 1 + warp; a < l; a += nwarp) {
                 const double rja = S[rj + a];
                 const int64_t ra = pidx(l, a, 0);
                 for (int b = a + lane; b < l; b += 32) S[ra + b] -= rja * S[rj + b];
+                if (a == j + 1) {   // only warp 0 reaches this row
+                    __syncwarp();
+                    pivot_row(a);
+                }
             }
             __syncthreads();
         }
@@ -193,28 +211,29 @@ __device__ __forceinline__ void dev_cholesky(int l, int64_t rows, const double* 
 }
 
 // Y = X R^{-1} for rows r_first, r_first + r_step, ... < r_end, one warp per
-// row; sR holds R packed + 1/diag (already in shared memory).
-template <int U>
-__device__ __forceinline__ void dev_trsm_rows(int l, const double* __restrict__ sR, const double* __restrict__ X,
+// row; sR holds R packed + 1/diag (already in shared memory) in type T, the
+// arithmetic type (double, or float for the mixed modes).
+template <int U, typename T>
+__device__ __forceinline__ void dev_trsm_rows(int l, const T* __restrict__ sR, const double* __restrict__ X,
                                               int64_t ldx, double* __restrict__ Y, int64_t ldy, int64_t r_first,
                                               int64_t r_end, int64_t r_step) {
     const int64_t P = (int64_t)l * (l + 1) / 2;
-    const double* dinv = sR + P;
+    const T* dinv = sR + P;
     const int lane = threadIdx.x & 31;
     for (int64_t r = r_first; r < r_end; r += r_step) {
-        double x[U];
+        T x[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int c = lane + 32 * u;
-            x[u] = (c < l) ? X[r * ldx + c] : 0.0;
+            x[u] = (c < l) ? (T)X[r * ldx + c] : (T)0;
         }
 #pragma unroll
         for (int u0 = 0; u0 < U; ++u0) {
             for (int tt = 0; tt < 32; ++tt) {
                 const int t = 32 * u0 + tt;
                 if (t >= l) break;
-                const double y = __shfl_sync(0xffffffffu, x[u0], tt) * dinv[t];
-                if (lane == tt) x[u0] = y;
+                if (lane == tt) x[u0] *= dinv[t];   // only the owner lane forms y_t
+                const T y = __shfl_sync(0xffffffffu, x[u0], tt);
                 const int64_t rt = pidx(l, t, 0);
 #pragma unroll
                 for (int u = u0; u < U; ++u) {
@@ -226,19 +245,23 @@ __device__ __forceinline__ void dev_trsm_rows(int l, const double* __restrict__ 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int c = lane + 32 * u;
-            if (c < l) Y[r * ldy + c] = x[u];
+            if (c < l) Y[r * ldy + c] = (double)x[u];
         }
     }
 }
 
-// Householder QR of R^T by the whole CTA (see k_small_qr).
+// Householder QR of W = R^T (Eq. 7) by the whole CTA.  The factor is stored
+// transposed (Wt = R, so a column of W is a contiguous row of Wt); reflector j
+// (entries i >= j) is row j of V.  Rtil = upper(W) with signs fixed to
+// diag >= 0, L = Rtil^T, Ptil = H_0 ... H_{l-1} [I] with the matching column
+// signs.  Wt and V (2 l^2 doubles) live in sm when given, else in work; Ptil
+// is formed in the storage of Wt once L has been written.
 __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R, double* __restrict__ L,
-                                             double* __restrict__ Ptil, double* __restrict__ work) {
-    double* Wt = work;
+                                             double* __restrict__ Ptil, double* __restrict__ work, double* sm) {
+    double* Wt = sm ? sm : work;
     double* V = Wt + (int64_t)l * l;
-    double* Pt = V + (int64_t)l * l;   // Ptil transposed: row c = column c of Ptil
-    double* vv = Pt + (int64_t)l * l;
-    double* sg = vv + l;
+    double* Pt = Wt;
+    __shared__ double vv[kMaxEll], sg[kMaxEll], tvv[kMaxEll];   // tvv = 2 / vv (0 for no reflector)
     __shared__ double s_alpha;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const int64_t ll = (int64_t)l * l;
@@ -246,7 +269,6 @@ __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R
         const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
         Wt[e] = (i >= c) ? R[e] : 0.0;
         V[e] = 0.0;
-        Pt[e] = (i == c) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int j = 0; j < l; ++j) {
@@ -259,12 +281,13 @@ __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R
             if (lane == 0) {
                 const double x0 = wj[j];
                 const double nrm = sqrt(x0 * x0 + t);
-                if (nrm == 0.0) { vv[j] = 0.0; s_alpha = 0.0; }
+                if (nrm == 0.0) { vv[j] = 0.0; tvv[j] = 0.0; s_alpha = 0.0; }
                 else {
                     const double alpha = (x0 >= 0.0) ? -nrm : nrm;
                     const double v0 = x0 - alpha;
                     V[(int64_t)j * l + j] = v0;
                     vv[j] = v0 * v0 + t;
+                    tvv[j] = 2.0 / vv[j];
                     s_alpha = alpha;
                 }
             }
@@ -273,7 +296,7 @@ __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R
         double* vj = V + (int64_t)j * l;
         for (int i = j + 1 + tid; i < l; i += nth) vj[i] = wj[i];
         __syncthreads();
-        const double vvj = vv[j];
+        const double vvj = vv[j], t2 = tvv[j];
         if (vvj != 0.0) {
             for (int c = j + 1 + warp; c < l; c += nwarp) {
                 double* wc = Wt + (int64_t)c * l;
@@ -281,28 +304,11 @@ __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R
                 for (int i = j + lane; i < l; i += 32) d += vj[i] * wc[i];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const double f = 2.0 * d / vvj;
+                const double f = d * t2;
                 for (int i = j + lane; i < l; i += 32) wc[i] -= f * vj[i];
             }
             if (tid == 0) wj[j] = s_alpha;
             for (int i = j + 1 + tid; i < l; i += nth) wj[i] = 0.0;
-        }
-        __syncthreads();
-    }
-    // Ptil = H_0 ... H_{l-1} [I]: columns c < j are untouched unit vectors at step j.
-    for (int j = l - 1; j >= 0; --j) {
-        const double vvj = vv[j];
-        if (vvj != 0.0) {
-            const double* vj = V + (int64_t)j * l;
-            for (int c = j + warp; c < l; c += nwarp) {
-                double* pc = Pt + (int64_t)c * l;
-                double d = 0.0;
-                for (int i = j + lane; i < l; i += 32) d += vj[i] * pc[i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const double f = 2.0 * d / vvj;
-                for (int i = j + lane; i < l; i += 32) pc[i] -= f * vj[i];
-            }
         }
         __syncthreads();
     }
@@ -312,8 +318,35 @@ __device__ __forceinline__ void dev_small_qr(int l, const double* __restrict__ R
     for (int64_t e = tid; e < ll; e += nth) {
         const int b = (int)(e / l), a = (int)(e - (int64_t)b * l);
         L[e] = (b >= a) ? sg[a] * Wt[e] : 0.0;
-        // Ptil[i][c] = sg[c] * Pt[c][i]  with (i, c) = (b, a)
-        Ptil[e] = sg[a] * Pt[(int64_t)a * l + b];
+    }
+    __syncthreads();
+    // Ptil = H_0 ... H_{l-1} [I] in the storage of Wt: columns c < j are
+    // untouched unit vectors at step j
+    for (int64_t e = tid; e < ll; e += nth) {
+        const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
+        Pt[e] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = l - 1; j >= 0; --j) {
+        const double vvj = vv[j], t2 = tvv[j];
+        if (vvj != 0.0) {
+            const double* vj = V + (int64_t)j * l;
+            for (int c = j + warp; c < l; c += nwarp) {
+                double* pc = Pt + (int64_t)c * l;
+                double d = 0.0;
+                for (int i = j + lane; i < l; i += 32) d += vj[i] * pc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                const double f = d * t2;
+                for (int i = j + lane; i < l; i += 32) pc[i] -= f * vj[i];
+            }
+        }
+        __syncthreads();
+    }
+    // Ptil[i][c] = sg[c] * Pt[c][i]
+    for (int64_t e = tid; e < ll; e += nth) {
+        const int i = (int)(e / l), c = (int)(e - (int64_t)i * l);
+        Ptil[e] = sg[c] * Pt[(int64_t)c * l + i];
     }
 }
 

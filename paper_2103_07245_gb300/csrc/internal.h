@@ -37,9 +37,17 @@ cudaError_t launch_dgemm_skinny(bool transA, int64_t M, int N, int64_t K, const 
 // Max resident CTAs per SM of the skinny GEMM for this N.
 int dgemm_skinny_occupancy(int N);
 
-// C[i*ldc + c] = sum_{s<S} part[s*part_stride + i*ldp + c]  (fixed order; deterministic).
+// C[i*ldc + c] = sum_{s<S} part[s*part_stride + i*ldp + c]  (fixed order; deterministic);
+// with upper, only c >= i.
 cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, int64_t part_stride,
-                                   int64_t ldp, double* C, int64_t ldc, const int* cond, cudaStream_t s);
+                                   int64_t ldp, double* C, int64_t ldc, const int* cond, cudaStream_t s,
+                                   bool upper = false);
+
+// Upper triangle of A^T B (A, B: K x l, ld ld) into the split-K partial
+// buffer: one launch per 64-row tile, columns from the tile's first row
+// (the Gram of CholeskyQR and R = Q^T D need only that triangle).
+cudaError_t launch_upper_product(int l, int64_t K, const double* A, const double* B, int64_t ld, double* part,
+                                 int64_t part_stride, int S, int64_t kchunk, const int* cond, cudaStream_t s);
 
 // One-CTA Cholesky G = R^T R of the l x l Gram (ld l) of a rows x l panel.
 // Writes R packed (upper, row-major packed) plus 1/diag (l values after the
@@ -48,13 +56,15 @@ cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, 
 cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rpacked, uint32_t* status,
                             int* ctl, int pass, cudaStream_t s);
 
-// Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels.
+// Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels; f32
+// solves in FP32 (the mixed modes) instead of FP64.
 cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rpacked, const double* X, int64_t ldx,
-                             double* Y, int64_t ldy, const int* cond, cudaStream_t s);
+                             double* Y, int64_t ldy, const int* cond, cudaStream_t s, bool f32 = false);
 
 // One-CTA Householder QR of R^T (R upper, l x l dense ld l, only upper part read):
 // R^T = Ptil Rtil with diag(Rtil) >= 0.  Writes L = Rtil^T (l x l, ld l) and
-// Ptil (l x l row-major, ld l).  work: 2*l*l + 2*l doubles.
+// Ptil (l x l row-major, ld l).  work: 2*l*l doubles (unused when they fit in
+// shared memory, l <= 121).
 cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s);
 
 // Zero the strictly-lower part of an l x l matrix (ld l) in place.

@@ -70,28 +70,29 @@ cudaError_t launch_cholesky_list(const MatUnit* units, int nunits, int lmax, cud
     return cudaGetLastError();
 }
 
-template <int U>
+template <int U, typename T>
 __global__ void __launch_bounds__(256) k_trsm_list(const TrsmUnit* __restrict__ units) {
-    extern __shared__ double sR[];
+    extern __shared__ __align__(16) unsigned char sraw[];
+    T* sR = (T*)sraw;
     const TrsmUnit u = units[blockIdx.x];
     if (u.cond && *u.cond == 0) return;
     const int64_t P = (int64_t)u.l * (u.l + 1) / 2;
-    for (int64_t e = threadIdx.x; e < P + u.l; e += blockDim.x) sR[e] = u.Rp[e];
+    for (int64_t e = threadIdx.x; e < P + u.l; e += blockDim.x) sR[e] = (T)u.Rp[e];
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    dev_trsm_rows<U>(u.l, sR, u.X, u.ldx, u.Y, u.ldy, u.r0 + warp, u.r1, 8);
+    dev_trsm_rows<U, T>(u.l, sR, u.X, u.ldx, u.Y, u.ldy, u.r0 + warp, u.r1, 8);
 }
 
-cudaError_t launch_trsm_list(const TrsmUnit* units, int nunits, int lmax, cudaStream_t s) {
-    if (nunits <= 0) return cudaSuccess;
-    const size_t smem = (size_t)(packed_tri(lmax) + lmax) * sizeof(double);
+template <typename T>
+static cudaError_t trsm_list_t(const TrsmUnit* units, int nunits, int lmax, cudaStream_t s) {
+    const size_t smem = (size_t)(packed_tri(lmax) + lmax) * sizeof(T);
     const int U = (lmax + 31) / 32;
     cudaError_t e = cudaSuccess;
     switch (U) {
 #define PBQ_T(UU) case UU: \
-        e = cudaFuncSetAttribute(k_trsm_list<UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = cudaFuncSetAttribute(k_trsm_list<UU, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e; \
-        k_trsm_list<UU><<<nunits, 256, smem, s>>>(units); break;
+        k_trsm_list<UU, T><<<nunits, 256, smem, s>>>(units); break;
         PBQ_T(1) PBQ_T(2) PBQ_T(3) PBQ_T(4) PBQ_T(5) PBQ_T(6) PBQ_T(7)
 #undef PBQ_T
         default: return cudaErrorInvalidValue;
@@ -100,14 +101,26 @@ cudaError_t launch_trsm_list(const TrsmUnit* units, int nunits, int lmax, cudaSt
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_small_qr_list(const MatUnit* __restrict__ units) {
-    const MatUnit& u = units[blockIdx.x];
-    dev_small_qr(u.l, u.G, u.L, u.Pt, u.work);
+cudaError_t launch_trsm_list(const TrsmUnit* units, int nunits, int lmax, cudaStream_t s, bool f32) {
+    if (nunits <= 0) return cudaSuccess;
+    return f32 ? trsm_list_t<float>(units, nunits, lmax, s) : trsm_list_t<double>(units, nunits, lmax, s);
 }
 
-cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, cudaStream_t s) {
+__global__ void __launch_bounds__(1024) k_small_qr_list(const MatUnit* __restrict__ units, int use_smem) {
+    extern __shared__ double qsm[];
+    const MatUnit& u = units[blockIdx.x];
+    dev_small_qr(u.l, u.G, u.L, u.Pt, u.work, use_smem ? qsm : nullptr);
+}
+
+cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, int lmax, cudaStream_t s) {
     if (nunits <= 0) return cudaSuccess;
-    k_small_qr_list<<<nunits, 256, 0, s>>>(units);
+    const size_t smem = 2 * (size_t)lmax * lmax * sizeof(double);
+    const bool fits = smem <= 220 * 1024;
+    if (fits) {
+        cudaError_t e = cudaFuncSetAttribute(k_small_qr_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_small_qr_list<<<nunits, 256, fits ? smem : 0, s>>>(units, fits ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }

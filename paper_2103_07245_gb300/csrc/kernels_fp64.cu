@@ -80,6 +80,20 @@ cudaError_t launch_dgemm_skinny(bool transA, int64_t M, int N, int64_t K, const 
                   : dispatch_dgemm<false>(TN, grid, M, N, K, A, lda, B, ldb, C, ldc, kchunk, part_stride, cond, s);
 }
 
+cudaError_t launch_upper_product(int l, int64_t K, const double* A, const double* B, int64_t ld, double* part,
+                                 int64_t part_stride, int S, int64_t kchunk, const int* cond, cudaStream_t s) {
+    for (int m0 = 0; m0 < l; m0 += kGemmBM) {
+        const int M = (l - m0 < kGemmBM) ? l - m0 : kGemmBM;
+        const int N = l - m0;
+        const int TN = (N + 15) / 16;
+        dim3 grid(1u, (unsigned)S);
+        cudaError_t e = dispatch_dgemm<true>(TN, grid, M, N, K, A + m0, ld, B + m0, ld, part + (int64_t)m0 * ld + m0,
+                                             ld, kchunk, part_stride, cond, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int dgemm_skinny_occupancy(int N) {
     const int TN = (N + 15) / 16;
     int occ = 1;
@@ -99,12 +113,14 @@ int dgemm_skinny_occupancy(int N) {
 // Deterministic split-K reduction.
 // ---------------------------------------------------------------------------
 __global__ void k_reduce_partials(int64_t M, int N, int S, const double* __restrict__ part, int64_t ps,
-                                  int64_t ldp, double* __restrict__ C, int64_t ldc, const int* __restrict__ cond) {
+                                  int64_t ldp, double* __restrict__ C, int64_t ldc, const int* __restrict__ cond,
+                                  int upper) {
     if (cond && *cond == 0) return;
     const int64_t total = M * (int64_t)N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / N;
         const int c = (int)(e - i * N);
+        if (upper && c < i) continue;   // only the upper triangle was computed
         const double* p = part + i * ldp + c;
         double acc = 0.0;
         for (int s = 0; s < S; ++s) acc += p[(int64_t)s * ps];
@@ -113,12 +129,12 @@ __global__ void k_reduce_partials(int64_t M, int N, int S, const double* __restr
 }
 
 cudaError_t launch_reduce_partials(int64_t M, int N, int S, const double* part, int64_t ps, int64_t ldp,
-                                   double* C, int64_t ldc, const int* cond, cudaStream_t s) {
+                                   double* C, int64_t ldc, const int* cond, cudaStream_t s, bool upper) {
     const int64_t total = M * (int64_t)N;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_reduce_partials<<<(unsigned)blocks, 256, 0, s>>>(M, N, S, part, ps, ldp, C, ldc, cond);
+    k_reduce_partials<<<(unsigned)blocks, 256, 0, s>>>(M, N, S, part, ps, ldp, C, ldc, cond, upper ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -151,31 +167,34 @@ cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rp, ui
 // x_c -= y_t r_tc (c > t); lane owns columns lane + 32u.  R (packed) and
 // 1/diag(R) sit in shared memory.
 // ---------------------------------------------------------------------------
-template <int U>
+template <int U, typename T>
 __global__ void __launch_bounds__(256)
 k_trsm_rows(int64_t rows, int l, const double* __restrict__ Rp, const double* __restrict__ X, int64_t ldx,
             double* __restrict__ Y, int64_t ldy, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
-    extern __shared__ double sR[];
+    extern __shared__ __align__(16) unsigned char sraw[];
+    T* sR = (T*)sraw;
     const int64_t P = (int64_t)l * (l + 1) / 2;
-    for (int64_t e = threadIdx.x; e < P + l; e += blockDim.x) sR[e] = Rp[e];
+    for (int64_t e = threadIdx.x; e < P + l; e += blockDim.x) sR[e] = (T)Rp[e];
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    dev_trsm_rows<U>(l, sR, X, ldx, Y, ldy, (int64_t)blockIdx.x * 8 + warp, rows, (int64_t)gridDim.x * 8);
+    dev_trsm_rows<U, T>(l, sR, X, ldx, Y, ldy, (int64_t)blockIdx.x * 8 + warp, rows, (int64_t)gridDim.x * 8);
 }
 
-cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double* X, int64_t ldx, double* Y,
-                             int64_t ldy, const int* cond, cudaStream_t s) {
-    const size_t smem = (size_t)(packed_tri(l) + l) * sizeof(double);
+template <typename T>
+static cudaError_t trsm_launch_t(int64_t rows, int l, const double* Rp, const double* X, int64_t ldx, double* Y,
+                                 int64_t ldy, const int* cond, cudaStream_t s) {
+    const size_t smem = (size_t)(packed_tri(l) + l) * sizeof(T);
+    const int64_t per_sm = 227 * 1024 / (int64_t)(smem + 1024) > 0 ? 227 * 1024 / (int64_t)(smem + 1024) : 1;
     int64_t blocks = (rows + 7) / 8;
-    if (blocks > 152 * 2) blocks = 152 * 2;
+    if (blocks > 152 * per_sm) blocks = 152 * per_sm;
     if (blocks < 1) blocks = 1;
     const int U = (l + 31) / 32;
     cudaError_t e = cudaSuccess;
 #define PBQ_TR(UU) case UU: \
-        e = cudaFuncSetAttribute(k_trsm_rows<UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = cudaFuncSetAttribute(k_trsm_rows<UU, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e; \
-        k_trsm_rows<UU><<<(unsigned)blocks, 256, smem, s>>>(rows, l, Rp, X, ldx, Y, ldy, cond); break;
+        k_trsm_rows<UU, T><<<(unsigned)blocks, 256, smem, s>>>(rows, l, Rp, X, ldx, Y, ldy, cond); break;
     switch (U) {
         PBQ_TR(1) PBQ_TR(2) PBQ_TR(3) PBQ_TR(4) PBQ_TR(5) PBQ_TR(6) PBQ_TR(7)
         default: return cudaErrorInvalidValue;
@@ -183,6 +202,12 @@ cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double
 #undef PBQ_TR
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double* X, int64_t ldx, double* Y,
+                             int64_t ldy, const int* cond, cudaStream_t s, bool f32) {
+    return f32 ? trsm_launch_t<float>(rows, l, Rp, X, ldx, Y, ldy, cond, s)
+               : trsm_launch_t<double>(rows, l, Rp, X, ldx, Y, ldy, cond, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -193,12 +218,19 @@ cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rp, const double
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
 k_small_qr(int l, const double* __restrict__ R, double* __restrict__ L, double* __restrict__ Ptil,
-           double* __restrict__ work) {
-    dev_small_qr(l, R, L, Ptil, work);
+           double* __restrict__ work, int use_smem) {
+    extern __shared__ double qsm[];
+    dev_small_qr(l, R, L, Ptil, work, use_smem ? qsm : nullptr);
 }
 
 cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s) {
-    k_small_qr<<<1, 1024, 0, s>>>(l, R, L, Ptil, work);
+    const size_t smem = 2 * (size_t)l * l * sizeof(double);
+    const bool fits = smem <= 220 * 1024;
+    if (fits) {
+        cudaError_t e = cudaFuncSetAttribute(k_small_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_small_qr<<<1, 1024, fits ? smem : 0, s>>>(l, R, L, Ptil, work, fits ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -46,7 +46,8 @@ template <int NPROD, int BN, int STAGES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int64_t tiles,
-          int KI, int smax, float* __restrict__ part, uint32_t* __restrict__ status, uint64_t timeout_ns) {
+          int KI, int smax, float* __restrict__ part, uint32_t* __restrict__ status, uint64_t timeout_ns,
+          int stall) {
     constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
     constexpr uint32_t B_BYTES = BN * kTcBK * 2;
     constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
@@ -98,8 +99,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
     };
 
     if (warp == 0) {
-        // ---------------- TMA producer
-        if (lane == 0) {
+        // ---------------- TMA producer (stall: a host-requested test of the
+        // bounded waits; nothing is issued and the consumers time out)
+        if (lane == 0 && !stall) {
             int li = 0;
             for (int64_t it = it_begin; it < it_end; ++it, ++li) {
                 const int s = li % STAGES;
@@ -326,7 +328,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
 
 template <int NPROD, int BN>
 cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part, uint32_t* status,
-                         uint64_t timeout_ns, cudaStream_t s) {
+                         uint64_t timeout_ns, cudaStream_t s, int stall) {
     constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2;
     constexpr uint32_t STAGE = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
     constexpr int STAGES = (int)((220u * 1024u) / STAGE) > 8 ? 8 : (int)((220u * 1024u) / STAGE);
@@ -335,16 +337,16 @@ cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int
     auto kern = k_tc_gemm<NPROD, BN, STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<G, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns);
+    kern<<<G, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns, stall);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int NPROD>
 cudaError_t launch_tc_nprod(int BN, const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part,
-                            uint32_t* status, uint64_t to, cudaStream_t s) {
+                            uint32_t* status, uint64_t to, cudaStream_t s, int stall) {
     switch (BN) {
-#define PBQ_BN(X) case X: return launch_tc_bn<NPROD, X>(m, tiles, KI, G, smax, part, status, to, s);
+#define PBQ_BN(X) case X: return launch_tc_bn<NPROD, X>(m, tiles, KI, G, smax, part, status, to, s, stall);
         PBQ_BN(16) PBQ_BN(32) PBQ_BN(48) PBQ_BN(64) PBQ_BN(80) PBQ_BN(96) PBQ_BN(112) PBQ_BN(128)
         PBQ_BN(144) PBQ_BN(160) PBQ_BN(176) PBQ_BN(192) PBQ_BN(208) PBQ_BN(224)
 #undef PBQ_BN
@@ -372,16 +374,18 @@ TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms) {
 int64_t tc_ld(int64_t K) { return round_up(K, 64); }
 
 cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, float* part, double* C, int64_t ldc,
-                              uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm) {
+                              uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm, int stall) {
     if (op.N < 1 || op.N > kMaxEll || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
     CUtensorMap maps[4];
     if (!make_map(&maps[0], op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
     if (!make_map(&maps[1], op.Alo ? op.Alo : op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
     if (!make_map(&maps[2], op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
     if (!make_map(&maps[3], op.Blo ? op.Blo : op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
-    const uint64_t timeout_ns = 2000000000ull;
-    cudaError_t e = nprod == 3 ? launch_tc_nprod<3>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s)
-                               : launch_tc_nprod<1>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s);
+    // a stalled test launch gives up after 50 ms; real launches after 2 s
+    const uint64_t timeout_ns = stall ? 50000000ull : 2000000000ull;
+    cudaError_t e = nprod == 3
+                        ? launch_tc_nprod<3>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall)
+                        : launch_tc_nprod<1>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall);
     if (e != cudaSuccess) return e;
     if (after_gemm && (e = cudaEventRecord(after_gemm, s)) != cudaSuccess) return e;
     const int64_t total = op.rows * (int64_t)op.N;

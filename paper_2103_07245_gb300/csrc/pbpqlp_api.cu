@@ -31,6 +31,7 @@ struct pbpqlp_plan_s {
     size_t off_part = 0, off_G = 0, off_Rp = 0, off_R = 0, off_Pt = 0, off_work = 0, off_red = 0, total = 0;
     // mixed modes: BF16 copies of A and A^T, transposed panels, stream-K partials
     int nprod = 0;                      // 1 (BF16) or 3 (split BF16); 0 in FP64 mode
+    int fault_stall = 0;                // PBPQLP_FAULT=tc_stall at plan creation (failure-detection test)
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
@@ -88,11 +89,11 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
 }
 
 // Split-K count for Mtiles output tiles over a contraction of K: the S that
-// best fills whole waves of `slots` resident CTAs with chunks of >= 64 rows.
-void choose_split(int64_t Mtiles, int64_t K, int64_t slots, int* S_out, int64_t* kc_out) {
+// best fills whole waves of `slots` resident CTAs with chunks of >= min_chunk rows.
+void choose_split(int64_t Mtiles, int64_t K, int64_t slots, int* S_out, int64_t* kc_out, int64_t min_chunk = 64) {
     int bestS = 1;
     double best = -1.0;
-    const int64_t maxS = K / 64 > 1 ? K / 64 : 1;
+    const int64_t maxS = K / min_chunk > 1 ? K / min_chunk : 1;
     for (int64_t S = 1; S <= maxS && S <= 512; ++S) {
         const int64_t kc = round_up((K + S - 1) / S, kGemmBK);
         const int64_t Seff = (K + kc - 1) / kc;
@@ -167,7 +168,7 @@ int tc_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t
     if (gg.part_floats > g->part_floats) return PBPQLP_EINVAL;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-    PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, C, ldc, w.status, s, ev.second));
+    PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, C, ldc, w.status, s, ev.second, P->fault_stall));
     return PBPQLP_OK;
 }
 
@@ -190,10 +191,11 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         double* dst = (pass & 1) ? Y : X;
         const int* cond = pass <= 2 ? nullptr : w.ctl + 8 + (pass + 1) / 2;
         const int64_t ps = (int64_t)l * ldp;
-        PBQ_TRY(launch_dgemm_skinny(true, l, l, rows, src, ldp, src, ldp, w.part, ldp, Sg, kcg, ps, cond, s));
-        PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s));
+        // the Cholesky reads only the upper triangle of the Gram
+        PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
+        PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
         PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
-        PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s));
+        PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s, P->nprod > 0));
     }
     return PBPQLP_OK;
 }
@@ -249,8 +251,10 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     const int64_t lt = (P->l + kGemmBM - 1) / kGemmBM;
     choose_split(mt, n, slots, &P->S_nn, &P->kc_nn);
     choose_split(nt, m, slots, &P->S_tn, &P->kc_tn);
-    choose_split(lt, m, slots, &P->S_gm, &P->kc_gm);
-    choose_split(lt, n, slots, &P->S_gn, &P->kc_gn);
+    // Grams and R = Q^T D are launched one 64-row tile at a time (upper triangle)
+    (void)lt;
+    choose_split(1, m, slots, &P->S_gm, &P->kc_gm, 32);
+    choose_split(1, n, slots, &P->S_gn, &P->kc_gn, 32);
 
     const int64_t ldp = P->ldp, l = P->l;
     int64_t part = (int64_t)P->S_nn * m * ldp;
@@ -274,10 +278,12 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->off_Rp = take(sizeof(double) * (packed_tri((int)l) + l));
     P->off_R = take(sizeof(double) * l * ldp);
     P->off_Pt = take(sizeof(double) * l * ldp);
-    P->off_work = take(sizeof(double) * (3 * l * l + 2 * l));
+    P->off_work = take(sizeof(double) * (2 * l * l + 2 * l));
     P->off_red = take(sizeof(double) * 2048);
     if (mode == PBPQLP_MODE_BF16 || mode == PBPQLP_MODE_BF16X3) {
         P->nprod = (mode == PBPQLP_MODE_BF16X3) ? 3 : 1;
+        const char* fault = std::getenv("PBPQLP_FAULT");
+        P->fault_stall = (fault && std::strcmp(fault, "tc_stall") == 0) ? 1 : 0;
         P->ldk_n = tc_ld(n);
         P->ldk_m = tc_ld(m);
         P->g_nn = tc_geometry(m, n, P->l, P->num_sms);
@@ -352,9 +358,8 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
     {
         const int64_t ps = (int64_t)l * ldp;
-        PBQ_TRY(launch_dgemm_skinny(true, l, l, m, w.Xm, ldp, w.Dm, ldp, w.part, ldp, P->S_gm, P->kc_gm, ps, nullptr, s));
-        PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s));
-        PBQ_TRY(launch_triu(l, w.R, s));
+        PBQ_TRY(launch_upper_product(l, m, w.Xm, w.Dm, ldp, w.part, ps, P->S_gm, P->kc_gm, nullptr, s));
+        PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s, true));
     }
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
     PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));

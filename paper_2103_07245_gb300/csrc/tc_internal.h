@@ -31,8 +31,10 @@ struct TcOperands {
 
 // C (FP64, rows x N, ldc) = Aop Bt^T with 1 (BF16) or 3 (split BF16) products.
 // after_gemm (optional) is recorded between the tensor-core kernel and the reduction.
+// stall != 0 is the failure-detection test: the producer issues nothing, the
+// bounded waits expire after 50 ms and the status word gets the timeout bit.
 cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, float* part, double* C, int64_t ldc,
-                              uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm = nullptr);
+                              uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm = nullptr, int stall = 0);
 
 // A (m x n, FP32 or FP64, lda) -> hi/lo BF16 (m x n, ld ldh) and, when thi is
 // given, the transposed hi/lo (n x m, ld ldt).  lo / tlo may be null.

@@ -90,8 +90,9 @@ def test_split_bf16_factorization_within_1p1_of_oracle(pq):
     e_mixed, e_orc, (Qa, L, Qb) = _mixed_errors(pq, A32, 20, 5, 2, 11, pq.PBPQLP_MODE_BF16X3)
     assert e_mixed <= 1.1 * e_orc, (e_mixed, e_orc)
     assert np.array_equal(L, np.tril(L))
-    assert np.allclose(Qa.T @ Qa, np.eye(25), atol=1e-12)
-    assert np.allclose(Qb.T @ Qb, np.eye(25), atol=1e-12)
+    # the mixed modes apply the triangular factors in FP32: orthonormal to ~1e-7
+    assert np.allclose(Qa.T @ Qa, np.eye(25), atol=1e-6)
+    assert np.allclose(Qb.T @ Qb, np.eye(25), atol=1e-6)
 
 
 def test_bf16_single_term_factorization_runs(pq):
@@ -115,3 +116,26 @@ def test_config3_full_size_within_1p1(pq):
     A32 = A.cpu().numpy()
     e_mixed, e_orc, _ = _mixed_errors(pq, A32, 200, 20, 2, 17, pq.PBPQLP_MODE_BF16X3)
     assert e_mixed <= 1.1 * e_orc, (e_mixed, e_orc)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(pq, monkeypatch):
+    """Failure detection without a GPU fault: with PBPQLP_FAULT=tc_stall the
+    tensor-core producer issues nothing, the consumers' bounded waits expire
+    (50 ms), the kernel frees its TMEM and returns, and the status reads
+    PBPQLP_ETIMEOUT; the next plan on the same context works."""
+    import torch
+    rng = np.random.default_rng(0)
+    A = torch.from_numpy(rng.standard_normal((300, 200)).astype(np.float32)).cuda()
+    Y = torch.from_numpy(rng.standard_normal((200, 16))).cuda()
+    monkeypatch.setenv("PBPQLP_FAULT", "tc_stall")
+    bad = pq.Plan(300, 200, 12, 4, 0, seed=1, mode=pq.PBPQLP_MODE_BF16X3)
+    monkeypatch.delenv("PBPQLP_FAULT")
+    bad.sketch(A, Y)
+    rc, flags = bad.sync_status()
+    assert rc == pq.PBPQLP_ETIMEOUT and (flags & 8), (rc, flags)
+    good = pq.Plan(300, 200, 12, 4, 0, seed=1, mode=pq.PBPQLP_MODE_BF16X3)
+    C = good.sketch(A, Y).cpu().numpy()
+    rc, flags = good.sync_status()
+    assert rc == pq.PBPQLP_OK, flags
+    ref = A.double().cpu().numpy() @ Y.cpu().numpy()
+    assert np.max(np.abs(C - ref)) <= 1e-3 * np.max(np.abs(ref))
