@@ -167,6 +167,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def dist_max(value, device=None):
+    """Maximum of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,10 +258,7 @@ def run_batched(args, w, world, rank, local):
     B = pq.Batch(ms_, ns_, ks_, p, q, seed=11 + rank, mode=mode, stream=stream, device=dev)
     outs = B.outputs(dev)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = dist_barrier
 
     B.factor(A32, out=outs)
     tuned_ms = None
@@ -273,13 +292,9 @@ def run_batched(args, w, world, rank, local):
     ms = e0.elapsed_time(e1) / args.steps
     tc_ms, tc_n = pq.pbpqlp_batch_read_timing(B.handle)   # the last step's grouped products
     pq.pbpqlp_batch_set_timing(B.handle, False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = dist_max(ms, dev)
     count = w["count"]
-    value = world * count / (ms / 1e3)
+    value = whole_job_rate(count, world, ms)
 
     def rel_errors(out_t, As):
         e = []
@@ -314,7 +329,7 @@ def run_batched(args, w, world, rank, local):
         e2e_step()
     f1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_e2e = f0.elapsed_time(f1) / args.steps
+    ms_e2e = dist_max(f0.elapsed_time(f1) / args.steps, dev)
 
     # the batched FP64 form on the same data (the plain-FP64 GPU reference)
     cmp = None
@@ -445,10 +460,7 @@ def main():
     plan = pq.Plan(m, n, k, p, q, seed=7 + rank, mode=mode, stream=stream, device=dev)
     Qa, L, Qb = plan.outputs(dev)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = dist_barrier
 
     def timed_run(pl, outs, steps, sampler=None):
         """K factorizations bracketed by barrier + synchronize; returns (ms/step, pass ms, passes, launches, clocks)."""
@@ -486,12 +498,8 @@ def main():
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
     sampler = ClockSampler(int(vis) if vis.isdigit() else local)
     ms, pass_ms, pass_launches, launches, clocks = timed_run(plan, (Qa, L, Qb), args.steps, sampler)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world / (ms / 1e3)
+    ms = dist_max(ms, dev)
+    value = whole_job_rate(1, world, ms)
     err_main = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_RESIDUAL)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -517,12 +525,7 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    ms_e2e = f0.elapsed_time(f1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = dist_max(f0.elapsed_time(f1) / args.steps, dev)
 
     flops = algorithmic_flops(m, n, l, q)
     avg_pass_ms = (pass_ms / pass_launches) if pass_launches else None
