@@ -38,21 +38,23 @@ namespace pbq {
 using namespace tcdev;
 
 constexpr int kTcBM = 128;   // rows per tile (one TMEM lane per row)
-constexpr int kTcBK = 64;    // BF16 elements per k-block (one 128-byte swizzle row)
-constexpr int kTcKC = 16;    // k-blocks per TMEM accumulation chunk (1024-deep sums)
+constexpr int kTcRowBytes = 128;   // one k-block = one 128-byte swizzle row: 64 BF16 or 32 TF32 elements
+constexpr int kTcKC = 16;    // k-blocks per TMEM accumulation chunk (1024-deep BF16, 512-deep TF32 sums)
+__host__ __device__ constexpr int tc_bk(bool tf32) { return tf32 ? 32 : 64; }
 constexpr int kTcThreads = 320;
 
-template <int NPROD, int BN, int STAGES>
+template <int NPROD, int BN, int STAGES, bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
           const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int64_t tiles,
           int KI, int smax, float* __restrict__ part, uint32_t* __restrict__ status, uint64_t timeout_ns,
           int stall) {
-    constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2;
-    constexpr uint32_t B_BYTES = BN * kTcBK * 2;
+    constexpr int BK = tc_bk(TF32);
+    constexpr uint32_t A_BYTES = kTcBM * kTcRowBytes;
+    constexpr uint32_t B_BYTES = BN * kTcRowBytes;
     constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
     constexpr uint32_t ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-    constexpr uint32_t IDESC = idesc_bf16_f32(kTcBM, BN);
+    constexpr uint32_t IDESC = TF32 ? idesc_tf32_f32(kTcBM, BN) : idesc_bf16_f32(kTcBM, BN);
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -112,7 +114,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                     }
                 }
                 const int64_t tile = it / KI;
-                const int k0 = (int)(it - tile * KI) * kTcBK;
+                const int k0 = (int)(it - tile * KI) * BK;
                 const int m0 = (int)(tile * kTcBM);
                 mbar_expect_tx(&full_bar[s], STAGE_BYTES);
                 tma_load_2d(stage_ptr(s, 0), &tmAhi, &full_bar[s], k0, m0);
@@ -156,13 +158,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUt
                         const uint32_t ahi = smem_u32(stage_ptr(s, 0)), bhi = smem_u32(stage_ptr(s, 1));
                         const uint32_t alo = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
 #pragma unroll
-                        for (int kk = 0; kk < kTcBK / 16; ++kk) {
-                            const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along the swizzled row
-                            tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(bhi + off), IDESC,
-                                        (first && kk == 0) ? 0u : 1u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            // one MMA k-step = 32 bytes of the swizzled row (16 BF16 or 8 TF32)
+                            const uint32_t off = kk * 32;
+                            auto mma = [&](uint32_t a, uint32_t b, uint32_t acc) {
+                                if (TF32) tc_mma_tf32(dt, sdesc_k_sw128(a + off), sdesc_k_sw128(b + off), IDESC, acc);
+                                else tc_mma_bf16(dt, sdesc_k_sw128(a + off), sdesc_k_sw128(b + off), IDESC, acc);
+                            };
+                            mma(ahi, bhi, (first && kk == 0) ? 0u : 1u);
                             if (NPROD == 3) {
-                                tc_mma_bf16(dt, sdesc_k_sw128(alo + off), sdesc_k_sw128(bhi + off), IDESC, 1u);
-                                tc_mma_bf16(dt, sdesc_k_sw128(ahi + off), sdesc_k_sw128(blo + off), IDESC, 1u);
+                                mma(alo, bhi, 1u);
+                                mma(ahi, blo, 1u);
                             }
                         }
                         first = false;
@@ -313,28 +319,30 @@ PFN_encodeTiled encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map over a rows x cols row-major matrix (ld elements), box {64, box_rows}.
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 2-D tensor map over a rows x cols row-major matrix (ld elements) of BF16 or
+// FP32 (TF32 operands), box {one 128-byte row of k, box_rows}.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows, bool tf32) {
     PFN_encodeTiled fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * (tf32 ? 4 : 2)};
+    cuuint32_t box[2] = {(cuuint32_t)tc_bk(tf32), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    return fn(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+              dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPROD, int BN>
+template <int NPROD, int BN, bool TF32>
 cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part, uint32_t* status,
                          uint64_t timeout_ns, cudaStream_t s, int stall) {
-    constexpr uint32_t A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2;
+    constexpr uint32_t A_BYTES = kTcBM * kTcRowBytes, B_BYTES = BN * kTcRowBytes;
     constexpr uint32_t STAGE = (A_BYTES + B_BYTES) * (NPROD == 3 ? 2 : 1);
     constexpr int STAGES = (int)((220u * 1024u) / STAGE) > 8 ? 8 : (int)((220u * 1024u) / STAGE);
     static_assert(STAGES >= 2, "stage ring too small");
     const size_t smem = (size_t)STAGES * STAGE + 1024;
-    auto kern = k_tc_gemm<NPROD, BN, STAGES>;
+    auto kern = k_tc_gemm<NPROD, BN, STAGES, TF32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<G, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns, stall);
@@ -342,11 +350,11 @@ cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int
     return cudaGetLastError();
 }
 
-template <int NPROD>
+template <int NPROD, bool TF32>
 cudaError_t launch_tc_nprod(int BN, const CUtensorMap* m, int64_t tiles, int KI, int G, int smax, float* part,
                             uint32_t* status, uint64_t to, cudaStream_t s, int stall) {
     switch (BN) {
-#define PBQ_BN(X) case X: return launch_tc_bn<NPROD, X>(m, tiles, KI, G, smax, part, status, to, s, stall);
+#define PBQ_BN(X) case X: return launch_tc_bn<NPROD, X, TF32>(m, tiles, KI, G, smax, part, status, to, s, stall);
         PBQ_BN(16) PBQ_BN(32) PBQ_BN(48) PBQ_BN(64) PBQ_BN(80) PBQ_BN(96) PBQ_BN(112) PBQ_BN(128)
         PBQ_BN(144) PBQ_BN(160) PBQ_BN(176) PBQ_BN(192) PBQ_BN(208) PBQ_BN(224)
 #undef PBQ_BN
@@ -356,11 +364,11 @@ cudaError_t launch_tc_nprod(int BN, const CUtensorMap* m, int64_t tiles, int KI,
 
 }  // namespace
 
-TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms) {
+TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms, bool tf32) {
     TcGeom g;
     g.BN = (int)round_up(N, 16);
     g.tiles = (rows + kTcBM - 1) / kTcBM;
-    g.KI = (int)((K + kTcBK - 1) / kTcBK);
+    g.KI = (int)((K + tc_bk(tf32) - 1) / tc_bk(tf32));
     const int64_t T = g.tiles * g.KI;
     g.G = (int)(T < num_sms ? T : num_sms);
     if (g.G < 1) g.G = 1;
@@ -371,21 +379,24 @@ TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms) {
     return g;
 }
 
-int64_t tc_ld(int64_t K) { return round_up(K, 64); }
+int64_t tc_ld(int64_t K, bool tf32) { return round_up(K, tc_bk(tf32)); }
 
 cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, float* part, double* C, int64_t ldc,
                               uint32_t* status, cudaStream_t s, cudaEvent_t after_gemm, int stall) {
     if (op.N < 1 || op.N > kMaxEll || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
     CUtensorMap maps[4];
-    if (!make_map(&maps[0], op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
-    if (!make_map(&maps[1], op.Alo ? op.Alo : op.Ahi, op.rows, op.K, op.lda, kTcBM)) return cudaErrorInvalidValue;
-    if (!make_map(&maps[2], op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
-    if (!make_map(&maps[3], op.Blo ? op.Blo : op.Bhi, op.N, op.K, op.ldb, g.BN)) return cudaErrorInvalidValue;
+    const bool t = op.tf32 != 0;
+    if (!make_map(&maps[0], op.Ahi, op.rows, op.K, op.lda, kTcBM, t)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[1], op.Alo ? op.Alo : op.Ahi, op.rows, op.K, op.lda, kTcBM, t)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[2], op.Bhi, op.N, op.K, op.ldb, g.BN, t)) return cudaErrorInvalidValue;
+    if (!make_map(&maps[3], op.Blo ? op.Blo : op.Bhi, op.N, op.K, op.ldb, g.BN, t)) return cudaErrorInvalidValue;
     // a stalled test launch gives up after 50 ms; real launches after 2 s
     const uint64_t timeout_ns = stall ? 50000000ull : 2000000000ull;
-    cudaError_t e = nprod == 3
-                        ? launch_tc_nprod<3>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall)
-                        : launch_tc_nprod<1>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall);
+    cudaError_t e;
+    if (t) e = nprod == 3 ? launch_tc_nprod<3, true>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall)
+                          : launch_tc_nprod<1, true>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall);
+    else e = nprod == 3 ? launch_tc_nprod<3, false>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall)
+                        : launch_tc_nprod<1, false>(g.BN, maps, g.tiles, g.KI, g.G, g.smax, part, status, timeout_ns, s, stall);
     if (e != cudaSuccess) return e;
     if (after_gemm && (e = cudaEventRecord(after_gemm, s)) != cudaSuccess) return e;
     const int64_t total = op.rows * (int64_t)op.N;
@@ -397,23 +408,42 @@ cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, 
 }
 
 // ---------------------------------------------------------------------------
-// Operand preparation: BF16 hi/lo splits (row-major and transposed).
-// hi = RN_bf16(x), lo = RN_bf16(x - hi).
+// Operand preparation: hi/lo splits (row-major and transposed) into BF16
+// (hi = RN_bf16(x), lo = RN_bf16(x - hi)) or TF32 held in FP32
+// (hi = RN_tf32(x), lo = RN_tf32(x - hi), rounding by cvt.rna.tf32).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_split_a(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda, __nv_bfloat16* __restrict__ hi,
-                          __nv_bfloat16* __restrict__ lo, int64_t ldh, __nv_bfloat16* __restrict__ thi,
-                          __nv_bfloat16* __restrict__ tlo, int64_t ldt) {
-    __shared__ __nv_bfloat16 sh[32][33], sl[32][33];
+struct SplitBf16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T rn(double x) { return __double2bfloat16(x); }
+    static __device__ __forceinline__ double back(T h) { return (double)__bfloat162float(h); }
+    static __device__ __forceinline__ T zero() { return __float2bfloat16_rn(0.f); }
+};
+struct SplitTf32 {
+    using T = float;
+    static __device__ __forceinline__ T rn(double x) {
+        uint32_t r;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+        return __uint_as_float(r);
+    }
+    static __device__ __forceinline__ double back(T h) { return (double)h; }
+    static __device__ __forceinline__ T zero() { return 0.f; }
+};
+
+template <typename Tin, typename SP>
+__global__ void k_split_a(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, typename SP::T* __restrict__ hi,
+                          typename SP::T* __restrict__ lo, int64_t ldh, typename SP::T* __restrict__ thi,
+                          typename SP::T* __restrict__ tlo, int64_t ldt) {
+    using T = typename SP::T;
+    __shared__ T sh[32][33], sl[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     for (int k = ty; k < 32; k += 8) {
         const int64_t r = r0 + k, cc = c0 + tx;
-        __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
+        T h = SP::zero(), l = h;
         if (r < m && cc < n) {
             const double x = (double)A[r * lda + cc];
-            h = __double2bfloat16(x);
-            l = __double2bfloat16(x - (double)__bfloat162float(h));
+            h = SP::rn(x);
+            l = SP::rn(x - SP::back(h));
             hi[r * ldh + cc] = h;
             if (lo) lo[r * ldh + cc] = l;
         }
@@ -431,40 +461,50 @@ __global__ void k_split_a(int64_t m, int64_t n, const T* __restrict__ A, int64_t
     }
 }
 
-cudaError_t launch_split_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, void* hi, void* lo, int64_t ldh,
-                           void* thi, void* tlo, int64_t ldt, cudaStream_t s) {
-    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
+template <typename SP>
+static void split_a_t(dim3 grid, dim3 block, int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, void* hi,
+                      void* lo, int64_t ldh, void* thi, void* tlo, int64_t ldt, cudaStream_t s) {
+    using T = typename SP::T;
     if (a_f32)
-        k_split_a<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldh,
-                                               (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+        k_split_a<float, SP><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, (T*)hi, (T*)lo, ldh, (T*)thi, (T*)tlo, ldt);
     else
-        k_split_a<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo,
-                                                ldh, (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+        k_split_a<double, SP><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, (T*)hi, (T*)lo, ldh, (T*)thi, (T*)tlo,
+                                                    ldt);
+}
+
+cudaError_t launch_split_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, void* hi, void* lo, int64_t ldh,
+                           void* thi, void* tlo, int64_t ldt, cudaStream_t s, bool tf32) {
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
+    if (tf32) split_a_t<SplitTf32>(grid, block, m, n, A, a_f32, lda, hi, lo, ldh, thi, tlo, ldt, s);
+    else split_a_t<SplitBf16>(grid, block, m, n, A, a_f32, lda, hi, lo, ldh, thi, tlo, ldt, s);
     count_launches(1);
     return cudaGetLastError();
 }
 
-// Panel P (rows x N FP64, ld ldp) -> transposed BF16 hi/lo (N x rows, ld ldt).
+// Panel P (rows x N FP64, ld ldp) -> transposed hi/lo (N x rows, ld ldt).
+template <typename SP>
 __global__ void k_split_panel_t(int64_t rows, int N, const double* __restrict__ P, int64_t ldp,
-                                __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo, int64_t ldt) {
+                                typename SP::T* __restrict__ thi, typename SP::T* __restrict__ tlo, int64_t ldt) {
     const int64_t total = rows * (int64_t)N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / rows);
         const int64_t r = e - (int64_t)j * rows;
         const double x = P[r * ldp + j];
-        const __nv_bfloat16 h = __double2bfloat16(x);
+        const typename SP::T h = SP::rn(x);
         thi[(int64_t)j * ldt + r] = h;
-        if (tlo) tlo[(int64_t)j * ldt + r] = __double2bfloat16(x - (double)__bfloat162float(h));
+        if (tlo) tlo[(int64_t)j * ldt + r] = SP::rn(x - SP::back(h));
     }
 }
 
 cudaError_t launch_split_panel_t(int64_t rows, int N, const double* P, int64_t ldp, void* thi, void* tlo, int64_t ldt,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool tf32) {
     const int64_t total = rows * (int64_t)N;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_split_panel_t<<<(unsigned)blocks, 256, 0, s>>>(rows, N, P, ldp, (__nv_bfloat16*)thi, (__nv_bfloat16*)tlo, ldt);
+    if (tf32) k_split_panel_t<SplitTf32><<<(unsigned)blocks, 256, 0, s>>>(rows, N, P, ldp, (float*)thi, (float*)tlo, ldt);
+    else k_split_panel_t<SplitBf16><<<(unsigned)blocks, 256, 0, s>>>(rows, N, P, ldp, (__nv_bfloat16*)thi,
+                                                                    (__nv_bfloat16*)tlo, ldt);
     count_launches(1);
     return cudaGetLastError();
 }

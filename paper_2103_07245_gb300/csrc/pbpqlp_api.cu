@@ -32,6 +32,7 @@ struct pbpqlp_plan_s {
     // mixed modes: BF16 copies of A and A^T, transposed panels, stream-K partials
     int nprod = 0;                      // 1 (BF16) or 3 (split BF16); 0 in FP64 mode
     int fault_stall = 0;                // PBPQLP_FAULT=tc_stall at plan creation (failure-detection test)
+    bool tf32 = false;                  // TF32 operands (modes TF32, TF32X3) instead of BF16
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
@@ -152,19 +153,20 @@ int tc_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t
     TcOperands op;
     const TcGeom* g;
     if (!transA) {
-        PBQ_TRY(launch_split_panel_t(P->n, N, Y, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s));
+        PBQ_TRY(launch_split_panel_t(P->n, N, Y, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s, P->tf32));
         op.Ahi = w.Ahi; op.Alo = w.Alo; op.rows = P->m; op.K = P->n; op.lda = P->ldk_n;
         op.Bhi = w.Bnhi; op.Blo = w.Bnlo; op.ldb = P->ldk_n;
         g = &P->g_nn;
     } else {
-        PBQ_TRY(launch_split_panel_t(P->m, N, Y, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s));
+        PBQ_TRY(launch_split_panel_t(P->m, N, Y, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s, P->tf32));
         op.Ahi = w.Athi; op.Alo = w.Atlo; op.rows = P->n; op.K = P->m; op.lda = P->ldk_m;
         op.Bhi = w.Bmhi; op.Blo = w.Bmlo; op.ldb = P->ldk_m;
         g = &P->g_tn;
     }
     op.N = N;
+    op.tf32 = P->tf32 ? 1 : 0;
     TcGeom gg = *g;
-    if (N != P->l) gg = tc_geometry(op.rows, op.K, N, P->num_sms);
+    if (N != P->l) gg = tc_geometry(op.rows, op.K, N, P->num_sms, P->tf32);
     if (gg.part_floats > g->part_floats) return PBPQLP_EINVAL;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
@@ -174,7 +176,8 @@ int tc_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t
 
 // Split A once per factorization into the BF16 operands of both orientations.
 int tc_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, int64_t lda) {
-    PBQ_TRY(launch_split_a(P->m, P->n, A, a_f32, lda, w.Ahi, w.Alo, P->ldk_n, w.Athi, w.Atlo, P->ldk_m, P->stream));
+    PBQ_TRY(launch_split_a(P->m, P->n, A, a_f32, lda, w.Ahi, w.Alo, P->ldk_n, w.Athi, w.Atlo, P->ldk_m, P->stream,
+                           P->tf32));
     return PBPQLP_OK;
 }
 
@@ -234,7 +237,6 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
     if (l64 > m || l64 > n || l64 > kMaxEll) return PBPQLP_EINVAL;
     if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_TF32X3) return PBPQLP_EINVAL;
-    if (mode == PBPQLP_MODE_TF32 || mode == PBPQLP_MODE_TF32X3) return PBPQLP_EUNSUPPORTED;
     pbpqlp_plan_s* P = new (std::nothrow) pbpqlp_plan_s();
     if (!P) return PBPQLP_ENOMEM;
     P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
@@ -280,24 +282,26 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->off_Pt = take(sizeof(double) * l * ldp);
     P->off_work = take(sizeof(double) * (2 * l * l + 2 * l));
     P->off_red = take(sizeof(double) * 2048);
-    if (mode == PBPQLP_MODE_BF16 || mode == PBPQLP_MODE_BF16X3) {
-        P->nprod = (mode == PBPQLP_MODE_BF16X3) ? 3 : 1;
+    if (mode != PBPQLP_MODE_FP64) {
+        P->tf32 = (mode == PBPQLP_MODE_TF32 || mode == PBPQLP_MODE_TF32X3);
+        P->nprod = (mode == PBPQLP_MODE_BF16X3 || mode == PBPQLP_MODE_TF32X3) ? 3 : 1;
         const char* fault = std::getenv("PBPQLP_FAULT");
         P->fault_stall = (fault && std::strcmp(fault, "tc_stall") == 0) ? 1 : 0;
-        P->ldk_n = tc_ld(n);
-        P->ldk_m = tc_ld(m);
-        P->g_nn = tc_geometry(m, n, P->l, P->num_sms);
-        P->g_tn = tc_geometry(n, m, P->l, P->num_sms);
+        P->ldk_n = tc_ld(n, P->tf32);
+        P->ldk_m = tc_ld(m, P->tf32);
+        P->g_nn = tc_geometry(m, n, P->l, P->num_sms, P->tf32);
+        P->g_tn = tc_geometry(n, m, P->l, P->num_sms, P->tf32);
         const int64_t BN = P->g_nn.BN;
         const bool split = P->nprod == 3;
-        P->off_Ahi = take(2 * (size_t)m * P->ldk_n);
-        if (split) P->off_Alo = take(2 * (size_t)m * P->ldk_n);
-        P->off_Athi = take(2 * (size_t)n * P->ldk_m);
-        if (split) P->off_Atlo = take(2 * (size_t)n * P->ldk_m);
-        P->off_Bnhi = take(2 * (size_t)BN * P->ldk_n);
-        if (split) P->off_Bnlo = take(2 * (size_t)BN * P->ldk_n);
-        P->off_Bmhi = take(2 * (size_t)BN * P->ldk_m);
-        if (split) P->off_Bmlo = take(2 * (size_t)BN * P->ldk_m);
+        const size_t es = P->tf32 ? 4 : 2;   // bytes per operand element
+        P->off_Ahi = take(es * (size_t)m * P->ldk_n);
+        if (split) P->off_Alo = take(es * (size_t)m * P->ldk_n);
+        P->off_Athi = take(es * (size_t)n * P->ldk_m);
+        if (split) P->off_Atlo = take(es * (size_t)n * P->ldk_m);
+        P->off_Bnhi = take(es * (size_t)BN * P->ldk_n);
+        if (split) P->off_Bnlo = take(es * (size_t)BN * P->ldk_n);
+        P->off_Bmhi = take(es * (size_t)BN * P->ldk_m);
+        if (split) P->off_Bmlo = take(es * (size_t)BN * P->ldk_m);
         const int64_t pf = P->g_nn.part_floats > P->g_tn.part_floats ? P->g_nn.part_floats : P->g_tn.part_floats;
         P->off_tcpart = take(sizeof(float) * (size_t)pf);
     }

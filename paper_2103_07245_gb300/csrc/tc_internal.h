@@ -14,10 +14,11 @@ struct TcGeom {
     int smax = 1;           // partial slots per CTA
     int64_t part_floats = 0;
 };
-TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms);
+TcGeom tc_geometry(int64_t rows, int64_t K, int N, int num_sms, bool tf32 = false);
 
-// Leading dimension (elements) of the BF16 copies: K rounded up to 64.
-int64_t tc_ld(int64_t K);
+// Leading dimension (elements) of the operand copies: K rounded up to one
+// 128-byte row (64 BF16 or 32 FP32 elements).
+int64_t tc_ld(int64_t K, bool tf32 = false);
 
 struct TcOperands {
     const void* Ahi = nullptr;   // rows x K BF16, ld lda (K-major)
@@ -27,6 +28,7 @@ struct TcOperands {
     const void* Blo = nullptr;
     int N = 0;
     int64_t ldb = 0;
+    int tf32 = 0;                // operands are TF32 held in FP32 (else BF16)
 };
 
 // C (FP64, rows x N, ldc) = Aop Bt^T with 1 (BF16) or 3 (split BF16) products.
@@ -39,11 +41,11 @@ cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, 
 // A (m x n, FP32 or FP64, lda) -> hi/lo BF16 (m x n, ld ldh) and, when thi is
 // given, the transposed hi/lo (n x m, ld ldt).  lo / tlo may be null.
 cudaError_t launch_split_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, void* hi, void* lo, int64_t ldh,
-                           void* thi, void* tlo, int64_t ldt, cudaStream_t s);
+                           void* thi, void* tlo, int64_t ldt, cudaStream_t s, bool tf32 = false);
 
 // Panel P (rows x N FP64, ld ldp) -> transposed BF16 hi/lo (N x rows, ld ldt); tlo may be null.
 cudaError_t launch_split_panel_t(int64_t rows, int N, const double* P, int64_t ldp, void* thi, void* tlo, int64_t ldt,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool tf32 = false);
 
 // ---- grouped TF32 products of the batched path (kernels_tc_list.cu) ----------
 // One unit: C[m0 .. m0+127, 0 .. N) = Aop Bt^T over the full contraction

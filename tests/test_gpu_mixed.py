@@ -36,7 +36,19 @@ def split(x):
     return hi, bf16_rn(x - hi)
 
 
-@pytest.mark.parametrize("mode_name", ["BF16", "BF16X3"])
+def tf32_rna(x):
+    """FP64 -> FP32 (nearest) -> TF32 (11 significant bits, ties away from zero)."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+    mant, ex = np.frexp(f)
+    return np.ldexp(np.sign(mant) * np.floor(np.abs(mant) * 2048.0 + 0.5), ex - 11)
+
+
+def split_tf32(x):
+    hi = tf32_rna(x)
+    return hi, tf32_rna(x - hi)
+
+
+@pytest.mark.parametrize("mode_name", ["BF16", "BF16X3", "TF32", "TF32X3"])
 @pytest.mark.parametrize("m,n,ncols,trans", [
     (300, 200, 20, False), (300, 200, 20, True),      # ragged row tiles and k-blocks
     (1000, 777, 224, False), (777, 1000, 224, True),  # widest N, several tiles
@@ -55,9 +67,10 @@ def test_tensor_core_product(pq, mode_name, m, n, ncols, trans):
     assert rc == pq.PBPQLP_OK, flags
     C = C.cpu().numpy()
     Aop = A.T if trans else A
-    ah, al = split(Aop)
-    yh, yl = split(Y)
-    if mode_name == "BF16":
+    sp = split_tf32 if mode_name.startswith("TF32") else split
+    ah, al = sp(Aop)
+    yh, yl = sp(Y)
+    if mode_name in ("BF16", "TF32"):
         ref = ah @ yh
         mag = np.abs(ah) @ np.abs(yh)
     else:
@@ -93,6 +106,13 @@ def test_split_bf16_factorization_within_1p1_of_oracle(pq):
     # the mixed modes apply the triangular factors in FP32: orthonormal to ~1e-7
     assert np.allclose(Qa.T @ Qa, np.eye(25), atol=1e-6)
     assert np.allclose(Qb.T @ Qb, np.eye(25), atol=1e-6)
+
+
+def test_split_tf32_factorization_within_1p1_of_oracle(pq):
+    A32 = synth.xyt_plus_noise(6, 1700, 1500, 24, 1e-3)
+    e_mixed, e_orc, (Qa, L, Qb) = _mixed_errors(pq, A32, 24, 8, 2, 21, pq.PBPQLP_MODE_TF32X3)
+    assert e_mixed <= 1.1 * e_orc, (e_mixed, e_orc)
+    assert np.array_equal(L, np.tril(L))
 
 
 def test_bf16_single_term_factorization_runs(pq):
