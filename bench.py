@@ -108,11 +108,24 @@ def read_traffic(kernel_file_tag):
     txt = open(path).read()
     mt = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     ms = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
-    src = os.path.join(ROOT, "paper_2103_07245_gb300", "csrc", "kernels_fp64.cu")
-    if not mt or not ms or not os.path.exists(src):
+    cur = kernel_source_hash()
+    if not mt or not ms or cur is None:
         return None
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
     return float(mt.group(1)) if cur.startswith(ms.group(1)) else None
+
+
+def kernel_source_hash():
+    """sha256 of the skinny FP64 GEMM's device body (the kernel the traffic figure belongs to)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2103_07245_gb300", "csrc", "fp64_device.cuh")
+    if not os.path.exists(src):
+        return None
+    txt = open(src).read()
+    a = txt.find("__device__ __forceinline__ void dev_dgemm_tile")
+    b = txt.find("__device__ __forceinline__ int64_t pidx", a)
+    if a < 0 or b < 0:
+        return None
+    return hashlib.sha256(txt[a:b].encode()).hexdigest()
 
 
 class ClockSampler:

@@ -41,6 +41,7 @@ struct MatUnit {
     double* out;         // Gaussian output (rows x l, ld)
     int64_t ld;
     uint64_t seed;
+    int64_t b0, b1;      // Gaussian: Box-Muller pairs [b0, b1) of this matrix's stream
 };
 
 // A block of rows of one panel for the row-wise triangular solve Y = X R^{-1}.

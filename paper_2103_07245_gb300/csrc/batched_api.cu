@@ -34,11 +34,14 @@ enum LaunchKind { L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL
 
 struct Launch {
     int kind;
-    int TN;
+    int TN;                // GEMM: column groups of 16; TRSM: the bucket's largest l
     bool transA;
     size_t off;            // byte offset of the unit list inside the list region
     int n;
 };
+
+constexpr int64_t kGaussPairsPerUnit = 8192;
+constexpr int64_t kPanelRowsPerUnit = 256;
 
 }  // namespace
 
@@ -97,14 +100,18 @@ size_t lists_bound(const pbpqlp_batch_s* B, int gram_chunk_min) {
         // reductions, Cholesky / small QR / Gaussian units, TRSM row blocks
         units += (size_t)(passes * 6 + 2) * sizeof(ReduceUnit);
         units += (size_t)(passes * 6 + 2) * sizeof(MatUnit);
+        units += (size_t)((B->m[i] * B->l[i] / 2 + kGaussPairsPerUnit) / kGaussPairsPerUnit + 1) * sizeof(MatUnit);
         units += (size_t)(passes * 6) * ((std::max(B->m[i], B->n[i]) + 63) / 64) * sizeof(TrsmUnit);
         if (B->nprod) {
             units += 8 * 128;                                                   // tensor maps
             units += (size_t)(passes * ((B->m[i] + 127) / 128 + (B->n[i] + 127) / 128)) * sizeof(TcUnit);
-            units += (size_t)((B->m[i] + 31) / 32) * sizeof(SplitUnit) + (size_t)passes * sizeof(PanelUnit);
+            units += (size_t)((B->m[i] + 31) / 32) * sizeof(SplitUnit);
+            units += (size_t)passes * ((std::max(B->m[i], B->n[i]) + kPanelRowsPerUnit - 1) / kPanelRowsPerUnit) *
+                     sizeof(PanelUnit);
         }
     }
-    return units + 64 * 1024 + 256 * 64;
+    // one list per width bucket: up to 14 GEMM and 7 TRSM buckets per step, 256-byte aligned
+    return units + 64 * 1024 + 256 * 64 + (size_t)(2 * B->q + 2) * 6 * 24 * 256 + 64 * 256;
 }
 
 class ListBuilder {
@@ -119,6 +126,23 @@ class ListBuilder {
         B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size()});
     }
     void memset_ctl() { B_->seq.push_back(Launch{L_MEMSET_CTL, 0, false, 0, 0}); }
+    // GEMM units bucketed by their own width (16-column groups), one launch per bucket
+    void add_gemm(const std::vector<GemmUnit>& units, bool transA) {
+        std::vector<GemmUnit> bucket[kMaxEll / 16 + 1];
+        for (const GemmUnit& g : units) bucket[(g.N + 15) / 16].push_back(g);
+        for (int tn = 1; tn <= kMaxEll / 16; ++tn) add(L_GEMM, bucket[tn], tn, transA);
+    }
+    // triangular-solve units bucketed by 32-column groups of their l
+    void add_trsm(const std::vector<TrsmUnit>& units) {
+        std::vector<TrsmUnit> bucket[kMaxEll / 32 + 2];
+        int lm[kMaxEll / 32 + 2] = {};
+        for (const TrsmUnit& t : units) {
+            const int u = (t.l + 31) / 32;
+            bucket[u].push_back(t);
+            lm[u] = std::max(lm[u], t.l);
+        }
+        for (int u = 1; u <= kMaxEll / 32 + 1; ++u) add(L_TRSM, bucket[u], lm[u]);
+    }
     // raw table at the start of the list region (the tensor maps)
     size_t raw(const void* data, size_t bytes) {
         size_t off = align_up(B_->host_lists.size(), 256);
@@ -148,7 +172,6 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     ListBuilder lb(B);
     const int cnt = B->count;
     const int64_t ldp = B->ldp;
-    const int TN = (B->lmax + 15) / 16;
     uint32_t* status = (uint32_t*)(pt.ws + B->off_status);
     int* ctl = (int*)(pt.ws + B->off_ctl);
 
@@ -184,11 +207,15 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     }
     // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i
     {
-        std::vector<MatUnit> u(cnt);
+        std::vector<MatUnit> u;
         for (int i = 0; i < cnt; ++i) {
-            MatUnit x{};
-            x.l = B->l[i]; x.rows = B->m[i]; x.out = P64(pt, B->mw[i].Xm); x.ld = ldp; x.seed = B->seed + (uint64_t)i;
-            u[i] = x;
+            const int64_t npairs = (B->m[i] * (int64_t)B->l[i] + 1) / 2;
+            for (int64_t b0 = 0; b0 < npairs; b0 += kGaussPairsPerUnit) {
+                MatUnit x{};
+                x.l = B->l[i]; x.rows = B->m[i]; x.out = P64(pt, B->mw[i].Xm); x.ld = ldp;
+                x.seed = B->seed + (uint64_t)i; x.b0 = b0; x.b1 = b0 + kGaussPairsPerUnit;
+                u.push_back(x);
+            }
         }
         lb.add(L_GAUSS, u);
     }
@@ -199,14 +226,18 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
             std::vector<TcUnit> tu;
             for (int i = 0; i < cnt; ++i) {
                 const MatWs& w = B->mw[i];
-                PanelUnit x{};
-                x.Y = ysel(i); x.ldy = ldp; x.N = B->l[i];
-                x.rows = transA ? B->m[i] : B->n[i];
-                x.thi = P32(pt, transA ? w.Bmhi : w.Bnhi);
-                const size_t lo = transA ? w.Bmlo : w.Bnlo;
-                x.tlo = lo ? P32(pt, lo) : nullptr;
-                x.ldt = transA ? w.ldm : w.ldn;
-                pu.push_back(x);
+                const int64_t prow = transA ? B->m[i] : B->n[i];
+                for (int64_t r0 = 0; r0 < prow; r0 += kPanelRowsPerUnit) {
+                    PanelUnit x{};
+                    x.Y = ysel(i); x.ldy = ldp; x.N = B->l[i];
+                    x.r0 = r0;
+                    x.rows = std::min<int64_t>(kPanelRowsPerUnit, prow - r0);
+                    x.thi = P32(pt, transA ? w.Bmhi : w.Bnhi);
+                    const size_t lo = transA ? w.Bmlo : w.Bnlo;
+                    x.tlo = lo ? P32(pt, lo) : nullptr;
+                    x.ldt = transA ? w.ldm : w.ldn;
+                    pu.push_back(x);
+                }
                 const int64_t M = transA ? B->n[i] : B->m[i], K = transA ? B->m[i] : B->n[i];
                 for (int64_t m0 = 0; m0 < M; m0 += 128) {
                     TcUnit t{};
@@ -236,7 +267,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 u.push_back(g);
             }
         }
-        lb.add(L_GEMM, u, TN, transA);
+        lb.add_gemm(u, transA);
     };
     // CholeskyQR passes for every matrix's panel (side 0: m x l panels, side 1: n x l)
     auto orth = [&](int side, auto srcsel, auto xsel, auto ysel) {
@@ -280,10 +311,10 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                     tu.push_back(t);
                 }
             }
-            lb.add(L_GEMM, gu, TN, true);
+            lb.add_gemm(gu, true);
             lb.add(L_REDUCE, ru);
             lb.add(L_CHOL, cu);
-            lb.add(L_TRSM, tu);
+            lb.add_trsm(tu);
         }
     };
     auto Xm = [&](int i) { return P64(pt, B->mw[i].Xm); };
@@ -324,7 +355,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
             r.cond = nullptr;
             ru.push_back(r);
         }
-        lb.add(L_GEMM, gu, TN, true);
+        lb.add_gemm(gu, true);
         lb.add(L_REDUCE, ru);
     }
     {                                       // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7)
@@ -348,7 +379,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 gu.push_back(g);
             }
         }
-        lb.add(L_GEMM, gu, TN, false);
+        lb.add_gemm(gu, false);
         std::vector<ReduceUnit> cu;          // a one-term "reduction" is a strided copy
         for (int i = 0; i < cnt; ++i) {
             ReduceUnit r{};
@@ -386,7 +417,7 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
             case L_GEMM: PBQ_TRY(launch_dgemm_list(L.TN, L.transA, (const GemmUnit*)u, L.n, s)); break;
             case L_REDUCE: PBQ_TRY(launch_reduce_list((const ReduceUnit*)u, L.n, s)); break;
             case L_CHOL: PBQ_TRY(launch_cholesky_list((const MatUnit*)u, L.n, B->lmax, s)); break;
-            case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, B->lmax, s, B->nprod > 0)); break;
+            case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, L.TN, s, B->nprod > 0)); break;
             case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, B->lmax, s)); break;
             case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, s)); break;
             case L_PSPLIT: PBQ_TRY(launch_split_panel_tf32_list((const PanelUnit*)u, L.n, s)); break;

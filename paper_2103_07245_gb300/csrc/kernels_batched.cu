@@ -127,7 +127,11 @@ cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, int lmax, cud
 
 __global__ void __launch_bounds__(256) k_gaussian_list(const MatUnit* __restrict__ units) {
     const MatUnit& u = units[blockIdx.x];
-    dev_gaussian(u.seed, u.rows, u.l, u.out, u.ld, threadIdx.x, blockDim.x);
+    // pairs [b0, b1) of the matrix's stream; the last unit's b1 is the stream end
+    const int64_t npairs = (u.rows * (int64_t)u.l + 1) / 2;
+    const int64_t end = u.b1 < npairs ? u.b1 : npairs;
+    for (int64_t b = u.b0 + threadIdx.x; b < end; b += blockDim.x)
+        dev_gaussian(u.seed, u.rows, u.l, u.out, u.ld, b, npairs);   // one pair (stride past the end)
 }
 
 cudaError_t launch_gaussian_list(const MatUnit* units, int nunits, cudaStream_t s) {

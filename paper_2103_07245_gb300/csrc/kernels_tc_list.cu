@@ -303,10 +303,11 @@ cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, cudaStrea
 
 __global__ void __launch_bounds__(256) k_split_panel_tf32_list(const PanelUnit* __restrict__ units) {
     const PanelUnit u = units[blockIdx.x];
+    // panel rows [r0, r0 + rows) (u.Y, u.thi, u.tlo point at row 0 of the panel)
     const int64_t total = u.rows * (int64_t)u.N;
     for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
         const int j = (int)(e / u.rows);
-        const int64_t r = e - (int64_t)j * u.rows;
+        const int64_t r = u.r0 + (e - (int64_t)j * u.rows);
         const double x = u.Y[r * u.ldy + j];
         const float h = to_tf32((float)x);
         u.thi[(int64_t)j * u.ldt + r] = h;

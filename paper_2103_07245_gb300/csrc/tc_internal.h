@@ -72,12 +72,13 @@ struct SplitUnit {
     int a_f32;
 };
 cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, cudaStream_t s);
-// One panel: Y (rows x N FP64, ld ldy) into transposed TF32 hi/lo (N x rows, ld ldt).
+// A row block of one panel: Y (rows x N FP64, ld ldy) into transposed TF32 hi/lo (N x rows, ld ldt).
 struct PanelUnit {
     const double* Y;
     float *thi, *tlo;
-    int64_t rows, ldy, ldt;
+    int64_t rows, ldy, ldt;   // this unit converts panel rows [r0, r0 + rows)
     int N;
+    int64_t r0;
 };
 cudaError_t launch_split_panel_tf32_list(const PanelUnit* units, int nunits, cudaStream_t s);
 
