@@ -56,6 +56,12 @@ cudaError_t launch_upper_product(int l, int64_t K, const double* A, const double
 cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rpacked, uint32_t* status,
                             int* ctl, int pass, cudaStream_t s);
 
+// The same Cholesky by a cluster of 8 CTAs (rows dealt cyclically, the pivot
+// row shared through distributed shared memory), for l > 128.
+bool cholesky_cluster_fits(int l);
+cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double* Rpacked, uint32_t* status, int* ctl,
+                                    int pass, cudaStream_t s);
+
 // Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels; f32
 // solves in FP32 (the mixed modes) instead of FP64.
 cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rpacked, const double* X, int64_t ldx,

@@ -33,6 +33,7 @@ struct pbpqlp_plan_s {
     int nprod = 0;                      // 1 (BF16) or 3 (split BF16); 0 in FP64 mode
     int fault_stall = 0;                // PBPQLP_FAULT=tc_stall at plan creation (failure-detection test)
     bool tf32 = false;                  // TF32 operands (modes TF32, TF32X3) instead of BF16
+    bool cluster_chol = false;          // Cholesky on an 8-CTA cluster (large l)
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
@@ -197,7 +198,8 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         // the Cholesky reads only the upper triangle of the Gram
         PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
         PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
-        PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
+        if (P->cluster_chol) PBQ_TRY(launch_cholesky_cluster(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
+        else PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s, P->nprod > 0));
     }
     return PBPQLP_OK;
@@ -242,6 +244,10 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
     P->seed = seed; P->mode = mode; P->stream = (cudaStream_t)stream;
     P->ldp = round_up(P->l, 8);
+    {
+        const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
+        P->cluster_chol = cholesky_cluster_fits(P->l) && !(nc && nc[0] == '1');
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
         int sms = 0;
