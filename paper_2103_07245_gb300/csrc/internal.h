@@ -73,6 +73,10 @@ cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rpacked, const d
 // shared memory, l <= 121).
 cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, double* work, cudaStream_t s);
 
+// The same QR by an 8-CTA cluster (columns dealt cyclically), for l > 128.
+bool small_qr_cluster_fits(int l);
+cudaError_t launch_small_qr_cluster(int l, const double* R, double* L, double* Ptil, cudaStream_t s);
+
 // Zero the strictly-lower part of an l x l matrix (ld l) in place.
 cudaError_t launch_triu(int l, double* R, cudaStream_t s);
 

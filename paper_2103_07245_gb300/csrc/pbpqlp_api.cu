@@ -372,7 +372,8 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s, true));
     }
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
-    PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
+    if (P->cluster_chol && small_qr_cluster_fits(l)) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
+    else PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
     PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
     PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
     return PBPQLP_OK;

@@ -80,7 +80,9 @@ def test_config1_parity(pq):
     (97, 1500, 30, 10, 1),    # wide
     (64, 64, 1, 0, 1),        # l = 1
     (130, 70, 60, 10, 1),     # l = min(m, n) = 70
-    (700, 650, 200, 24, 1),   # l = 224 (largest)
+    (700, 650, 200, 24, 1),   # l = 224 (largest; cluster Cholesky and QR)
+    (600, 500, 120, 11, 1),   # l = 131: cluster kernels, uneven rows per CTA
+    (900, 800, 200, 17, 2),   # l = 217: cluster kernels, uneven rows per CTA
     (2049, 1031, 100, 17, 2), # l = 117, ragged tails everywhere
 ])
 def test_parity_shapes(pq, m, n, k, p, q):
