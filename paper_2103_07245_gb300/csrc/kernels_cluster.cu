@@ -313,7 +313,7 @@ k_small_qr_cluster(int l, const double* __restrict__ R, double* __restrict__ L, 
 
 bool small_qr_cluster_fits(int l) {
     const int nloc = (l + kClusterCtas - 1) / kClusterCtas;
-    return l > 128 && ((int64_t)2 * nloc * l + 2 * (int64_t)l) * (int64_t)sizeof(double) <= 200 * 1024;
+    return l > 64 && ((int64_t)2 * nloc * l + 2 * (int64_t)l) * (int64_t)sizeof(double) <= 200 * 1024;
 }
 
 cudaError_t launch_small_qr_cluster(int l, const double* R, double* L, double* Ptil, cudaStream_t s) {

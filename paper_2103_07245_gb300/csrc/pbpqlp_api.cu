@@ -33,7 +33,8 @@ struct pbpqlp_plan_s {
     int nprod = 0;                      // 1 (BF16) or 3 (split BF16); 0 in FP64 mode
     int fault_stall = 0;                // PBPQLP_FAULT=tc_stall at plan creation (failure-detection test)
     bool tf32 = false;                  // TF32 operands (modes TF32, TF32X3) instead of BF16
-    bool cluster_chol = false;          // Cholesky on an 8-CTA cluster (large l)
+    bool cluster_chol = false;          // Cholesky on an 8-CTA cluster (l > 128)
+    bool cluster_qr = false;            // small QR on an 8-CTA cluster (l > 64)
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
@@ -247,6 +248,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     {
         const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
         P->cluster_chol = cholesky_cluster_fits(P->l) && !(nc && nc[0] == '1');
+        P->cluster_qr = small_qr_cluster_fits(P->l) && !(nc && nc[0] == '1');
     }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -372,7 +374,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s, true));
     }
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
-    if (P->cluster_chol && small_qr_cluster_fits(l)) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
+    if (P->cluster_qr) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
     else PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
     PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
     PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
