@@ -1,13 +1,6 @@
-// Cholesky of the l x l CholeskyQR Gram by a thread-block cluster (8 CTAs on
-// 8 SMs) for large l, where one SM's FP64 rate (2 lanes per clock on GB300)
-// makes the one-CTA kernel the bottleneck.
-//
-// Rows of the packed upper triangle are dealt cyclically: row a lives in the
-// shared memory of CTA a % C.  Step j copies the finished pivot row j from its
-// owner through distributed shared memory, every CTA updates its own rows
-// (S_ab -= R_ja R_jb), and the owner of row j + 1 finishes that row (pivot,
-// sqrt, one reciprocal, row scaling) before the step's cluster barrier.  The
-// arithmetic, thresholds and shifted retry are those of the one-CTA kernel.
+// Cholesky of the l x l CholeskyQR Gram and Householder QR of R^T (Eq. 7) by
+// a thread-block cluster (8 CTAs on 8 SMs) for large l, where one SM's FP64
+// rate (2 lanes per clock on GB300) makes the one-CTA kernels the bottleneck.
 #include <cooperative_groups.h>
 #include <cmath>
 #include <cstdint>
@@ -21,13 +14,17 @@ namespace pbq {
 namespace {
 constexpr int kClusterCtas = 8;
 constexpr int kClusterThreads = 512;
-
-// First packed entry of local row la (global row la*C + rank) in a CTA's store.
-__device__ __forceinline__ int64_t lrow_start(int l, int C, int rank, int la) {
-    return (int64_t)la * (l - rank) - (int64_t)C * la * (la - 1) / 2;
-}
+constexpr int kCholNb = 16;   // rows per block of the blocked Cholesky
 }  // namespace
 
+// Blocked right-looking Cholesky G = R^T R by the cluster.  Blocks of 16 rows
+// are dealt cyclically (block t lives in CTA t % C; each owned row is stored at
+// full length l in shared memory, row a at local row (t / C) * 16 + a % 16).
+// The owner of block t factors its 16 rows completely (pivots, scaling and the
+// in-block updates, with block barriers only); after one cluster barrier every
+// CTA copies that block row through distributed shared memory and applies the
+// rank-16 update S_ab -= sum_i R_ia R_ib to its own later rows.  One cluster
+// barrier per block.  Thresholds and the shifted retry follow the one-CTA kernel.
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
 k_cholesky_cluster(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
                    uint32_t* __restrict__ status, int* __restrict__ ctl, int pass) {
@@ -35,90 +32,113 @@ k_cholesky_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
+    const int nblk = (l + kCholNb - 1) / kCholNb;
+    const int nbmax = (nblk + C - 1) / C;                    // blocks per CTA (same layout everywhere)
     extern __shared__ double smc[];
-    const int nloc = (l - rank + C - 1) / C;                 // rows this CTA owns
-    const int64_t nstore = lrow_start(l, C, rank, nloc);
-    double* S = smc;                                         // own rows, packed
-    double* rowj = S + nstore;                               // copy of the current pivot row (l doubles)
-    double* dinv = rowj + l;                                 // 1/diag of own rows (nloc)
+    double* S = smc;                                         // nbmax*16 rows x l
+    double* Rb = S + (int64_t)nbmax * kCholNb * l;           // copy of the current block row (16 x l)
+    double* dinv = Rb + (int64_t)kCholNb * l;                // 1/diag of own rows (nbmax*16)
     __shared__ int s_fail;
-    __shared__ double s_shift;
+    __shared__ double s_shift, s_inv;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const double tau = 1e-12;
+    auto lrow = [&](int a) { return ((a / kCholNb) / C) * kCholNb + (a % kCholNb); };
 
     if (tid == 0) { s_fail = 0; s_shift = 0.0; }
     __syncthreads();
     int shifted = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const double shift = s_shift;
-        for (int la = warp; la < nloc; la += nwarp) {
-            const int a = la * C + rank;
-            const int64_t ra = lrow_start(l, C, rank, la) - a;   // index of (a, b) is ra + b
-            for (int b = a + lane; b < l; b += 32) S[ra + b] = G[(int64_t)a * l + b] + (a == b ? shift : 0.0);
-        }
+        for (int t = rank; t < nblk; t += C)
+            for (int r = warp; r < kCholNb; r += nwarp) {
+                const int a = t * kCholNb + r;
+                if (a >= l) continue;
+                double* sa = S + (int64_t)lrow(a) * l;
+                for (int b = a + lane; b < l; b += 32) sa[b] = G[(int64_t)a * l + b] + (a == b ? shift : 0.0);
+            }
         if (tid == 0) s_fail = 0;
         __syncthreads();
-        // finish pivot row i (owned here): lane 0 of warp 0 takes the pivot, the warp scales
-        auto finish_row = [&](int i) {
-            const int li = i / C;
-            const int64_t ri = lrow_start(l, C, rank, li) - i;
-            double inv = 0.0;
-            int f = 0;
-            if (lane == 0) {
-                const double d = S[ri + i];
-                const double thr = (attempt == 0) ? tau * G[(int64_t)i * l + i] : 0.0;
-                f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
-                if (f) s_fail = f;
-                else {
-                    const double r = sqrt(d);
-                    S[ri + i] = r;
-                    inv = 1.0 / r;
-                    dinv[li] = inv;
+        // factor the 16 rows of own block t: pivots, scaling, in-block updates
+        auto factor_block = [&](int t) {
+            const int a0 = t * kCholNb, a1 = min(l, a0 + kCholNb);
+            for (int i = a0; i < a1; ++i) {
+                double* si = S + (int64_t)lrow(i) * l;
+                if (tid == 0) {
+                    const double d = si[i];
+                    const double thr = (attempt == 0) ? tau * G[(int64_t)i * l + i] : 0.0;
+                    const int f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
+                    if (f) s_fail = f;
+                    else {
+                        const double rr = sqrt(d);
+                        si[i] = rr;
+                        s_inv = 1.0 / rr;
+                        dinv[lrow(i)] = s_inv;
+                    }
                 }
+                __syncthreads();
+                if (s_fail) return;
+                const double inv = s_inv;
+                for (int c = i + 1 + tid; c < l; c += nth) si[c] *= inv;
+                __syncthreads();
+                for (int a = i + 1 + warp; a < a1; a += nwarp) {
+                    double* sa = S + (int64_t)lrow(a) * l;
+                    const double ria = si[a];
+                    for (int b = a + lane; b < l; b += 32) sa[b] -= ria * si[b];
+                }
+                __syncthreads();
             }
-            f = __shfl_sync(0xffffffffu, f, 0);
-            inv = __shfl_sync(0xffffffffu, inv, 0);
-            if (!f)
-                for (int c = i + 1 + lane; c < l; c += 32) S[ri + c] *= inv;
-            __syncwarp();
         };
-        if (rank == 0 && warp == 0) finish_row(0);
+        if (rank == 0) factor_block(0);
         cluster.sync();
         int fail = 0;
-        for (int j = 0; j < l; ++j) {
-            const int owner = j % C;
-            // a failed pivot stops every CTA at the same step
-            const int* ofail = cluster.map_shared_rank(&s_fail, owner);
-            fail = *ofail;
+        for (int t = 0; t < nblk; ++t) {
+            const int owner = t % C;
+            fail = *cluster.map_shared_rank(&s_fail, owner);
             if (fail) break;
-            const double* orow = cluster.map_shared_rank(S, owner) + (lrow_start(l, C, owner, j / C) - j);
-            for (int b = j + tid; b < l; b += nth) rowj[b] = orow[b];
-            __syncthreads();
-            for (int la = warp; la < nloc; la += nwarp) {
-                const int a = la * C + rank;
-                if (a <= j) continue;
-                const double rja = rowj[a];
-                const int64_t ra = lrow_start(l, C, rank, la) - a;
-                for (int b = a + lane; b < l; b += 32) S[ra + b] -= rja * rowj[b];
+            const int a0 = t * kCholNb, a1 = min(l, a0 + kCholNb), nb = a1 - a0;
+            // copy block row t (rows a0..a1-1, columns >= a0) from its owner
+            const double* orows = cluster.map_shared_rank(S, owner) + (int64_t)((t / C) * kCholNb) * l;
+            for (int e = tid; e < nb * (l - a0); e += nth) {
+                const int r = e / (l - a0), b = a0 + e % (l - a0);
+                Rb[(int64_t)r * l + b] = orows[(int64_t)r * l + b];
             }
             __syncthreads();
-            if (j + 1 < l && (j + 1) % C == rank && warp == 0) finish_row(j + 1);
+            // rank-nb update of own rows a >= a1
+            for (int u = rank; u < nblk; u += C)
+                for (int r = warp; r < kCholNb; r += nwarp) {
+                    const int a = u * kCholNb + r;
+                    if (a < a1 || a >= l) continue;
+                    double* sa = S + (int64_t)lrow(a) * l;
+                    double ra[kCholNb];
+#pragma unroll
+                    for (int i = 0; i < kCholNb; ++i) ra[i] = (i < nb) ? Rb[(int64_t)i * l + a] : 0.0;
+                    for (int b = a + lane; b < l; b += 32) {
+                        double acc = sa[b];
+#pragma unroll
+                        for (int i = 0; i < kCholNb; ++i)
+                            if (i < nb) acc -= ra[i] * Rb[(int64_t)i * l + b];
+                        sa[b] = acc;
+                    }
+                }
+            __syncthreads();
+            if (t + 1 < nblk && (t + 1) % C == rank) factor_block(t + 1);
             cluster.sync();
         }
         __syncthreads();
         if (!fail) break;
         if (fail == 2 || attempt == 1) {
             if (rank == 0 && tid == 0) atomicOr(status, fail == 2 ? kStNonFinite : kStBreakdown);
-            for (int la = warp; la < nloc; la += nwarp) {
-                const int a = la * C + rank;
-                const int64_t ra = lrow_start(l, C, rank, la) - a;
-                for (int b = a + lane; b < l; b += 32) S[ra + b] = (a == b) ? 1.0 : 0.0;
-            }
-            for (int la = tid; la < nloc; la += nth) dinv[la] = 1.0;
+            for (int t = rank; t < nblk; t += C)
+                for (int r = warp; r < kCholNb; r += nwarp) {
+                    const int a = t * kCholNb + r;
+                    if (a >= l) continue;
+                    double* sa = S + (int64_t)lrow(a) * l;
+                    for (int b = a + lane; b < l; b += 32) sa[b] = (a == b) ? 1.0 : 0.0;
+                    if (lane == 0) dinv[lrow(a)] = 1.0;
+                }
             __syncthreads();
             break;
         }
-        // shifted retry on G + s I (every CTA computes the same shift from G's diagonal)
         if (tid == 0) {
             double tr = 0.0;
             for (int j = 0; j < l; ++j) tr += G[(int64_t)j * l + j];
@@ -131,13 +151,15 @@ k_cholesky_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     }
     // own rows to the global packed layout (index a(2l - a + 1)/2 + (b - a)) and 1/diag
     const int64_t P = (int64_t)l * (l + 1) / 2;
-    for (int la = warp; la < nloc; la += nwarp) {
-        const int a = la * C + rank;
-        const int64_t ra = lrow_start(l, C, rank, la) - a;
-        const int64_t ga = (int64_t)a * (2 * l - a + 1) / 2 - a;
-        for (int b = a + lane; b < l; b += 32) Rp[ga + b] = S[ra + b];
-        if (lane == 0) Rp[P + a] = dinv[la];
-    }
+    for (int t = rank; t < nblk; t += C)
+        for (int r = warp; r < kCholNb; r += nwarp) {
+            const int a = t * kCholNb + r;
+            if (a >= l) continue;
+            const double* sa = S + (int64_t)lrow(a) * l;
+            const int64_t ga = (int64_t)a * (2 * l - a + 1) / 2 - a;
+            for (int b = a + lane; b < l; b += 32) Rp[ga + b] = sa[b];
+            if (lane == 0) Rp[P + a] = dinv[lrow(a)];
+        }
     if (rank == 0 && tid == 0) {
         ctl[pass] = shifted;
         if ((pass & 1) == 0) ctl[8 + pass / 2 + 1] = (ctl[pass - 1] | ctl[pass]) ? 1 : 0;
@@ -146,24 +168,23 @@ k_cholesky_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-bool cholesky_cluster_fits(int l) {
-    const int nloc = (l + kClusterCtas - 1) / kClusterCtas;
-    const int64_t store = (int64_t)nloc * l + 2 * (int64_t)l + 64;
-    return l > 128 && store * (int64_t)sizeof(double) <= 200 * 1024;
+static size_t chol_cluster_smem(int l) {
+    const int nblk = (l + kCholNb - 1) / kCholNb;
+    const int nbmax = (nblk + kClusterCtas - 1) / kClusterCtas;
+    return ((size_t)nbmax * kCholNb * l + (size_t)kCholNb * l + (size_t)nbmax * kCholNb) * sizeof(double);
 }
+
+bool cholesky_cluster_fits(int l) { return l > 64 && chol_cluster_smem(l) <= 200 * 1024; }
 
 cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double* Rp, uint32_t* status, int* ctl,
                                     int pass, cudaStream_t s) {
-    // rank 0 stores the most: ceil(l/C) rows of at most l entries (bounded loosely), + rowj + dinv
-    const int nloc = (l + kClusterCtas - 1) / kClusterCtas;
-    const size_t smem = ((size_t)nloc * l + 2 * (size_t)l + 64) * sizeof(double);
+    const size_t smem = chol_cluster_smem(l);
     cudaError_t e = cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_cholesky_cluster<<<kClusterCtas, kClusterThreads, smem, s>>>(l, rows, G, Rp, status, ctl, pass);
     count_launches(1);
     return cudaGetLastError();
 }
-
 
 // ---------------------------------------------------------------------------
 // Householder QR of W = R^T (Eq. 7) by an 8-CTA cluster, for large l.
