@@ -112,7 +112,10 @@ int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
 
 /*
  * Algorithm 3: factor A ~= Qa L Qb^T.
- *   A         : device, m x n, row-major, leading dimension lda >= n,
+ *   A         : device memory, or pinned host memory the device can address
+ *               (out-of-core: every pass then streams A over the host link;
+ *               the FP64 passes need ~8 bytes per 2 l flops, far below
+ *               NVLink-C2C bandwidth), m x n, row-major, leading dimension lda >= n,
  *               element type a_dtype (PBPQLP_F64 in MODE_FP64; PBPQLP_F32 or
  *               PBPQLP_F64 in the mixed modes, which split A into BF16 hi/lo
  *               copies in the workspace once per call).
@@ -161,6 +164,20 @@ int pbpqlp_error(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
                  const double* Qa, const double* L, const double* Qb, int r,
                  int method, int nprobes, uint64_t probe_seed,
                  void* workspace, size_t ws_bytes, double* rel_err);
+
+/*
+ * Rank-revealing outputs of a factorization (Section IV-C: the diagonal of L
+ * approximates sigma_1..sigma_l; Section V-D: |L_11| estimates ||A||_2, and
+ * Theorem 7 bounds sigma_min(L_11) <= sigma_k).
+ *   L        : device, l x l factor from pbpqlp_factor.
+ *   lvalues  : device output, l doubles: |L_ii|.
+ *   *norm2_est (host): |L_11| (never above ||A||_2: |L_11| <= sigma_1(L) <= sigma_1(A)).
+ *   *rank_est  (host): number of i with |L_ii| > tol |L_11| (numerical rank at
+ *               relative tolerance tol >= 0).
+ * Synchronous; uses the workspace for two scalars.
+ */
+int pbpqlp_rank_revealing(pbpqlp_plan_t plan, const double* L, double tol, double* lvalues,
+                          void* workspace, size_t ws_bytes, double* norm2_est, int* rank_est);
 
 /*
  * Wait for the plan's stream and return the latched device status of the

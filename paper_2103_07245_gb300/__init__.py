@@ -126,6 +126,9 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_propose.restype = ci
     L.pbpqlp_factor_static.argtypes = [vp, vp, i64, ci, vp, vp, vp, vp]
     L.pbpqlp_factor_static.restype = ci
+    L.pbpqlp_rank_revealing.argtypes = [vp, vp, ctypes.c_double, vp, vp, sz, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ci)]
+    L.pbpqlp_rank_revealing.restype = ci
     L.pbpqlp_set_timing.argtypes = [vp, ci]
     L.pbpqlp_set_timing.restype = ci
     L.pbpqlp_read_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -269,6 +272,15 @@ def pbpqlp_propose(features, count, params, q_out, p_index_out, workspace, ws_by
                                  _ptr(workspace), int(ws_bytes), _stream(stream)), "pbpqlp_propose")
 
 
+def pbpqlp_rank_revealing(plan, L, tol, lvalues, workspace, ws_bytes):
+    """Returns (norm2 estimate |L_11|, numerical rank at tol); |L_ii| land in lvalues."""
+    nrm = ctypes.c_double(0.0)
+    rk = ctypes.c_int(0)
+    _check(load().pbpqlp_rank_revealing(plan, _ptr(L), float(tol), _ptr(lvalues), _ptr(workspace), int(ws_bytes),
+                                        ctypes.byref(nrm), ctypes.byref(rk)), "pbpqlp_rank_revealing")
+    return nrm.value, int(rk.value)
+
+
 def pbpqlp_set_timing(plan, enable):
     _check(load().pbpqlp_set_timing(plan, 1 if enable else 0), "pbpqlp_set_timing")
 
@@ -370,7 +382,8 @@ class Plan:
     def factor(self, A, omega=None, out=None):
         import torch
         a_dtype = PBPQLP_F32 if A.dtype == torch.float32 else PBPQLP_F64
-        Qa, L, Qb = out if out is not None else self.outputs(A.device)
+        # outputs live on the plan's device even when A is pinned host memory
+        Qa, L, Qb = out if out is not None else self.outputs(self.workspace.device)
         pbpqlp_factor(self.handle, A, A.stride(0), a_dtype, self.workspace, self.ws_bytes, omega, Qa, L, Qb)
         return Qa, L, Qb
 
@@ -406,6 +419,13 @@ class Plan:
 
     def sync_status(self):
         return pbpqlp_sync_status(self.handle)
+
+    def rank_revealing(self, L, tol=1e-8):
+        """(L-values tensor, ||A||_2 estimate, numerical rank at tol)."""
+        import torch
+        lv = torch.empty(self.l, dtype=torch.float64, device=L.device)
+        nrm, rk = pbpqlp_rank_revealing(self.handle, L, tol, lv, self.workspace, self.ws_bytes)
+        return lv, nrm, rk
 
     def __del__(self):
         h = getattr(self, "handle", None)

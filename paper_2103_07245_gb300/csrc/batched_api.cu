@@ -598,8 +598,14 @@ int pbpqlp_factor_batched(pbpqlp_batch_t B, const void* const* A, const int64_t*
     if (!B || !A || !lda || !Qa || !L || !Qb) return PBPQLP_EINVAL;
     if (B->nprod ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
     if (!workspace || ws_bytes < B->total || ((uintptr_t)workspace & 255u)) return PBPQLP_EWORKSPACE;
-    for (int i = 0; i < B->count; ++i)
+    for (int i = 0; i < B->count; ++i) {
         if (!A[i] || !Qa[i] || !L[i] || !Qb[i] || lda[i] < B->n[i]) return PBPQLP_EINVAL;
+        // device, managed, or pinned host memory mapped at the same address
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, A[i]) != cudaSuccess) { cudaGetLastError(); return PBPQLP_EINVAL; }
+        if (at.type == cudaMemoryTypeUnregistered || (at.type == cudaMemoryTypeHost && at.devicePointer != A[i]))
+            return PBPQLP_EINVAL;
+    }
     B->last_ws = workspace;
     if (B->a_f32 != (a_dtype == PBPQLP_F32)) { B->a_f32 = a_dtype == PBPQLP_F32; B->key.clear(); }
     Ptrs pt{(char*)workspace, A, lda, Qa, L, Qb};

@@ -95,6 +95,9 @@ cudaError_t launch_sumsq(int64_t rows, int64_t cols, const void* X, int x_f32, i
 // out[0] = sum of part[0..n) in index order (one CTA).
 cudaError_t launch_sum(int n, const double* part, double* out, cudaStream_t s);
 
+// L-values |L_ii| into lv (l), out2[0] = |L_11|, out2[1] = #{i : |L_ii| > tol |L_11|} (as a double).
+cudaError_t launch_lvalues(int l, const double* L, double tol, double* lv, double* out2, cudaStream_t s);
+
 // Copy a rows x cols FP64 block between leading dimensions.
 cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
                    cudaStream_t s);

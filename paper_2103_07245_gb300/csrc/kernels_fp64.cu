@@ -387,6 +387,30 @@ cudaError_t launch_sumsq(int64_t rows, int64_t cols, const void* X, int x_f32, i
     return launch_sum((int)nb, part, out, s);
 }
 
+// L-values |L_ii|, the 2-norm estimate |L_11| and the count of |L_ii| > tol |L_11|.
+__global__ void k_lvalues(int l, const double* __restrict__ L, double tol, double* __restrict__ lv,
+                          double* __restrict__ out2) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const double l11 = fabs(L[0]);
+    int c = 0;
+    for (int i = threadIdx.x; i < l; i += blockDim.x) {
+        const double d = fabs(L[(int64_t)i * l + i]);
+        lv[i] = d;
+        c += (d > tol * l11) ? 1 : 0;
+    }
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) { out2[0] = l11; out2[1] = (double)cnt; }
+}
+
+cudaError_t launch_lvalues(int l, const double* L, double tol, double* lv, double* out2, cudaStream_t s) {
+    k_lvalues<<<1, 256, 0, s>>>(l, L, tol, lv, out2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
                    cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;

@@ -206,6 +206,20 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
     return PBPQLP_OK;
 }
 
+// A must be addressable by the device at the given address: device or managed
+// memory, or pinned host memory mapped at the same address (out-of-core A).
+// Anything else (pageable host memory) is rejected before any launch.
+int check_device_addressable(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return PBPQLP_EINVAL;
+    }
+    if (at.type == cudaMemoryTypeUnregistered) return PBPQLP_EINVAL;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer != p) return PBPQLP_EINVAL;
+    return PBPQLP_OK;
+}
+
 int check_ws(pbpqlp_plan_t P, void* ws, size_t ws_bytes) {
     if (!ws || ws_bytes < P->total || ((uintptr_t)ws & 255u) != 0) return PBPQLP_EWORKSPACE;
     return PBPQLP_OK;
@@ -337,6 +351,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
+    if ((rc = check_device_addressable(Av))) return rc;
     P->last_ws = workspace;
     const Ws w = carve(P, workspace);
     cudaStream_t s = P->stream;
@@ -390,6 +405,7 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
+    if ((rc = check_device_addressable(A))) return rc;
     P->last_ws = workspace;
     const Ws w = carve(P, workspace);
     cudaStream_t s = P->stream;
@@ -439,6 +455,7 @@ int pbpqlp_error(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, const
     if (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) return PBPQLP_EINVAL;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
+    if ((rc = check_device_addressable(A))) return rc;
     const Ws w = carve(P, workspace);
     cudaStream_t s = P->stream;
     const int l = P->l;
@@ -481,6 +498,22 @@ int pbpqlp_error(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, const
         return PBPQLP_EINVAL;
     }
     if (!std::isfinite(*rel_err)) return PBPQLP_ENONFINITE;
+    return PBPQLP_OK;
+}
+
+int pbpqlp_rank_revealing(pbpqlp_plan_t P, const double* L, double tol, double* lvalues, void* workspace,
+                          size_t ws_bytes, double* norm2_est, int* rank_est) {
+    if (!P || !L || !lvalues || !norm2_est || !rank_est || !(tol >= 0.0)) return PBPQLP_EINVAL;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    PBQ_TRY(launch_lvalues(P->l, L, tol, lvalues, w.scal, s));
+    double host[2] = {0.0, 0.0};
+    PBQ_TRY(cudaMemcpyAsync(host, w.scal, sizeof(host), cudaMemcpyDeviceToHost, s));
+    PBQ_TRY(cudaStreamSynchronize(s));
+    *norm2_est = host[0];
+    *rank_est = (int)host[1];
     return PBPQLP_OK;
 }
 

@@ -176,3 +176,52 @@ def test_config2_full_size_parity(pq):
     ref = oracle.pbpqlp(A_np, 110, 2, seed=3)
     g = _np(Qa, L, Qb)
     assert _parity(A_np, g, ref, 100) <= TOL
+
+
+def test_rank_revealing_outputs(pq):
+    """L-values, ||A||_2 estimate and numerical rank (Sections IV-C, V-D)."""
+    import torch
+    # norm estimate on a decaying spectrum: below sigma_1, and within 1e-3 of it with q = 2
+    A_np = synth.poly_decay(12, 400, 300, 1.0)
+    plan, A, out, rc, flags = _run(pq, A_np, 10, 5, 2, seed=6)
+    assert rc == pq.PBPQLP_OK
+    Qa, L, Qb = out
+    lv, nrm, rk = plan.rank_revealing(L, tol=1e-6)
+    s = np.linalg.svd(A_np, compute_uv=False)
+    assert np.array_equal(lv.cpu().numpy(), np.abs(np.diag(L.cpu().numpy())))
+    ref = oracle.pbpqlp(A_np, 15, 2, seed=6)
+    assert abs(nrm - abs(ref["L"][0, 0])) <= 1e-12 * s[0]      # the estimate the algorithm defines
+    assert nrm <= s[0] * (1 + 1e-12) and nrm >= 0.98 * s[0]
+    # numerical rank of a rank-13 matrix plus 1e-10 noise
+    rng = np.random.default_rng(3)
+    B_np = synth.rank_r(8, 400, 300, 13) + 1e-10 * rng.standard_normal((400, 300))
+    plan, B, out, rc, flags = _run(pq, B_np, 20, 5, 2, seed=6)
+    lv, nrm, rk = plan.rank_revealing(out[1], tol=1e-6)
+    assert rk == 13
+    assert nrm <= np.linalg.svd(B_np, compute_uv=False)[0] * (1 + 1e-12)
+
+
+def test_out_of_core_A_in_pinned_host_memory(pq):
+    """A left in pinned host memory: the passes read it over the host link and
+    the factors are bitwise those of a device-resident A."""
+    import torch
+    A_np = synth.poly_decay(17, 900, 700, 1.5)
+    A_host = torch.from_numpy(A_np).pin_memory()
+    A_dev = A_host.cuda()
+    for mode in (pq.PBPQLP_MODE_FP64, pq.PBPQLP_MODE_BF16X3):
+        plan = pq.Plan(900, 700, 20, 8, 2, seed=4, mode=mode)
+        ref = [t.cpu() for t in plan.factor(A_dev)]
+        got = [t.cpu() for t in plan.factor(A_host)]
+        rc, flags = plan.sync_status()
+        assert rc == pq.PBPQLP_OK, flags
+        for a, b in zip(ref, got):
+            assert torch.equal(a, b)
+
+
+def test_pageable_host_A_is_rejected_before_any_launch(pq):
+    import torch
+    A = torch.from_numpy(synth.poly_decay(1, 200, 150, 1.0))      # pageable host memory
+    plan = pq.Plan(200, 150, 10, 5, 1, seed=1)
+    with pytest.raises(pq.PbpqlpError) as e:
+        plan.factor(A)
+    assert e.value.status == pq.PBPQLP_EINVAL

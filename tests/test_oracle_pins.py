@@ -310,3 +310,15 @@ def test_oracle_mlp_closed_forms():
     p = np.zeros(mlp.PARAMS)
     loss, _ = mlp.loss_grad(p, np.ones((4, mlp.IN)), [0, 1, 2, 3], [0, 1, 2, 0])
     assert abs(loss - (np.log(5) + np.log(3))) < 1e-12
+
+
+def test_l11_estimates_two_norm_from_below(orc):
+    """Section V-D: |L_11| estimates ||A||_2; it can never exceed it
+    (|L_11| <= sigma_1(L) <= sigma_1(A)) and with q = 2 it is within 1e-3."""
+    for seed in range(3):
+        A = synth.poly_decay(300 + seed, 200, 150, 1.0)
+        s1 = _sv(A)[0]
+        for q in (0, 1, 2):
+            o = orc.pbpqlp(A, 12, q, seed=seed)
+            assert abs(o["L"][0, 0]) <= s1 * (1 + 1e-13)
+        assert abs(o["L"][0, 0]) >= (1 - 1e-3) * s1
