@@ -443,6 +443,7 @@ def main():
     ap.add_argument("--workload", default="fp64_8000", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-out-of-core", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -573,6 +574,24 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+
+    # ---- out of core: A left in pinned host memory, streamed over the host link every pass
+    if w["mode"] == "FP64" and not args.no_out_of_core:
+        ooc_out = plan.outputs(dev)
+        for _ in range(1):
+            plan.factor(A_host, out=ooc_out)
+        torch.cuda.synchronize(dev)
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(args.steps):
+            plan.factor(A_host, out=ooc_out)
+        o1.record(stream)
+        torch.cuda.synchronize(dev)
+        oms = dist_max(o0.elapsed_time(o1) / args.steps, dev)
+        line["out_of_core"] = {"value": whole_job_rate(1, world, oms), "unit": UNIT, "ms_per_step": oms,
+                               "bitwise_equal": bool(all(torch.equal(a, b) for a, b in zip(ooc_out, (Qa, L, Qb)))),
+                               "note": "A in pinned host memory, read by the kernels over the host link each pass"}
 
     # ---- the same matrix in the mixed mode: speed at (near) equal relative error
     if w.get("compare"):

@@ -255,3 +255,64 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
     return {"fixed_success": float(ok_fixed.mean()), "proposer_success": float(ok_prop.mean()),
             "fixed_passes": float(2 * FIXED[0] + 2), "proposer_passes": float(np.mean(passes)),
             "fallback_rate": float(np.mean(fallback)), "proposals": list(zip(qs, ps))}
+
+
+def main(argv=None):
+    """Generate labelled matrices, train on the GPU, evaluate against fixed (2, 10).
+
+    python -m paper_2103_07245_gb300.proposer --chunks 16 --chunk 128 --eval 128 \
+        --save weights.npz --json summary.json
+    """
+    import argparse
+    import json
+    import time
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--chunks", type=int, default=8)
+    ap.add_argument("--chunk", type=int, default=96)
+    ap.add_argument("--max-dim", type=int, default=2048)
+    ap.add_argument("--eval", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--save", default=None)
+    ap.add_argument("--json", default=None)
+    args = ap.parse_args(argv)
+    pq.load(build_if_missing=True)
+    t0 = time.time()
+    F_all, yq_all, yp_all = [], [], []
+    for c in range(args.chunks):
+        As, ks, tails = make_matrices(1000 * args.seed + c, args.chunk, m_range=(512, args.max_dim))
+        F, err, yq, yp = label(As, ks, tails, seed=c)
+        F_all.append(F)
+        yq_all.append(yq)
+        yp_all.append(yp)
+        del As
+    t_label = time.time() - t0
+    F = torch.cat(F_all)
+    yq = np.concatenate(yq_all)
+    yp = np.concatenate(yp_all)
+    prop = Proposer(seed=args.seed + 1)
+    hist = train(prop, F, yq, yp, epochs=args.epochs, batch=128, lr=2e-3, seed=args.seed)
+    t_train = time.time() - t0 - t_label
+    if args.save:
+        prop.save(args.save)
+    As, ks, tails = make_matrices(999_000 + args.seed, args.eval, fixed=(2048, 2048, 64), eval_mix=True)
+    res = evaluate(prop, As, ks, tails)
+    props = res.pop("proposals")
+    res.update({"train_matrices": int(F.shape[0]), "eval_matrices": args.eval, "loss_first": hist[0],
+                "loss_last": hist[-1], "label_q_hist": np.bincount(yq, minlength=5).tolist(),
+                "label_p_hist": np.bincount(yp, minlength=3).tolist(),
+                "proposed_q_hist": np.bincount([q for q, _ in props], minlength=5).tolist(),
+                "seconds_label": t_label, "seconds_train": t_train, "seconds_total": time.time() - t0})
+    out = json.dumps(res)
+    print(out, flush=True)
+    if args.json:
+        with open(args.json, "w") as f:
+            f.write(out + "\n")
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())
