@@ -31,7 +31,7 @@ UNIT = "factorizations/s"
 
 WORKLOADS = {
     "fp64_8000": dict(m=8000, n=8000, k=100, p=10, q=2, gen="svd", spectrum="exp", scale=40.0, rank_cap=1500,
-                      mode="FP64", compare="BF16X3",
+                      mode="FP64", compare="BF16X3", emulated=True,
                       desc="plain FP64, A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
     "bf16x3_20000": dict(m=20000, n=20000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
                          compare=None,
@@ -95,6 +95,31 @@ def tc_roofline(rows, K, l, nprod, avg_ms, hbm_peak, tc_peak):
             "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak,
             "achieved_basis": "tensor-pipe MMA flops (%d MMAs per product, N padded to %d)" % (nprod, bn)
             if tensor else "bytes of the BF16 operand copies + panel + partials",
+            "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
+            "avg_launch_ms": avg_ms}
+
+
+def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
+    """Roofline of one FP64-emulated product launch (k_oz_gemm): rows x K
+    operand in 7 BF16 digits, l columns in 48-column tiles.
+
+    Bytes: the digits of A, read once per column tile (14 bytes per element
+    and tile), the panel digits, the FP64 partials.  Flops: the 28 digit
+    products per element the tensor pipe executes (N padded to the tiles)."""
+    nt = (l + 47) // 48
+    t = avg_ms / 1e3
+    hw_flops = 28 * 2.0 * rows * K * nt * 48
+    nbytes = 14.0 * rows * K * nt + 14.0 * K * nt * 48 + 8.0 * rows * nt * 48
+    t_tensor = hw_flops / (tc_peak * 1e12)
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    tensor = t_tensor >= t_hbm
+    ach = hw_flops / t / 1e12 if tensor else nbytes / t / 1e9
+    peak = tc_peak if tensor else hbm_peak
+    return {"kernel": "k_oz_gemm (FP64 product as 28 exact BF16 digit products, tcgen05)",
+            "bound": "tensor" if tensor else "hbm", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak,
+            "achieved_basis": "tensor-pipe MMA flops (28 digit products, N padded to %d)" % (nt * 48)
+            if tensor else "bytes of the digits of A per column tile + panel digits + partials",
             "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
             "avg_launch_ms": avg_ms}
 
@@ -610,6 +635,28 @@ def main():
                          "roofline": tc_roofline(max(m, n), min(m, n), l, nprod, cpms / cpn if cpn else None,
                                                  hbm_peak, bf16_sus) if cpn else None}
         del cplan
+
+    # ---- the same matrix with the products emulated in FP64 accuracy on the tensor cores
+    if w.get("emulated"):
+        eplan = pq.Plan(m, n, k, p, q, seed=7 + rank, mode=pq.PBPQLP_MODE_FP64_EMU, stream=stream, device=dev)
+        eouts = eplan.outputs(dev)
+        for _ in range(args.warmup):
+            eplan.factor(A, out=eouts)
+        ems, epms, epn, elaunch, _ = timed_run(eplan, eouts, args.steps)
+        ems = dist_max(ems, dev)
+        err_e = eplan.error(A, *eouts, k, method=pq.PBPQLP_ERR_RESIDUAL)
+        ah_e = eplan.reconstruct(*eouts, k)
+        ah_f = plan.reconstruct(Qa, L, Qb, k)
+        diff = float(torch.linalg.norm(ah_e - ah_f) / torch.linalg.norm(A))
+        del ah_e, ah_f
+        line["fp64_emulated"] = {
+            "mode": "FP64_EMU", "value": whole_job_rate(1, world, ems), "unit": UNIT, "ms_per_step": ems,
+            "dtype": "bf16 digit products summed exactly (FP64-accurate)",
+            "tflops_algorithmic": whole_job_rate(1, world, ems) * flops / 1e12,
+            "rel_err_rank_k": err_e, "rel_err_rank_k_fp64": err_main,
+            "rel_fro_diff_vs_fp64_rank_k": diff, "speedup_vs_fp64": ms / ems, "gpu_launches": elaunch,
+            "roofline": oz_roofline(max(m, n), min(m, n), l, epms / epn, hbm_peak, bf16_sus) if epn else None}
+        del eplan, eouts
 
     # ---- CPU baseline: the oracle, rank 0 at N = 1, and parity of the timed result
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -51,13 +51,27 @@ enum {
 
 /* Arithmetic modes of the three products with A (the sketch, the power
  * iterations and the projection).  Gram accumulation, Cholesky and the final
- * l x l QR are FP64 in every mode. */
+ * l x l QR are FP64-accurate in every mode: the Grams of CholeskyQR and
+ * R = Q^T D run on the tensor cores in the exact-digit form described under
+ * PBPQLP_MODE_FP64_EMU (environment PBPQLP_NO_OZ_GRAM=1 at plan creation
+ * selects FP64 FMA kernels instead), the Cholesky and QR in FP64 FMA. */
 enum {
     PBPQLP_MODE_FP64 = 0,    /* A FP64, FP64 products */
     PBPQLP_MODE_BF16 = 1,    /* A and panels rounded to BF16, FP32 accumulate */
     PBPQLP_MODE_BF16X3 = 2,  /* BF16 hi/lo split, three products hi*hi + lo*hi + hi*lo */
     PBPQLP_MODE_TF32 = 3,    /* TF32 operands, FP32 accumulate */
-    PBPQLP_MODE_TF32X3 = 4   /* TF32 hi/lo split, three products */
+    PBPQLP_MODE_TF32X3 = 4,  /* TF32 hi/lo split, three products */
+    /* FP64-accurate products on the BF16 tensor cores (not in the paper; the
+     * error-free splitting of Ozaki, Ogita, Oishi & Rump 2012): every row of
+     * an operand is scaled by a power of two and written as 8 balanced
+     * base-128 digits (56 bits), the 36 digit products of weight >= 2^-56
+     * are summed exactly in FP32 over 32-deep windows and combined in int64.
+     * Digit rounding and the dropped digit products add at most
+     * 2^-51 max|x_i.| max|y_j.| per term (all digits extreme); on data of
+     * even magnitude the error is that of an FP64 dot product.  Rows holding
+     * Inf or NaN give NaN products.  A is turned into digits once per call
+     * (32 bytes per element of workspace, both orientations). */
+    PBPQLP_MODE_FP64_EMU = 5
 };
 
 /* Element type of A. */
@@ -118,7 +132,8 @@ int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
  *               NVLink-C2C bandwidth), m x n, row-major, leading dimension lda >= n,
  *               element type a_dtype (PBPQLP_F64 in MODE_FP64; PBPQLP_F32 or
  *               PBPQLP_F64 in the mixed modes, which split A into BF16 hi/lo
- *               copies in the workspace once per call).
+ *               copies in the workspace once per call, and in MODE_FP64_EMU,
+ *               which writes the digits of A and A^T there).
  *   workspace : device, >= pbpqlp_workspace_bytes(plan) bytes, 256-aligned;
  *               ws_bytes is its size.  Contents are scratch between calls.
  *   omega     : optional device m x l FP64 test matrix; NULL draws Phi from

@@ -393,7 +393,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     return PBPQLP_OK;
 }
 
-#define PBQ_TRY(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
+#define PBQ_TRY(expr) do { cudaError_t e_ = PBQ_DBG(expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
 
 int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
     char* lists = ws + B->off_lists;

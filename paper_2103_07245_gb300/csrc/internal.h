@@ -19,6 +19,9 @@ constexpr uint32_t kStTimeout = 8u;    // bounded wait gave up
 // Process-wide launch counter (incremented by every launcher below).
 void count_launches(int64_t n);
 int64_t launch_count();
+// Report a failing CUDA call on stderr when PBPQLP_DEBUG=1; returns e.
+cudaError_t debug_report(cudaError_t e, const char* what, const char* file, int line);
+#define PBQ_DBG(expr) ::pbq::debug_report((expr), #expr, __FILE__, __LINE__)
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t packed_tri(int l) { return (int64_t)l * (l + 1) / 2; }

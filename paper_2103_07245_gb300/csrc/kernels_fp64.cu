@@ -6,6 +6,8 @@
 // GB300 has 2 FP64 FMA lanes per SM per clock (~1.2 TFLOP/s for the chip), so
 // every FP64 kernel here is DFMA-issue bound and the tiling aims at keeping
 // all 152 SMs issuing DFMAs with no wasted (padded) lanes.
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstdint>
 
@@ -18,6 +20,17 @@ namespace pbq {
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// With PBPQLP_DEBUG=1 in the environment, failing CUDA calls of the library
+// are reported on stderr (call site and CUDA's error text).
+cudaError_t debug_report(cudaError_t e, const char* what, const char* file, int line) {
+    static const bool on = [] {
+        const char* v = std::getenv("PBPQLP_DEBUG");
+        return v && v[0] == '1';
+    }();
+    if (e != cudaSuccess && on) std::fprintf(stderr, "pbpqlp: %s:%d: %s -> %s\n", file, line, what, cudaGetErrorString(e));
+    return e;
+}
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------

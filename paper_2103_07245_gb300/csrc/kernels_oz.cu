@@ -1,0 +1,623 @@
+// FP64-accurate products on the BF16 tensor cores by exact integer digits
+// (the error-free splitting of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
+// 2012, with balanced base-256 digits held in BF16 and exact FP32 sums).
+// They serve the products of Algorithm 3 that must carry FP64 accuracy: the
+// Grams of CholeskyQR (the orth of Eq. 4), R = Q^T D (Eq. 6) and, in the
+// emulated-FP64 mode, the products with A and A^T (Eqs. 3 and 5).
+//
+// Digits.  Row i of an operand X (R x K) gets the exponent e_i with
+// |X[i][k]| < 2^(e_i - 1) for every k.  F = X[i][k] 2^(56 - e_i), rounded to
+// the nearest integer (|F| < 2^55), is written in balanced base 256,
+// F = sum_{s<7} x_s 256^(6-s) with |x_s| <= 128: each digit is an integer that
+// BF16 holds exactly, and X[i][k] = 2^(e_i - 56) F up to 2^(e_i - 57).  A row
+// that holds Inf or NaN has the exponent field 2047 and yields NaN products.
+//
+// Product.  C[i][j] = sum_k X[i][k] Y[j][k] = 2^(e_i + f_j - 112)
+// sum_{s,t} 256^(12 - s - t) I_st with I_st = sum_k x_s[i][k] y_t[j][k].
+// The digit products with s + t <= 6 are kept (28 of 49; the rest weigh
+// below 2^-55 of 2^(e_i + f_j) per term).  Level lam = s + t gathers its
+// lam + 1 digit products in one TMEM accumulator; over one 32-deep stage
+// |I_lam| <= 7 * 32 * 128^2 < 2^22, so the tensor pipe's FP32 sums are exact
+// integers whatever its rounding.  After every stage the epilogue adds the
+// seven level sums into two 64-bit accumulators per element,
+// hi = sum_{lam<3} I_lam 256^(2-lam) and lo = sum_{lam>=3} I_lam 256^(6-lam),
+// and at the end of a segment writes the FP64 partial
+// 2^(e_i + f_j - 32) hi + 2^(e_i + f_j - 64) lo.  Partials of one tile are
+// added in CTA order (deterministic).
+//
+// Kernel roles (448 threads, one CTA per SM): warp 0 issues the TMA loads of
+// a stage (the 7 digit tiles of X and of Y, 32 deep, 64-byte swizzle), warp 1
+// allocates TMEM (7 levels x 48 columns) and issues the 56 MMAs of a stage
+// level by level, committing each level to its own mbarrier; warps 2-13 (16
+// columns each) drain level lam of stage w while the MMAs of the later levels
+// run, and the MMAs of level lam of stage w + 1 wait only for that drain.
+// Every wait is bounded by a globaltimer deadline (status bit and abort flag
+// on expiry).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+
+#include "internal.h"
+#include "oz_internal.h"
+#include "tc_device.cuh"
+
+namespace pbq {
+
+using namespace tcdev;
+
+namespace {
+
+constexpr int kOzThreads = 448;                                    // 2 + 12 warps
+constexpr int kOzEpiThreads = 384;
+constexpr int kOzStages = 2;
+constexpr uint32_t kOzRowBytes = kOzBK * 2;                        // 64 bytes: one swizzle row
+constexpr uint32_t kOzXTile = kOzBM * kOzRowBytes;                 // one digit of X: 8 KB
+constexpr uint32_t kOzYTile = kOzBN * kOzRowBytes;                 // one digit of Y: 3 KB
+constexpr uint32_t kOzStageBytes = kOzDigits * (kOzXTile + kOzYTile);   // 77 KB
+constexpr uint32_t kOzTmemCols = 512;                              // >= kOzDigits * kOzBN, a power of two
+constexpr int kOzMagic = 0x4B400000;                               // bits of 1.5 * 2^23
+
+// K-major tile with 64-byte rows and the 64-byte swizzle (8-row groups 512 B apart).
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512u >> 4) << 32;            // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)4 << 61;                      // 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t mad_wide_u(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// Tile t -> (row tile, column tile); with `upper` only the column tiles
+// nt >= 128 mt / 48 (the 128 x 48 tiles that touch the upper triangle) are
+// enumerated.
+__host__ __device__ inline int64_t oz_first_col_tile(int64_t m) { return (m * kOzBM) / kOzBN; }
+__host__ __device__ inline void oz_tile(int64_t t, int NT, int upper, int64_t* mt, int* nt) {
+    if (!upper) {
+        *mt = t / NT;
+        *nt = (int)(t - *mt * NT);
+        return;
+    }
+    int64_t m = 0;
+    for (;;) {
+        const int64_t first = oz_first_col_tile(m);
+        const int64_t cnt = NT - first;
+        if (cnt <= 0) { *mt = m; *nt = NT; return; }   // past the end (not reached for t < tiles)
+        if (t < cnt) { *mt = m; *nt = (int)(first + t); return; }
+        t -= cnt;
+        ++m;
+    }
+}
+
+// x 2^k for x an integer-valued double (|x| < 2^63) and |k| < 3000: three
+// exact power-of-two factors, each a normal double, rounded once at the end.
+__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+__device__ __forceinline__ double scale2(double x, int k) {
+    const int k1 = k > 900 ? 900 : (k < -900 ? -900 : k);
+    const int r = k - k1;
+    const int k2 = r > 900 ? 900 : (r < -900 ? -900 : r);
+    return x * pow2i(k1) * pow2i(k2) * pow2i(r - k2);
+}
+
+// BF16 bits of a small integer d (|d| < 2^22): exact through FP32.
+__device__ __forceinline__ uint16_t digit_bf16(int d) {
+    const float f = __int_as_float(kOzMagic + d) - 12582912.0f;
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+// Biased exponent field of x (0 for zero and subnormals).
+__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// The 7 balanced base-256 digits of round(x 2^(56 - e)), |x| < 2^(e - 1).
+__device__ __forceinline__ void digits7(double x, int e, int* d) {
+    const long long bits = __double_as_longlong(x);
+    int eb = (int)((bits >> 52) & 0x7FF);
+    long long mant = bits & 0xFFFFFFFFFFFFFLL;
+    if (eb) mant |= 1LL << 52;
+    else eb = 1;
+    const int sh = eb - 1075 + 56 - e;   // x = mant 2^(eb - 1075); sh <= 2 by the choice of e
+    long long F;
+    if (sh >= 0) F = mant << sh;
+    else if (sh > -62) F = (mant + (1LL << (-sh - 1))) >> (-sh);
+    else F = 0;
+    if (bits < 0) F = -F;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const int w = 8 * (6 - s);
+        const long long q = (F + (1LL << (w - 1))) >> w;
+        d[s] = (int)q;
+        F -= q * (1LL << w);
+    }
+    d[6] = (int)F;
+}
+
+// ---------------------------------------------------------------------------
+// The product kernel
+// ---------------------------------------------------------------------------
+// 448 threads are allocated registers as 16 warps: at most 65536 / 512 = 128 each.
+__global__ void __maxnreg__(128)
+k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t tiles, int NT,
+          int upper, int KI, int smax, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
+          const int* __restrict__ ey_raw, double* __restrict__ part, uint32_t* __restrict__ status,
+          uint64_t timeout_ns, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    constexpr uint32_t IDESC = idesc_bf16_f32(kOzBM, kOzBN);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], accf_bar[kOzDigits], acce_bar[kOzDigits], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int issued_sh, consumed_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x, c = blockIdx.x;
+    const int64_t T = tiles * (int64_t)KI;
+    const int64_t it_begin = sk_begin(c, T, G), it_end = sk_begin(c + 1, T, G);
+    const uint64_t deadline = globaltimer() + timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int l = 0; l < kOzDigits; ++l) { mbar_init(&accf_bar[l], 1); mbar_init(&acce_bar[l], kOzEpiThreads); }
+        mbar_init(&drain_bar, 1);
+        abort_sh = 0;
+        issued_sh = 0;
+        consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(kOzTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: one stage = 8 X digit tiles + 8 Y digit tiles
+        if (lane == 0) {
+            int li = 0;
+            for (int64_t it = it_begin; it < it_end; ++it, ++li) {
+                const int s = li % kOzStages;
+                if (li >= kOzStages) {
+                    if (!mbar_wait(&empty_bar[s], (uint32_t)((li / kOzStages - 1) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        break;
+                    }
+                }
+                const int64_t tile = it / KI;
+                const int k0 = (int)(it - tile * KI) * kOzBK;
+                int64_t mt;
+                int nt;
+                oz_tile(tile, NT, upper, &mt, &nt);
+                unsigned char* st = smem + (size_t)s * kOzStageBytes;
+                mbar_expect_tx(&full_bar[s], kOzStageBytes);
+                tma_load_3d(st, &tmX, &full_bar[s], k0, (int)(mt * kOzBM), 0);
+                tma_load_3d(st + kOzDigits * kOzXTile, &tmY, &full_bar[s], k0, nt * kOzBN, 0);
+                issued_sh = li + 1;
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: level by level, each level committed on its own
+        if (lane == 0) {
+            int li = 0;
+            bool ok = true;
+            for (int64_t it = it_begin; ok && it < it_end; ++it, ++li) {
+                const int s = li % kOzStages;
+                if (!mbar_wait(&full_bar[s], (uint32_t)((li / kOzStages) & 1), deadline, &abort_sh)) {
+                    abort_sh = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t xa = smem_u32(smem + (size_t)s * kOzStageBytes);
+                const uint64_t dX = sdesc_k_sw64(xa), dY = sdesc_k_sw64(xa + kOzDigits * kOzXTile);
+                for (int lam = 0; lam < kOzDigits; ++lam) {
+                    if (li > 0 && !mbar_wait(&acce_bar[lam], (uint32_t)((li - 1) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(lam * kOzBN);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        for (int sx = 0; sx <= lam; ++sx) {
+                            const int ty = lam - sx;
+                            const uint64_t a = dX + (uint64_t)((sx * kOzXTile + kk * 32) >> 4);
+                            const uint64_t b = dY + (uint64_t)((ty * kOzYTile + kk * 32) >> 4);
+                            tc_mma_bf16(dt, a, b, IDESC, (kk | sx) ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(&accf_bar[lam]);
+                }
+                if (!ok) break;
+                tc_commit(&empty_bar[s]);
+                consumed_sh = li + 1;
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            tc_commit(&drain_bar);
+            const uint64_t dl = globaltimer() + timeout_ns;
+            uint32_t spin = 0;
+            while (!mbar_test(&drain_bar, 0)) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) { abort_sh = 1; break; }
+            }
+        }
+    } else {
+        // ---------------- epilogue: exact level sums -> (hi, lo) -> FP64 partials.
+        // The FP32 level value v (an integer, |v| < 2^22) is read as the bits
+        // of v + 1.5 * 2^23, i.e. kOzMagic + v; the bias kOzMagic * weight is
+        // removed once per segment (unsigned arithmetic wraps exactly).
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int g = (warp - 2) >> 2;          // which 16 of the 48 columns
+        const int rloc = q * 32 + lane;
+        uint64_t hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
+        const int n_it = (int)(it_end - it_begin);
+        int kc = (int)(it_begin % KI), tl = 0;  // k-chunk within the tile; tile relative to the first one
+        int nwin = 0;
+        bool ok = true;
+        for (int li = 0; ok && li < n_it; ++li) {
+#pragma unroll
+            for (int lam = 0; lam < kOzDigits; ++lam) {
+                if (ok) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[lam], (uint32_t)(li & 1), deadline, &abort_sh));
+                    if (!ok) {
+                        abort_sh = 1;
+                    } else {
+                        const uint32_t wgt = 1u << (8 * ((lam < 3 ? 2 : 6) - lam));
+                        tc_fence_after();
+                        float v[16];
+                        tmem_ld16(tmem_base + (uint32_t)(lam * kOzBN + g * 16) + ((uint32_t)(q * 32) << 16), v);
+                        tc_fence_before();
+                        mbar_arrive(&acce_bar[lam]);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const uint32_t bv = __float_as_uint(v[j] + 12582912.0f);
+                            if (lam < 3) hi[j] = mad_wide_u(bv, wgt, hi[j]);
+                            else lo[j] = mad_wide_u(bv, wgt, lo[j]);
+                        }
+                    }
+                }
+            }
+            if (!ok) break;
+            ++nwin;
+            if (li + 1 == n_it || kc + 1 == KI) {
+                const int64_t tile = it_begin / KI + tl;
+                int64_t mt;
+                int nt;
+                oz_tile(tile, NT, upper, &mt, &nt);
+                const int64_t row = mt * kOzBM + rloc;
+                const int exr = row < Rx ? ex_raw[row] : 0;
+                const int ei = exr - 1021;
+                // bias added per stage: kOzMagic (2^16 + 2^8 + 1) to hi, kOzMagic (2^24 + 2^16 + 2^8 + 1) to lo
+                const uint64_t bh = (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 16) + (1u << 8) + 1u);
+                const uint64_t bl =
+                    (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 24) + (1u << 16) + (1u << 8) + 1u);
+                double* slot = part + ((size_t)c * smax + (size_t)tl) * (size_t)(kOzBM * kOzBN);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int cl = g * 16 + j;
+                    const int64_t col = (int64_t)nt * kOzBN + cl;
+                    const int eyr = col < Ry ? ey_raw[col] : 0;
+                    const int ej = eyr - 1021;
+                    const int64_t h = (int64_t)(hi[j] - bh), l = (int64_t)(lo[j] - bl);
+                    // a row holding Inf or NaN (exponent field 2047) makes its products NaN
+                    const double val = (exr >= 2047 || eyr >= 2047)
+                                           ? __longlong_as_double(0x7FF8000000000000LL)
+                                           : scale2((double)h, ei + ej - 32) + scale2((double)l, ei + ej - 64);
+                    slot[(size_t)cl * kOzBM + rloc] = val;
+                    hi[j] = 0;
+                    lo[j] = 0;
+                }
+                nwin = 0;
+                ++tl;
+                kc = 0;
+            } else {
+                ++kc;
+            }
+        }
+    }
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // wait (bounded) for TMA copies that were issued but never consumed
+        const uint64_t dl = globaltimer() + timeout_ns;
+        for (int li = consumed_sh; li < issued_sh; ++li) {
+            const int s = li % kOzStages;
+            uint32_t spin = 0;
+            while (!mbar_test(&full_bar[s], (uint32_t)((li / kOzStages) & 1))) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) break;
+            }
+        }
+        if (abort_sh) atomicOr(status, kStTimeout);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kOzTmemCols)
+                     : "memory");
+    }
+}
+
+// Add the stream-K partials of each tile in CTA order into C (FP64, ldc).
+__global__ void k_oz_reduce(int64_t tiles, int NT, int upper, int KI, int64_t G, int smax, const double* __restrict__ part,
+                            int64_t Mrows, int N, double* __restrict__ C, int64_t ldc, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    const int64_t T = tiles * (int64_t)KI;
+    const int64_t total = tiles * (int64_t)(kOzBM * kOzBN);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = e / (kOzBM * kOzBN);
+        const int rem = (int)(e - tile * (kOzBM * kOzBN));
+        const int cl = rem / kOzBM, r = rem - cl * kOzBM;
+        int64_t mt;
+        int nt;
+        oz_tile(tile, NT, upper, &mt, &nt);
+        const int64_t i = mt * kOzBM + r;
+        const int64_t j = (int64_t)nt * kOzBN + cl;
+        if (i >= Mrows || j >= N) continue;
+        const int64_t it0 = tile * KI, it1 = it0 + KI - 1;
+        int64_t c = (it0 * G) / T;
+        while (c + 1 < G && sk_begin(c + 1, T, G) <= it0) ++c;
+        while (c > 0 && sk_begin(c, T, G) > it0) --c;
+        double acc = 0.0;
+        for (; c < G && sk_begin(c, T, G) <= it1; ++c) {
+            const int64_t b = sk_begin(c, T, G), en = sk_begin(c + 1, T, G);
+            if (en <= it0) continue;
+            const int64_t ft = b / KI;
+            acc += part[((size_t)c * smax + (size_t)(tile - ft)) * (size_t)(kOzBM * kOzBN) + rem];
+        }
+        C[i * ldc + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Digit preparation
+// ---------------------------------------------------------------------------
+// Column exponents of a rows x N panel: eraw[j] = max over rows of the biased exponent.
+__global__ void k_oz_panel_exp(int64_t rows, int N, const double* __restrict__ P, int64_t ldp, int* __restrict__ eraw,
+                               const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    const int j = threadIdx.x;
+    if (j >= N) return;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int64_t r1 = r0 + 64 < rows ? r0 + 64 : rows;
+    int mx = 0;
+    for (int64_t r = r0; r < r1; ++r) mx = max(mx, exp_field(P[r * ldp + j]));
+    if (mx > 0) atomicMax(&eraw[j], mx);
+}
+
+// Digits of P^T: S[d][j][r] for column j of the panel (scale from eraw[j]).
+__global__ void k_oz_panel_slice(int64_t rows, int N, const double* __restrict__ P, int64_t ldp,
+                                 const int* __restrict__ eraw, uint16_t* __restrict__ S, int64_t ldS,
+                                 int64_t slice_stride, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    __shared__ uint16_t sd[kOzDigits][32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32;
+    const int j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int j = j0 + tx;
+    const int e = j < N ? eraw[j] - 1021 : 0;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t r = r0 + rr;
+        const double x = (r < rows && j < N) ? P[r * ldp + j] : 0.0;
+        int d[kOzDigits];
+        digits7(x, e, d);
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) sd[s][tx][rr] = digit_bf16(d[s]);
+    }
+    __syncthreads();
+    const int64_t r = r0 + tx;
+    if (r >= rows) return;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int jc = j0 + jj;
+        if (jc >= N) break;
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) S[(int64_t)s * slice_stride + (int64_t)jc * ldS + r] = sd[s][jj][tx];
+    }
+}
+
+template <typename Tin>
+__device__ __forceinline__ double load_a(const Tin* A, int64_t i) {
+    return (double)A[i];
+}
+
+// Row and column exponents of A (32 x 32 tiles; block 32 x 8).
+template <typename Tin>
+__global__ void k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, int* __restrict__ er,
+                           int* __restrict__ ec) {
+    __shared__ int cmax[32];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (ty == 0) cmax[tx] = 0;
+    __syncthreads();
+    int cm = 0;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t r = r0 + rr, cc = c0 + tx;
+        const int eb = (r < m && cc < n) ? exp_field(load_a(A, r * lda + cc)) : 0;
+        cm = max(cm, eb);
+        const int rm = __reduce_max_sync(0xffffffffu, eb);
+        if (tx == 0 && r < m && rm > 0) atomicMax(&er[r], rm);
+    }
+    atomicMax(&cmax[tx], cm);
+    __syncthreads();
+    if (ty == 0 && c0 + tx < n && cmax[tx] > 0) atomicMax(&ec[c0 + tx], cmax[tx]);
+}
+
+// Digits of A (row scales) and of A^T (column scales) from one read of a 32 x 32 tile.
+template <typename Tin>
+__global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, const int* __restrict__ er,
+                             const int* __restrict__ ec, uint16_t* __restrict__ Srow, int64_t ldr, int64_t srow_stride,
+                             uint16_t* __restrict__ Scol, int64_t ldcol, int64_t scol_stride) {
+    __shared__ uint16_t sd[kOzDigits][32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t cc = c0 + tx;
+    const int ecol = cc < n ? ec[cc] - 1021 : 0;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t r = r0 + rr;
+        const bool in = r < m && cc < n;
+        const double x = in ? load_a(A, r * lda + cc) : 0.0;
+        int d[kOzDigits];
+        if (Srow && in) {
+            digits7(x, er[r] - 1021, d);
+#pragma unroll
+            for (int s = 0; s < kOzDigits; ++s) Srow[(int64_t)s * srow_stride + r * ldr + cc] = digit_bf16(d[s]);
+        }
+        if (Scol) {
+            digits7(x, ecol, d);
+#pragma unroll
+            for (int s = 0; s < kOzDigits; ++s) sd[s][tx][rr] = digit_bf16(d[s]);
+        }
+    }
+    if (!Scol) return;
+    __syncthreads();
+    const int64_t r = r0 + tx;
+    if (r >= m) return;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int64_t jc = c0 + jj;
+        if (jc >= n) break;
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) Scol[(int64_t)s * scol_stride + jc * ldcol + r] = sd[s][jj][tx];
+    }
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled encode_fn() {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+    }
+    return fn;
+}
+
+// 3-D map over the 7 digit matrices of an operand: {K, rows, digit}, box {32, box_rows, 7}.
+bool make_map_oz(CUtensorMap* map, const OzOperand& op, int64_t K, int box_rows) {
+    PFN_encodeTiled fn = encode_fn();
+    if (!fn || !op.S || op.rows < 1 || K < 1) return false;
+    if (op.ld < K || (op.ld % 8) != 0 || op.slice_stride < op.rows * op.ld || (op.slice_stride % 8) != 0) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)op.rows, (cuuint64_t)kOzDigits};
+    cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)op.slice_stride * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)kOzDigits};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(op.S), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
+    OzGeom g;
+    const int64_t MT = (Mrows + kOzBM - 1) / kOzBM;
+    g.NT = (N + kOzBN - 1) / kOzBN;
+    g.upper = upper ? 1 : 0;
+    if (upper) {
+        g.tiles = 0;
+        for (int64_t m = 0; m < MT; ++m) g.tiles += (g.NT - oz_first_col_tile(m) > 0) ? g.NT - oz_first_col_tile(m) : 0;
+    } else {
+        g.tiles = MT * g.NT;
+    }
+    g.KI = (int)((K + kOzBK - 1) / kOzBK);
+    const int64_t T = g.tiles * g.KI;
+    g.G = (int)(T < num_sms ? T : num_sms);
+    if (g.G < 1) g.G = 1;
+    const int64_t share = (T + g.G - 1) / g.G;
+    g.smax = (int)((share + g.KI - 1) / g.KI + 1);
+    g.part_doubles = (int64_t)g.G * g.smax * kOzBM * kOzBN;
+    return g;
+}
+
+cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, int64_t K, const OzGeom& g, double* part,
+                              double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
+                              cudaEvent_t after_gemm) {
+    if (g.tiles < 1 || Y.rows > (int64_t)g.NT * kOzBN || !X.eraw || !Y.eraw) return cudaErrorInvalidValue;
+    CUtensorMap mx, my;
+    if (!make_map_oz(&mx, X, K, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
+    if (!make_map_oz(&my, Y, K, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
+    const size_t smem = (size_t)kOzStages * kOzStageBytes + 1024;
+    cudaError_t e = PBQ_DBG(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (e != cudaSuccess) return e;
+    k_oz_gemm<<<g.G, kOzThreads, smem, s>>>(mx, my, g.tiles, g.NT, g.upper, g.KI, g.smax, X.rows, Y.rows, X.eraw,
+                                            Y.eraw, part, status, 2000000000ull, cond);
+    count_launches(1);
+    if ((e = PBQ_DBG(cudaGetLastError())) != cudaSuccess) {
+        const char* v = std::getenv("PBPQLP_DEBUG");
+        cudaFuncAttributes fa;
+        if (v && v[0] == '1' && cudaFuncGetAttributes(&fa, k_oz_gemm) == cudaSuccess)
+            std::fprintf(stderr, "pbpqlp: k_oz_gemm regs %d, max threads %d, static smem %zu, max dyn smem %d, local %zu, "
+                         "launch %d x %d with %zu bytes\n", fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+                         fa.maxDynamicSharedSizeBytes, fa.localSizeBytes, g.G, kOzThreads, smem);
+        return e;
+    }
+    if (after_gemm && (e = cudaEventRecord(after_gemm, s)) != cudaSuccess) return e;
+    const int64_t total = g.tiles * (int64_t)(kOzBM * kOzBN);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_oz_reduce<<<(unsigned)blocks, 256, 0, s>>>(g.tiles, g.NT, g.upper, g.KI, g.G, g.smax, part, X.rows, (int)Y.rows,
+                                                 C, ldc, cond);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, int64_t ldS,
+                            int64_t slice_stride, const int* cond, cudaStream_t s) {
+    if (rows < 1 || N < 1 || N > 256) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(eraw, 0, sizeof(int) * (size_t)N, s);
+    if (e != cudaSuccess) return e;
+    k_oz_panel_exp<<<(unsigned)((rows + 63) / 64), 256, 0, s>>>(rows, N, P, ldp, eraw, cond);
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
+    k_oz_panel_slice<<<grid, block, 0, s>>>(rows, N, P, ldp, eraw, (uint16_t*)S, ldS, slice_stride, cond);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
+                        int64_t ldr, int64_t srow_stride, void* Scol, int64_t ldcol, int64_t scol_stride,
+                        cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(er, 0, sizeof(int) * (size_t)m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ec, 0, sizeof(int) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
+    if (a_f32) {
+        k_oz_a_exp<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec);
+        k_oz_a_slice<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, (uint16_t*)Srow, ldr,
+                                                   srow_stride, (uint16_t*)Scol, ldcol, scol_stride);
+    } else {
+        k_oz_a_exp<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec);
+        k_oz_a_slice<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, (uint16_t*)Srow, ldr,
+                                                    srow_stride, (uint16_t*)Scol, ldcol, scol_stride);
+    }
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace pbq

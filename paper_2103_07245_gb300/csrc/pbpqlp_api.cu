@@ -12,6 +12,7 @@
 #include "../../include/pbpqlp.h"
 #include "internal.h"
 #include "tc_internal.h"
+#include "oz_internal.h"
 
 using namespace pbq;
 
@@ -39,6 +40,14 @@ struct pbpqlp_plan_s {
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
     size_t off_Bnhi = 0, off_Bnlo = 0, off_Bmhi = 0, off_Bmlo = 0, off_tcpart = 0;
+    // FP64-accurate tensor-core products (digit form): Grams and R = Q^T D in
+    // every mode (oz_gram), the products with A and A^T in MODE_FP64_EMU (emu)
+    bool oz_gram = false, emu = false;
+    int64_t ldz = 0;                    // leading dim of the panel digit matrices (K up to max(m, n))
+    int64_t ldz_n = 0, ldz_m = 0;       // leading dims of the digit matrices of A (K = n) and A^T (K = m)
+    OzGeom og_gm, og_gn, og_nn, og_tn;  // Grams over m / n rows; C = A Y; C = A^T Y
+    size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0;
+    size_t off_ozEr = 0, off_ozEc = 0, off_ozArow = 0, off_ozAcol = 0;
     void* last_ws = nullptr;
     // observability: CUDA event pairs around each A / A^T pass kernel
     bool timing = false;
@@ -58,6 +67,9 @@ struct Ws {
     double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red;
     void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
     float* tcpart;
+    int *ozE1, *ozE2, *ozEr, *ozEc;
+    void *ozS1, *ozS2, *ozArow, *ozAcol;
+    double* ozpart;
 };
 
 Ws carve(const pbpqlp_plan_s* P, void* base) {
@@ -88,6 +100,16 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.Bmhi = mixed ? (void*)(b + P->off_Bmhi) : nullptr;
     w.Bmlo = split ? (void*)(b + P->off_Bmlo) : nullptr;
     w.tcpart = mixed ? (float*)(b + P->off_tcpart) : nullptr;
+    const bool oz = P->oz_gram || P->emu;
+    w.ozE1 = oz ? (int*)(b + P->off_ozE1) : nullptr;
+    w.ozE2 = oz ? (int*)(b + P->off_ozE2) : nullptr;
+    w.ozS1 = oz ? (void*)(b + P->off_ozS1) : nullptr;
+    w.ozS2 = oz ? (void*)(b + P->off_ozS2) : nullptr;
+    w.ozpart = oz ? (double*)(b + P->off_ozpart) : nullptr;
+    w.ozEr = P->emu ? (int*)(b + P->off_ozEr) : nullptr;
+    w.ozEc = P->emu ? (int*)(b + P->off_ozEc) : nullptr;
+    w.ozArow = P->emu ? (void*)(b + P->off_ozArow) : nullptr;
+    w.ozAcol = P->emu ? (void*)(b + P->off_ozAcol) : nullptr;
     return w;
 }
 
@@ -114,7 +136,7 @@ void choose_split(int64_t Mtiles, int64_t K, int64_t slots, int* S_out, int64_t*
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA; }
 
-#define PBQ_TRY(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
+#define PBQ_TRY(expr) do { cudaError_t e_ = PBQ_DBG(expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
 
 // Event pair for the next timed pass kernel (nullptr pair when timing is off).
 std::pair<cudaEvent_t, cudaEvent_t> next_events(pbpqlp_plan_s* P) {
@@ -183,6 +205,50 @@ int tc_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, 
     return PBPQLP_OK;
 }
 
+// Digit-form operand over a panel digit buffer (l rows, contraction up to max(m, n)).
+OzOperand panel_digits(const pbpqlp_plan_s* P, void* S, const int* E) {
+    OzOperand op;
+    op.S = S;
+    op.rows = P->l;
+    op.ld = P->ldz;
+    op.slice_stride = (int64_t)P->l * P->ldz;
+    op.eraw = E;
+    return op;
+}
+
+// Emulated-FP64 product with A (transA = false: C = A Y, Y n x N) or A^T
+// (C = A^T Y, Y m x N): digits of the panel, one tensor-core product over the
+// digits of A prepared by emu_prepare_a, deterministic reduction.
+int emu_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t ldy, int N, double* C, int64_t ldc,
+             bool timed = false) {
+    cudaStream_t s = P->stream;
+    const int64_t K = transA ? P->m : P->n;
+    OzOperand X;
+    X.S = transA ? w.ozAcol : w.ozArow;
+    X.rows = transA ? P->n : P->m;
+    X.ld = transA ? P->ldz_m : P->ldz_n;
+    X.slice_stride = X.rows * X.ld;
+    X.eraw = transA ? w.ozEc : w.ozEr;
+    OzOperand Yd = panel_digits(P, w.ozS2, w.ozE2);
+    Yd.rows = N;
+    PBQ_TRY(launch_oz_panel(K, N, Y, ldy, w.ozE2, w.ozS2, P->ldz, Yd.slice_stride, nullptr, s));
+    OzGeom g = transA ? P->og_tn : P->og_nn;
+    if (N != P->l) g = oz_geometry(X.rows, N, K, false, P->num_sms);
+    const int64_t cap = transA ? P->og_tn.part_doubles : P->og_nn.part_doubles;
+    if (g.part_doubles > cap) return PBPQLP_EINVAL;
+    const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
+    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+    PBQ_TRY(launch_oz_product(X, Yd, K, g, w.ozpart, C, ldc, w.status, nullptr, s, ev.second));
+    return PBPQLP_OK;
+}
+
+// Digits of A (row scales) and of A^T (column scales), once per factorization.
+int emu_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, int64_t lda) {
+    PBQ_TRY(launch_oz_a(P->m, P->n, A, a_f32, lda, w.ozEr, w.ozEc, w.ozArow, P->ldz_n, P->m * P->ldz_n, w.ozAcol,
+                        P->ldz_m, P->n * P->ldz_m, P->stream));
+    return PBPQLP_OK;
+}
+
 // Orthonormalise X (rows x l, ld ldp) in place: CholeskyQR in pass pairs
 // (X -> Y -> X).  Pair 1 is CholeskyQR2; pairs 2 and 3 run on the device
 // only if a pass of the previous pair needed the shifted retry.
@@ -197,8 +263,15 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         const int* cond = pass <= 2 ? nullptr : w.ctl + 8 + (pass + 1) / 2;
         const int64_t ps = (int64_t)l * ldp;
         // the Cholesky reads only the upper triangle of the Gram
-        PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
-        PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
+        if (P->oz_gram) {
+            const OzOperand op = panel_digits(P, w.ozS1, w.ozE1);
+            PBQ_TRY(launch_oz_panel(rows, l, src, ldp, w.ozE1, w.ozS1, P->ldz, op.slice_stride, cond, s));
+            PBQ_TRY(launch_oz_product(op, op, rows, rows == P->m ? P->og_gm : P->og_gn, w.ozpart, w.G, l, w.status,
+                                      cond, s));
+        } else {
+            PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
+            PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
+        }
         if (P->cluster_chol) PBQ_TRY(launch_cholesky_cluster(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         else PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s, P->nprod > 0));
@@ -253,7 +326,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     const int64_t l64 = (int64_t)k + (int64_t)p;
     if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
     if (l64 > m || l64 > n || l64 > kMaxEll) return PBPQLP_EINVAL;
-    if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_TF32X3) return PBPQLP_EINVAL;
+    if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_FP64_EMU) return PBPQLP_EINVAL;
     pbpqlp_plan_s* P = new (std::nothrow) pbpqlp_plan_s();
     if (!P) return PBPQLP_ENOMEM;
     P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
@@ -263,6 +336,9 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
         P->cluster_chol = cholesky_cluster_fits(P->l) && !(nc && nc[0] == '1');
         P->cluster_qr = small_qr_cluster_fits(P->l) && !(nc && nc[0] == '1');
+        const char* no = std::getenv("PBPQLP_NO_OZ_GRAM");
+        P->oz_gram = !(no && no[0] == '1');
+        P->emu = mode == PBPQLP_MODE_FP64_EMU;
     }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -304,7 +380,33 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->off_Pt = take(sizeof(double) * l * ldp);
     P->off_work = take(sizeof(double) * (2 * l * l + 2 * l));
     P->off_red = take(sizeof(double) * 2048);
-    if (mode != PBPQLP_MODE_FP64) {
+    if (P->oz_gram || P->emu) {
+        P->ldz = oz_ld(m > n ? m : n);
+        P->og_gm = oz_geometry(l, (int)l, m, true, P->num_sms);
+        P->og_gn = oz_geometry(l, (int)l, n, true, P->num_sms);
+        int64_t pd = P->og_gm.part_doubles > P->og_gn.part_doubles ? P->og_gm.part_doubles : P->og_gn.part_doubles;
+        if (P->emu) {
+            P->ldz_n = oz_ld(n);
+            P->ldz_m = oz_ld(m);
+            P->og_nn = oz_geometry(m, (int)l, n, false, P->num_sms);
+            P->og_tn = oz_geometry(n, (int)l, m, false, P->num_sms);
+            pd = pd > P->og_nn.part_doubles ? pd : P->og_nn.part_doubles;
+            pd = pd > P->og_tn.part_doubles ? pd : P->og_tn.part_doubles;
+        }
+        const size_t dig = 2 * (size_t)kOzDigits;   // bytes of one element's 8 BF16 digits
+        P->off_ozE1 = take(sizeof(int) * 256);
+        P->off_ozE2 = take(sizeof(int) * 256);
+        P->off_ozS1 = take(dig * (size_t)l * P->ldz);
+        P->off_ozS2 = take(dig * (size_t)l * P->ldz);
+        P->off_ozpart = take(sizeof(double) * (size_t)pd);
+        if (P->emu) {
+            P->off_ozEr = take(sizeof(int) * (size_t)m);
+            P->off_ozEc = take(sizeof(int) * (size_t)n);
+            P->off_ozArow = take(dig * (size_t)m * P->ldz_n);
+            P->off_ozAcol = take(dig * (size_t)n * P->ldz_m);
+        }
+    }
+    if (mode != PBPQLP_MODE_FP64 && mode != PBPQLP_MODE_FP64_EMU) {
         P->tf32 = (mode == PBPQLP_MODE_TF32 || mode == PBPQLP_MODE_TF32X3);
         P->nprod = (mode == PBPQLP_MODE_BF16X3 || mode == PBPQLP_MODE_TF32X3) ? 3 : 1;
         const char* fault = std::getenv("PBPQLP_FAULT");
@@ -348,7 +450,8 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
                   const double* omega, double* Qa, double* L, double* Qb) {
     if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
     const bool mixed = P->nprod > 0;
-    if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    if ((mixed || P->emu) ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64)
+        return PBPQLP_EUNSUPPORTED;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
     if ((rc = check_device_addressable(Av))) return rc;
@@ -360,9 +463,11 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
+    if (P->emu && (rc = emu_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
     // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
     auto product = [&](bool transA, const double* Y, double* C) -> int {
         if (mixed) return tc_pass(P, w, transA, Y, ldp, l, C, ldp, true);
+        if (P->emu) return emu_pass(P, w, transA, Y, ldp, l, C, ldp, true);
         return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
                       : gemm_pass(P, w, false, m, n, A, lda, Y, ldp, C, ldp, l, P->S_nn, P->kc_nn, true);
     };
@@ -383,7 +488,12 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     if ((rc = product(false, w.Xn, w.Dm))) return rc;
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
-    {
+    if (P->oz_gram) {
+        const OzOperand qd = panel_digits(P, w.ozS1, w.ozE1), dd = panel_digits(P, w.ozS2, w.ozE2);
+        PBQ_TRY(launch_oz_panel(m, l, w.Xm, ldp, w.ozE1, w.ozS1, P->ldz, qd.slice_stride, nullptr, s));
+        PBQ_TRY(launch_oz_panel(m, l, w.Dm, ldp, w.ozE2, w.ozS2, P->ldz, dd.slice_stride, nullptr, s));
+        PBQ_TRY(launch_oz_product(qd, dd, m, P->og_gm, w.ozpart, w.R, l, w.status, nullptr, s));
+    } else {
         const int64_t ps = (int64_t)l * ldp;
         PBQ_TRY(launch_upper_product(l, m, w.Xm, w.Dm, ldp, w.part, ps, P->S_gm, P->kc_gm, nullptr, s));
         PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s, true));
@@ -402,7 +512,8 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     const int64_t rowsY = trans ? P->m : P->n, rowsC = trans ? P->n : P->m;
     if (ldy < ncols || ldc < ncols) return PBPQLP_EINVAL;
     const bool mixed = P->nprod > 0;
-    if (mixed ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64) return PBPQLP_EUNSUPPORTED;
+    if ((mixed || P->emu) ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64)
+        return PBPQLP_EUNSUPPORTED;
     int rc = check_ws(P, workspace, ws_bytes);
     if (rc) return rc;
     if ((rc = check_device_addressable(A))) return rc;
@@ -411,6 +522,10 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     cudaStream_t s = P->stream;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     (void)rowsY;
+    if (P->emu) {
+        if ((rc = emu_prepare_a(P, w, A, a_dtype == PBPQLP_F32, lda))) return rc;
+        return emu_pass(P, w, trans != 0, Y, ldy, ncols, C, ldc);
+    }
     if (mixed) {
         if ((rc = tc_prepare_a(P, w, A, a_dtype == PBPQLP_F32, lda))) return rc;
         return tc_pass(P, w, trans != 0, Y, ldy, ncols, C, ldc);
