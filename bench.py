@@ -41,6 +41,10 @@ WORKLOADS = {
                              "sigma_i = i^-alpha, alpha~U[1,3], k~U[8,64], p=8, q=1, A in FP32"),
     "batched_64": dict(batched=True, count=64, p=8, q=1, mode="TF32X3", compare="FP64",
                        desc="batched split-TF32: 64 matrices of the 512-matrix distribution (profiling size)"),
+    "fp64emu_8000": dict(m=8000, n=8000, k=100, p=10, q=2, gen="svd", spectrum="exp", scale=40.0, rank_cap=1500,
+                         mode="FP64_EMU", compare=None,
+                         desc="FP64-accurate products as exact BF16 digit sums on the tensor cores, "
+                              "A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
     "bf16x3_10000": dict(m=10000, n=10000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
                          compare=None,
                          desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 10000x10000, k=200 p=20 q=2 (profiling size)"),
@@ -101,24 +105,24 @@ def tc_roofline(rows, K, l, nprod, avg_ms, hbm_peak, tc_peak):
 
 def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
     """Roofline of one FP64-emulated product launch (k_oz_gemm): rows x K
-    operand in 7 BF16 digits, l columns in 48-column tiles.
+    operand in 8 BF16 digits, l columns in 48-column tiles.
 
-    Bytes: the digits of A, read once per column tile (14 bytes per element
-    and tile), the panel digits, the FP64 partials.  Flops: the 28 digit
+    Bytes: the digits of A, read once per column tile (16 bytes per element
+    and tile), the panel digits, the FP64 partials.  Flops: the 36 digit
     products per element the tensor pipe executes (N padded to the tiles)."""
     nt = (l + 47) // 48
     t = avg_ms / 1e3
-    hw_flops = 28 * 2.0 * rows * K * nt * 48
-    nbytes = 14.0 * rows * K * nt + 14.0 * K * nt * 48 + 8.0 * rows * nt * 48
+    hw_flops = 36 * 2.0 * rows * K * nt * 48
+    nbytes = 16.0 * rows * K * nt + 16.0 * K * nt * 48 + 8.0 * rows * nt * 48
     t_tensor = hw_flops / (tc_peak * 1e12)
     t_hbm = nbytes / (hbm_peak * 1e9)
     tensor = t_tensor >= t_hbm
     ach = hw_flops / t / 1e12 if tensor else nbytes / t / 1e9
     peak = tc_peak if tensor else hbm_peak
-    return {"kernel": "k_oz_gemm (FP64 product as 28 exact BF16 digit products, tcgen05)",
+    return {"kernel": "k_oz_gemm (FP64 product as 36 exact BF16 digit products, tcgen05)",
             "bound": "tensor" if tensor else "hbm", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak,
-            "achieved_basis": "tensor-pipe MMA flops (28 digit products, N padded to %d)" % (nt * 48)
+            "achieved_basis": "tensor-pipe MMA flops (36 digit products, N padded to %d)" % (nt * 48)
             if tensor else "bytes of the digits of A per column tile + panel digits + partials",
             "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
             "avg_launch_ms": avg_ms}
@@ -577,6 +581,13 @@ def main():
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
                     "launches_timed": pass_launches, "avg_launch_ms": avg_pass_ms}
         dtype = "f64"
+    elif w["mode"] == "FP64_EMU":
+        roofline = oz_roofline(max(m, n), min(m, n), l, avg_pass_ms, hbm_peak, bf16_sus) if avg_pass_ms else None
+        if roofline:
+            roofline["traffic"] = None
+            roofline["peak_source"] = "%s (MEASURED_PEAKS.json: HBM copy GB/s, bf16 sustained TFLOP/s)" % peak_src
+            roofline["launches_timed"] = pass_launches
+        dtype = "f64-emulated (bf16 digit products, exact sums)"
     else:
         nprod = 3 if w["mode"] == "BF16X3" else 1
         roofline = tc_roofline(max(m, n), min(m, n), l, nprod, avg_pass_ms, hbm_peak, bf16_sus)
@@ -671,7 +682,7 @@ def main():
         Qa_n, L_n, Qb_n = (t.numpy() for t in out_host)
         Ag = oracle.reconstruct(Qa_n, L_n, Qb_n, k)
         Ac = oracle.reconstruct(ref["Q"], ref["L"], ref["P"], k)
-        if w["mode"] == "FP64":
+        if w["mode"] in ("FP64", "FP64_EMU"):
             line["parity"] = {"rel_fro_diff_rank_k": float(np.linalg.norm(Ag - Ac) / np.linalg.norm(A_np)),
                               "tol": 1e-11}
         else:

@@ -7,32 +7,35 @@
 //
 // Digits.  Row i of an operand X (R x K) gets the exponent e_i with
 // |X[i][k]| < 2^(e_i - 1) for every k.  F = X[i][k] 2^(56 - e_i), rounded to
-// the nearest integer (|F| < 2^55), is written in balanced base 256,
-// F = sum_{s<7} x_s 256^(6-s) with |x_s| <= 128: each digit is an integer that
+// the nearest integer (|F| < 2^55), is written in balanced base 128,
+// F = sum_{s<8} x_s 128^(7-s) with |x_s| <= 64: each digit is an integer that
 // BF16 holds exactly, and X[i][k] = 2^(e_i - 56) F up to 2^(e_i - 57).  A row
 // that holds Inf or NaN has the exponent field 2047 and yields NaN products.
 //
 // Product.  C[i][j] = sum_k X[i][k] Y[j][k] = 2^(e_i + f_j - 112)
-// sum_{s,t} 256^(12 - s - t) I_st with I_st = sum_k x_s[i][k] y_t[j][k].
-// The digit products with s + t <= 6 are kept (28 of 49; the rest weigh
+// sum_{s,t} 128^(14 - s - t) I_st with I_st = sum_k x_s[i][k] y_t[j][k].
+// The digit products with s + t <= 7 are kept (36 of 64; the rest weigh
 // below 2^-55 of 2^(e_i + f_j) per term).  Level lam = s + t gathers its
-// lam + 1 digit products in one TMEM accumulator; over one 32-deep stage
-// |I_lam| <= 7 * 32 * 128^2 < 2^22, so the tensor pipe's FP32 sums are exact
-// integers whatever its rounding.  After every stage the epilogue adds the
-// seven level sums into two 64-bit accumulators per element,
-// hi = sum_{lam<3} I_lam 256^(2-lam) and lo = sum_{lam>=3} I_lam 256^(6-lam),
+// digit products in one TMEM accumulator (48 columns); over one 128-deep
+// window |I_lam| <= 8 * 128 * 64^2 = 2^22, so the tensor pipe's FP32 sums
+// are exact integers whatever its rounding.  After every window the epilogue
+// adds the eight level sums into two 64-bit accumulators per element,
+// hi = sum_{lam<4} I_lam 128^(3-lam) and lo = sum_{lam>=4} I_lam 128^(7-lam),
 // and at the end of a segment writes the FP64 partial
-// 2^(e_i + f_j - 32) hi + 2^(e_i + f_j - 64) lo.  Partials of one tile are
+// 2^(e_i + f_j - 35) hi + 2^(e_i + f_j - 63) lo.  Partials of one tile are
 // added in CTA order (deterministic).
 //
+// MMAs.  The eight Y digit tiles of a stage sit one after the other in shared
+// memory, so X digit s times Y digits t0 .. t0 + c - 1 is one MMA of N = 48 c
+// that lands in the TMEM columns of levels s + t0 .. s + t0 + c - 1: 11 MMAs
+// (N <= 240) per 16-deep k-step instead of 36.
+//
 // Kernel roles (448 threads, one CTA per SM): warp 0 issues the TMA loads of
-// a stage (the 7 digit tiles of X and of Y, 32 deep, 64-byte swizzle), warp 1
-// allocates TMEM (7 levels x 48 columns) and issues the 56 MMAs of a stage
-// level by level, committing each level to its own mbarrier; warps 2-13 (16
-// columns each) drain level lam of stage w while the MMAs of the later levels
-// run, and the MMAs of level lam of stage w + 1 wait only for that drain.
-// Every wait is bounded by a globaltimer deadline (status bit and abort flag
-// on expiry).
+// a stage (the 8 digit tiles of X and of Y, 32 deep, 64-byte swizzle), warp 1
+// allocates TMEM and issues the MMAs; warps 2-13 (16 columns each) drain the
+// eight levels after each window, and the next window's MMAs wait for that
+// drain.  Every wait is bounded by a globaltimer deadline (status bit and
+// abort flag on expiry).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -55,8 +58,9 @@ constexpr int kOzStages = 2;
 constexpr uint32_t kOzRowBytes = kOzBK * 2;                        // 64 bytes: one swizzle row
 constexpr uint32_t kOzXTile = kOzBM * kOzRowBytes;                 // one digit of X: 8 KB
 constexpr uint32_t kOzYTile = kOzBN * kOzRowBytes;                 // one digit of Y: 3 KB
-constexpr uint32_t kOzStageBytes = kOzDigits * (kOzXTile + kOzYTile);   // 77 KB
-constexpr uint32_t kOzTmemCols = 512;                              // >= kOzDigits * kOzBN, a power of two
+constexpr uint32_t kOzStageBytes = kOzDigits * (kOzXTile + kOzYTile);   // 88 KB
+constexpr int kOzWindow = 4;                                       // stages (32-deep) per exact window
+constexpr uint32_t kOzTmemCols = 512;                              // >= kOzDigits * kOzBN = 384, a power of two
 constexpr int kOzMagic = 0x4B400000;                               // bits of 1.5 * 2^23
 
 // K-major tile with 64-byte rows and the 64-byte swizzle (8-row groups 512 B apart).
@@ -70,12 +74,18 @@ __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
-            "r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
+}
+
+// Element (digit s, row r, k) of the k-chunked digit layout (rows x Kp per digit).
+__device__ __forceinline__ int64_t oz_idx(int s, int64_t r, int64_t k, int64_t rows, int64_t Kp) {
+    return (int64_t)s * rows * Kp + (k >> 5) * rows * 32 + r * 32 + (k & 31);
 }
 
 __device__ __forceinline__ uint64_t mad_wide_u(uint32_t a, uint32_t b, uint64_t c) {
@@ -124,8 +134,8 @@ __device__ __forceinline__ uint16_t digit_bf16(int d) {
 // Biased exponent field of x (0 for zero and subnormals).
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
-// The 7 balanced base-256 digits of round(x 2^(56 - e)), |x| < 2^(e - 1).
-__device__ __forceinline__ void digits7(double x, int e, int* d) {
+// The 8 balanced base-128 digits of round(x 2^(56 - e)), |x| < 2^(e - 1).
+__device__ __forceinline__ void digits8(double x, int e, int* d) {
     const long long bits = __double_as_longlong(x);
     int eb = (int)((bits >> 52) & 0x7FF);
     long long mant = bits & 0xFFFFFFFFFFFFFLL;
@@ -138,13 +148,13 @@ __device__ __forceinline__ void digits7(double x, int e, int* d) {
     else F = 0;
     if (bits < 0) F = -F;
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-        const int w = 8 * (6 - s);
+    for (int s = 0; s < 7; ++s) {
+        const int w = 7 * (7 - s);
         const long long q = (F + (1LL << (w - 1))) >> w;
         d[s] = (int)q;
         F -= q * (1LL << w);
     }
-    d[6] = (int)F;
+    d[7] = (int)F;
 }
 
 // ---------------------------------------------------------------------------
@@ -157,11 +167,10 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
           const int* __restrict__ ey_raw, double* __restrict__ part, uint32_t* __restrict__ status,
           uint64_t timeout_ns, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
-    constexpr uint32_t IDESC = idesc_bf16_f32(kOzBM, kOzBN);
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], accf_bar[kOzDigits], acce_bar[kOzDigits], drain_bar;
+    __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], accf_bar, acce_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ int issued_sh, consumed_sh;
@@ -174,7 +183,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOzStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int l = 0; l < kOzDigits; ++l) { mbar_init(&accf_bar[l], 1); mbar_init(&acce_bar[l], kOzEpiThreads); }
+        mbar_init(&accf_bar, 1);
+        mbar_init(&acce_bar, kOzEpiThreads);
         mbar_init(&drain_bar, 1);
         abort_sh = 0;
         issued_sh = 0;
@@ -205,53 +215,62 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     }
                 }
                 const int64_t tile = it / KI;
-                const int k0 = (int)(it - tile * KI) * kOzBK;
+                const int kc = (int)(it - tile * KI);
                 int64_t mt;
                 int nt;
                 oz_tile(tile, NT, upper, &mt, &nt);
                 unsigned char* st = smem + (size_t)s * kOzStageBytes;
                 mbar_expect_tx(&full_bar[s], kOzStageBytes);
-                tma_load_3d(st, &tmX, &full_bar[s], k0, (int)(mt * kOzBM), 0);
-                tma_load_3d(st + kOzDigits * kOzXTile, &tmY, &full_bar[s], k0, nt * kOzBN, 0);
+                tma_load_4d(st, &tmX, &full_bar[s], 0, (int)(mt * kOzBM), kc, 0);
+                tma_load_4d(st + kOzDigits * kOzXTile, &tmY, &full_bar[s], 0, nt * kOzBN, kc, 0);
                 issued_sh = li + 1;
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer: level by level, each level committed on its own
+        // ---------------- MMA issuer.  A window is the stages of one tile with
+        // k-chunks kOzWindow w .. kOzWindow w + 3 (clipped to the CTA's range).
         if (lane == 0) {
-            int li = 0;
+            int li = 0, win = -1;
             bool ok = true;
             for (int64_t it = it_begin; ok && it < it_end; ++it, ++li) {
+                const int kc = (int)(it % KI);
+                const bool wfirst = (it == it_begin) || (kc % kOzWindow == 0);
+                const bool wlast = (it + 1 == it_end) || (kc % kOzWindow == kOzWindow - 1) || (kc + 1 == KI);
                 const int s = li % kOzStages;
                 if (!mbar_wait(&full_bar[s], (uint32_t)((li / kOzStages) & 1), deadline, &abort_sh)) {
                     abort_sh = 1;
                     ok = false;
                     break;
                 }
-                tc_fence_after();
-                const uint32_t xa = smem_u32(smem + (size_t)s * kOzStageBytes);
-                const uint64_t dX = sdesc_k_sw64(xa), dY = sdesc_k_sw64(xa + kOzDigits * kOzXTile);
-                for (int lam = 0; lam < kOzDigits; ++lam) {
-                    if (li > 0 && !mbar_wait(&acce_bar[lam], (uint32_t)((li - 1) & 1), deadline, &abort_sh)) {
+                if (wfirst) {
+                    ++win;
+                    // the epilogue has read the previous window's levels out of TMEM
+                    if (win > 0 && !mbar_wait(&acce_bar, (uint32_t)((win - 1) & 1), deadline, &abort_sh)) {
                         abort_sh = 1;
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t dt = tmem_base + (uint32_t)(lam * kOzBN);
+                }
+                tc_fence_after();
+                const uint32_t xa = smem_u32(smem + (size_t)s * kOzStageBytes);
+                const uint64_t dX = sdesc_k_sw64(xa), dY = sdesc_k_sw64(xa + kOzDigits * kOzXTile);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        for (int sx = 0; sx <= lam; ++sx) {
-                            const int ty = lam - sx;
+                for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                    for (int sx = 0; sx < kOzDigits; ++sx) {
+#pragma unroll
+                        for (int t0 = 0; t0 < kOzDigits - sx; t0 += 5) {
+                            const int cnt = (kOzDigits - sx - t0) < 5 ? (kOzDigits - sx - t0) : 5;
                             const uint64_t a = dX + (uint64_t)((sx * kOzXTile + kk * 32) >> 4);
-                            const uint64_t b = dY + (uint64_t)((ty * kOzYTile + kk * 32) >> 4);
-                            tc_mma_bf16(dt, a, b, IDESC, (kk | sx) ? 1u : 0u);
+                            const uint64_t b = dY + (uint64_t)((t0 * kOzYTile + kk * 32) >> 4);
+                            const uint32_t idesc = idesc_bf16_f32(kOzBM, cnt * kOzBN);
+                            tc_mma_bf16(tmem_base + (uint32_t)((sx + t0) * kOzBN), a, b, idesc,
+                                        (wfirst && kk == 0 && sx == 0) ? 0u : 1u);
                         }
                     }
-                    tc_commit(&accf_bar[lam]);
                 }
-                if (!ok) break;
                 tc_commit(&empty_bar[s]);
+                if (wlast) tc_commit(&accf_bar);
                 consumed_sh = li + 1;
             }
             // all MMAs issued by this thread complete before TMEM is released
@@ -264,7 +283,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
         }
     } else {
         // ---------------- epilogue: exact level sums -> (hi, lo) -> FP64 partials.
-        // The FP32 level value v (an integer, |v| < 2^22) is read as the bits
+        // The FP32 level value v (an integer, |v| <= 2^22) is read as the bits
         // of v + 1.5 * 2^23, i.e. kOzMagic + v; the bias kOzMagic * weight is
         // removed once per segment (unsigned arithmetic wraps exactly).
         const int q = warp & 3;                 // TMEM lane quarter of this warp
@@ -275,34 +294,37 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
         for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
         const int n_it = (int)(it_end - it_begin);
         int kc = (int)(it_begin % KI), tl = 0;  // k-chunk within the tile; tile relative to the first one
-        int nwin = 0;
+        int win = -1, nwin = 0;
         bool ok = true;
         for (int li = 0; ok && li < n_it; ++li) {
+            const bool wfirst = (li == 0) || (kc % kOzWindow == 0);
+            const bool tile_end = (li + 1 == n_it) || (kc + 1 == KI);
+            const bool wlast = tile_end || (kc % kOzWindow == kOzWindow - 1);
+            if (wfirst) ++win;
+            if (wlast) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar, (uint32_t)(win & 1), deadline, &abort_sh));
+                if (!ok) {
+                    abort_sh = 1;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll
-            for (int lam = 0; lam < kOzDigits; ++lam) {
-                if (ok) {
-                    ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[lam], (uint32_t)(li & 1), deadline, &abort_sh));
-                    if (!ok) {
-                        abort_sh = 1;
-                    } else {
-                        const uint32_t wgt = 1u << (8 * ((lam < 3 ? 2 : 6) - lam));
-                        tc_fence_after();
-                        float v[16];
-                        tmem_ld16(tmem_base + (uint32_t)(lam * kOzBN + g * 16) + ((uint32_t)(q * 32) << 16), v);
-                        tc_fence_before();
-                        mbar_arrive(&acce_bar[lam]);
+                for (int lam = 0; lam < kOzDigits; ++lam) {
+                    const uint32_t wgt = 1u << (7 * ((lam < 4 ? 3 : 7) - lam));
+                    float v[16];
+                    tmem_ld16(tmem_base + (uint32_t)(lam * kOzBN + g * 16) + ((uint32_t)(q * 32) << 16), v);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const uint32_t bv = __float_as_uint(v[j] + 12582912.0f);
-                            if (lam < 3) hi[j] = mad_wide_u(bv, wgt, hi[j]);
-                            else lo[j] = mad_wide_u(bv, wgt, lo[j]);
-                        }
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t bv = __float_as_uint(v[j] + 12582912.0f);
+                        if (lam < 4) hi[j] = mad_wide_u(bv, wgt, hi[j]);
+                        else lo[j] = mad_wide_u(bv, wgt, lo[j]);
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&acce_bar);
+                ++nwin;
             }
-            if (!ok) break;
-            ++nwin;
-            if (li + 1 == n_it || kc + 1 == KI) {
+            if (tile_end) {
                 const int64_t tile = it_begin / KI + tl;
                 int64_t mt;
                 int nt;
@@ -310,10 +332,9 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                 const int64_t row = mt * kOzBM + rloc;
                 const int exr = row < Rx ? ex_raw[row] : 0;
                 const int ei = exr - 1021;
-                // bias added per stage: kOzMagic (2^16 + 2^8 + 1) to hi, kOzMagic (2^24 + 2^16 + 2^8 + 1) to lo
-                const uint64_t bh = (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 16) + (1u << 8) + 1u);
-                const uint64_t bl =
-                    (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 24) + (1u << 16) + (1u << 8) + 1u);
+                // bias added per window to each of hi and lo: kOzMagic (2^21 + 2^14 + 2^7 + 1)
+                const uint64_t bias =
+                    (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 21) + (1u << 14) + (1u << 7) + 1u);
                 double* slot = part + ((size_t)c * smax + (size_t)tl) * (size_t)(kOzBM * kOzBN);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -321,11 +342,11 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     const int64_t col = (int64_t)nt * kOzBN + cl;
                     const int eyr = col < Ry ? ey_raw[col] : 0;
                     const int ej = eyr - 1021;
-                    const int64_t h = (int64_t)(hi[j] - bh), l = (int64_t)(lo[j] - bl);
+                    const int64_t h = (int64_t)(hi[j] - bias), l = (int64_t)(lo[j] - bias);
                     // a row holding Inf or NaN (exponent field 2047) makes its products NaN
                     const double val = (exr >= 2047 || eyr >= 2047)
                                            ? __longlong_as_double(0x7FF8000000000000LL)
-                                           : scale2((double)h, ei + ej - 32) + scale2((double)l, ei + ej - 64);
+                                           : scale2((double)h, ei + ej - 35) + scale2((double)l, ei + ej - 63);
                     slot[(size_t)cl * kOzBM + rloc] = val;
                     hi[j] = 0;
                     lo[j] = 0;
@@ -407,12 +428,13 @@ __global__ void k_oz_panel_exp(int64_t rows, int N, const double* __restrict__ P
     if (mx > 0) atomicMax(&eraw[j], mx);
 }
 
-// Digits of P^T: S[d][j][r] for column j of the panel (scale from eraw[j]).
+// Digits of P^T (rows N, contraction over the panel rows, zero digits up to
+// the padded contraction length) with the column scales eraw[j].
 __global__ void k_oz_panel_slice(int64_t rows, int N, const double* __restrict__ P, int64_t ldp,
-                                 const int* __restrict__ eraw, uint16_t* __restrict__ S, int64_t ldS,
-                                 int64_t slice_stride, const int* __restrict__ cond) {
+                                 const int* __restrict__ eraw, uint16_t* __restrict__ S, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
     __shared__ uint16_t sd[kOzDigits][32][33];
+    const int64_t Kp = oz_kpad(rows);
     const int64_t r0 = (int64_t)blockIdx.y * 32;
     const int j0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -422,18 +444,17 @@ __global__ void k_oz_panel_slice(int64_t rows, int N, const double* __restrict__
         const int64_t r = r0 + rr;
         const double x = (r < rows && j < N) ? P[r * ldp + j] : 0.0;
         int d[kOzDigits];
-        digits7(x, e, d);
+        digits8(x, e, d);
 #pragma unroll
         for (int s = 0; s < kOzDigits; ++s) sd[s][tx][rr] = digit_bf16(d[s]);
     }
     __syncthreads();
-    const int64_t r = r0 + tx;
-    if (r >= rows) return;
+    const int64_t r = r0 + tx;   // < Kp: the grid covers the padded contraction exactly
     for (int jj = ty; jj < 32; jj += 8) {
         const int jc = j0 + jj;
         if (jc >= N) break;
 #pragma unroll
-        for (int s = 0; s < kOzDigits; ++s) S[(int64_t)s * slice_stride + (int64_t)jc * ldS + r] = sd[s][jj][tx];
+        for (int s = 0; s < kOzDigits; ++s) S[oz_idx(s, jc, r, N, Kp)] = sd[s][jj][tx];
     }
 }
 
@@ -464,12 +485,14 @@ __global__ void k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int6
     if (ty == 0 && c0 + tx < n && cmax[tx] > 0) atomicMax(&ec[c0 + tx], cmax[tx]);
 }
 
-// Digits of A (row scales) and of A^T (column scales) from one read of a 32 x 32 tile.
+// Digits of A (row scales; rows m, contraction n) and of A^T (column scales;
+// rows n, contraction m) from one read of a 32 x 32 tile; the grid covers
+// both padded contraction lengths, whose digits are zero.
 template <typename Tin>
 __global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, const int* __restrict__ er,
-                             const int* __restrict__ ec, uint16_t* __restrict__ Srow, int64_t ldr, int64_t srow_stride,
-                             uint16_t* __restrict__ Scol, int64_t ldcol, int64_t scol_stride) {
+                             const int* __restrict__ ec, uint16_t* __restrict__ Srow, uint16_t* __restrict__ Scol) {
     __shared__ uint16_t sd[kOzDigits][32][33];
+    const int64_t mp = oz_kpad(m), np = oz_kpad(n);
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t cc = c0 + tx;
@@ -479,26 +502,25 @@ __global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, in
         const bool in = r < m && cc < n;
         const double x = in ? load_a(A, r * lda + cc) : 0.0;
         int d[kOzDigits];
-        if (Srow && in) {
-            digits7(x, er[r] - 1021, d);
+        if (Srow && r < m) {
+            digits8(x, er[r] - 1021, d);
 #pragma unroll
-            for (int s = 0; s < kOzDigits; ++s) Srow[(int64_t)s * srow_stride + r * ldr + cc] = digit_bf16(d[s]);
+            for (int s = 0; s < kOzDigits; ++s) Srow[oz_idx(s, r, cc, m, np)] = digit_bf16(d[s]);
         }
         if (Scol) {
-            digits7(x, ecol, d);
+            digits8(x, ecol, d);
 #pragma unroll
             for (int s = 0; s < kOzDigits; ++s) sd[s][tx][rr] = digit_bf16(d[s]);
         }
     }
     if (!Scol) return;
     __syncthreads();
-    const int64_t r = r0 + tx;
-    if (r >= m) return;
+    const int64_t r = r0 + tx;   // < mp
     for (int jj = ty; jj < 32; jj += 8) {
         const int64_t jc = c0 + jj;
         if (jc >= n) break;
 #pragma unroll
-        for (int s = 0; s < kOzDigits; ++s) Scol[(int64_t)s * scol_stride + jc * ldcol + r] = sd[s][jj][tx];
+        for (int s = 0; s < kOzDigits; ++s) Scol[oz_idx(s, jc, r, n, mp)] = sd[s][jj][tx];
     }
 }
 
@@ -519,16 +541,17 @@ PFN_encodeTiled encode_fn() {
     return fn;
 }
 
-// 3-D map over the 7 digit matrices of an operand: {K, rows, digit}, box {32, box_rows, 7}.
-bool make_map_oz(CUtensorMap* map, const OzOperand& op, int64_t K, int box_rows) {
+// 4-D map over the k-chunked digits of an operand: {32, rows, chunks, digit},
+// box {32, box_rows, 1, 7} (one stage: a 32-deep block of box_rows rows, all digits).
+bool make_map_oz(CUtensorMap* map, const OzOperand& op, int box_rows) {
     PFN_encodeTiled fn = encode_fn();
-    if (!fn || !op.S || op.rows < 1 || K < 1) return false;
-    if (op.ld < K || (op.ld % 8) != 0 || op.slice_stride < op.rows * op.ld || (op.slice_stride % 8) != 0) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)op.rows, (cuuint64_t)kOzDigits};
-    cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)op.slice_stride * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)kOzDigits};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(op.S), dims, strides, box, estr,
+    if (!fn || !op.S || op.rows < 1 || op.K < 1) return false;
+    const int64_t Kp = oz_kpad(op.K);
+    cuuint64_t dims[4] = {32, (cuuint64_t)op.rows, (cuuint64_t)(Kp / 32), (cuuint64_t)kOzDigits};
+    cuuint64_t strides[3] = {64, (cuuint64_t)op.rows * 64, (cuuint64_t)op.rows * Kp * 2};
+    cuuint32_t box[4] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, 1, (cuuint32_t)kOzDigits};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(op.S), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -556,13 +579,12 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     return g;
 }
 
-cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, int64_t K, const OzGeom& g, double* part,
-                              double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
-                              cudaEvent_t after_gemm) {
-    if (g.tiles < 1 || Y.rows > (int64_t)g.NT * kOzBN || !X.eraw || !Y.eraw) return cudaErrorInvalidValue;
+cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, double* C,
+                              int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s, cudaEvent_t after_gemm) {
+    if (g.tiles < 1 || Y.rows > (int64_t)g.NT * kOzBN || !X.eraw || !Y.eraw || X.K != Y.K) return cudaErrorInvalidValue;
     CUtensorMap mx, my;
-    if (!make_map_oz(&mx, X, K, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
-    if (!make_map_oz(&my, Y, K, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
+    if (!make_map_oz(&mx, X, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
+    if (!make_map_oz(&my, Y, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
     const size_t smem = (size_t)kOzStages * kOzStageBytes + 1024;
     cudaError_t e = PBQ_DBG(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (e != cudaSuccess) return e;
@@ -588,33 +610,32 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, int64_t K,
     return cudaGetLastError();
 }
 
-cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, int64_t ldS,
-                            int64_t slice_stride, const int* cond, cudaStream_t s) {
+cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, const int* cond,
+                            cudaStream_t s) {
     if (rows < 1 || N < 1 || N > 256) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(eraw, 0, sizeof(int) * (size_t)N, s);
     if (e != cudaSuccess) return e;
     k_oz_panel_exp<<<(unsigned)((rows + 63) / 64), 256, 0, s>>>(rows, N, P, ldp, eraw, cond);
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
-    k_oz_panel_slice<<<grid, block, 0, s>>>(rows, N, P, ldp, eraw, (uint16_t*)S, ldS, slice_stride, cond);
+    k_oz_panel_slice<<<grid, block, 0, s>>>(rows, N, P, ldp, eraw, (uint16_t*)S, cond);
     count_launches(2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
-                        int64_t ldr, int64_t srow_stride, void* Scol, int64_t ldcol, int64_t scol_stride,
-                        cudaStream_t s) {
+                        void* Scol, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(er, 0, sizeof(int) * (size_t)m, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ec, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
     if (a_f32) {
         k_oz_a_exp<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec);
-        k_oz_a_slice<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, (uint16_t*)Srow, ldr,
-                                                   srow_stride, (uint16_t*)Scol, ldcol, scol_stride);
+        k_oz_a_slice<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, (uint16_t*)Srow,
+                                                   (uint16_t*)Scol);
     } else {
         k_oz_a_exp<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec);
-        k_oz_a_slice<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, (uint16_t*)Srow, ldr,
-                                                    srow_stride, (uint16_t*)Scol, ldcol, scol_stride);
+        k_oz_a_slice<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, (uint16_t*)Srow,
+                                                    (uint16_t*)Scol);
     }
     count_launches(2);
     return cudaGetLastError();

@@ -5,20 +5,25 @@
 
 namespace pbq {
 
-constexpr int kOzDigits = 7;    // balanced base-256 digits per element (56 bits)
+constexpr int kOzDigits = 8;    // balanced base-128 digits per element (56 bits)
 constexpr int kOzBM = 128;      // output rows per tile (one TMEM lane per row)
 constexpr int kOzBN = 48;       // output columns per tile
 constexpr int kOzBK = 32;       // contraction depth of one shared-memory stage
 
-// One operand in digit form: kOzDigits BF16 matrices of `rows` x K (K-major,
-// leading dimension ld elements, digit d at S + d*slice_stride), and the
+// One operand in digit form: kOzDigits BF16 matrices of `rows` x K and the
 // per-row maximum biased FP64 exponent eraw[rows] (the row scale is
-// 2^(eraw - 1021)).
+// 2^(eraw - 1021)).  Layout ("k-chunked"): digit s, row r, contraction index
+// k at S[s * rows * Kp + (k / 32) * rows * 32 + r * 32 + k % 32], Kp = K
+// rounded up to 32 with zero digits, so the 32-deep block of a row tile that
+// one stage loads is a single contiguous run per digit.
 struct OzOperand {
     const void* S = nullptr;
-    int64_t rows = 0, ld = 0, slice_stride = 0;
+    int64_t rows = 0, K = 0;
     const int* eraw = nullptr;
 };
+__host__ __device__ inline int64_t oz_kpad(int64_t K) { return (K + 31) / 32 * 32; }
+// Bytes of the digits of a rows x K operand.
+inline size_t oz_digit_bytes(int64_t rows, int64_t K) { return 2 * (size_t)kOzDigits * (size_t)rows * oz_kpad(K); }
 
 // Work split of one product C (Mrows x N) = X Y^T over K: 128 x 48 tiles
 // (with `upper`, only the tiles that touch the upper triangle), stream-K over
@@ -30,26 +35,23 @@ struct OzGeom {
 };
 OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms);
 
-// Leading dimension of a digit matrix with contraction length K.
-inline int64_t oz_ld(int64_t K) { return (K + 63) / 64 * 64; }
-
 // C[i*ldc + j] = sum_k X[i][k] Y[j][k] (FP64), i < X.rows, j < Y.rows.
 // cond (device, optional): nothing runs when *cond == 0.
-cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, int64_t K, const OzGeom& g, double* part,
-                              double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
+// (X.K == Y.K is the contraction length.)
+cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, double* C,
+                              int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
                               cudaEvent_t after_gemm = nullptr);
 
 // Panel P (rows x N FP64, ld ldp) as the operand P^T (N rows, contraction
-// over the panel rows): column exponents into eraw[N] and digits into S
-// (ld ldS, digit stride slice_stride).
-cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, int64_t ldS,
-                            int64_t slice_stride, const int* cond, cudaStream_t s);
+// over the panel rows): column exponents into eraw[N] and digits into S, laid
+// out as an OzOperand {S, N, rows}.
+cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, const int* cond,
+                            cudaStream_t s);
 
-// A (m x n, FP64 or FP32, lda) as both operands: A itself (rows m, row
-// exponents er, digits Srow) and A^T (rows n, column exponents ec, digits
-// Scol).  Either digit set may be null (its exponents are still formed).
+// A (m x n, FP64 or FP32, lda) as both operands: A itself (OzOperand {Srow,
+// m, n}, row exponents er) and A^T ({Scol, n, m}, column exponents ec).
+// Either digit set may be null (its exponents are still formed).
 cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
-                        int64_t ldr, int64_t srow_stride, void* Scol, int64_t ldcol, int64_t scol_stride,
-                        cudaStream_t s);
+                        void* Scol, cudaStream_t s);
 
 }  // namespace pbq

@@ -43,8 +43,6 @@ struct pbpqlp_plan_s {
     // FP64-accurate tensor-core products (digit form): Grams and R = Q^T D in
     // every mode (oz_gram), the products with A and A^T in MODE_FP64_EMU (emu)
     bool oz_gram = false, emu = false;
-    int64_t ldz = 0;                    // leading dim of the panel digit matrices (K up to max(m, n))
-    int64_t ldz_n = 0, ldz_m = 0;       // leading dims of the digit matrices of A (K = n) and A^T (K = m)
     OzGeom og_gm, og_gn, og_nn, og_tn;  // Grams over m / n rows; C = A Y; C = A^T Y
     size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0;
     size_t off_ozEr = 0, off_ozEc = 0, off_ozArow = 0, off_ozAcol = 0;
@@ -205,13 +203,12 @@ int tc_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, 
     return PBPQLP_OK;
 }
 
-// Digit-form operand over a panel digit buffer (l rows, contraction up to max(m, n)).
-OzOperand panel_digits(const pbpqlp_plan_s* P, void* S, const int* E) {
+// Digit-form operand of a panel transposed: N rows (its columns), contraction over its `rows` rows.
+OzOperand panel_digits(void* S, const int* E, int N, int64_t rows) {
     OzOperand op;
     op.S = S;
-    op.rows = P->l;
-    op.ld = P->ldz;
-    op.slice_stride = (int64_t)P->l * P->ldz;
+    op.rows = N;
+    op.K = rows;
     op.eraw = E;
     return op;
 }
@@ -226,26 +223,23 @@ int emu_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_
     OzOperand X;
     X.S = transA ? w.ozAcol : w.ozArow;
     X.rows = transA ? P->n : P->m;
-    X.ld = transA ? P->ldz_m : P->ldz_n;
-    X.slice_stride = X.rows * X.ld;
+    X.K = K;
     X.eraw = transA ? w.ozEc : w.ozEr;
-    OzOperand Yd = panel_digits(P, w.ozS2, w.ozE2);
-    Yd.rows = N;
-    PBQ_TRY(launch_oz_panel(K, N, Y, ldy, w.ozE2, w.ozS2, P->ldz, Yd.slice_stride, nullptr, s));
+    const OzOperand Yd = panel_digits(w.ozS2, w.ozE2, N, K);
+    PBQ_TRY(launch_oz_panel(K, N, Y, ldy, w.ozE2, w.ozS2, nullptr, s));
     OzGeom g = transA ? P->og_tn : P->og_nn;
     if (N != P->l) g = oz_geometry(X.rows, N, K, false, P->num_sms);
     const int64_t cap = transA ? P->og_tn.part_doubles : P->og_nn.part_doubles;
     if (g.part_doubles > cap) return PBPQLP_EINVAL;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-    PBQ_TRY(launch_oz_product(X, Yd, K, g, w.ozpart, C, ldc, w.status, nullptr, s, ev.second));
+    PBQ_TRY(launch_oz_product(X, Yd, g, w.ozpart, C, ldc, w.status, nullptr, s, ev.second));
     return PBPQLP_OK;
 }
 
 // Digits of A (row scales) and of A^T (column scales), once per factorization.
 int emu_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32, int64_t lda) {
-    PBQ_TRY(launch_oz_a(P->m, P->n, A, a_f32, lda, w.ozEr, w.ozEc, w.ozArow, P->ldz_n, P->m * P->ldz_n, w.ozAcol,
-                        P->ldz_m, P->n * P->ldz_m, P->stream));
+    PBQ_TRY(launch_oz_a(P->m, P->n, A, a_f32, lda, w.ozEr, w.ozEc, w.ozArow, w.ozAcol, P->stream));
     return PBPQLP_OK;
 }
 
@@ -264,10 +258,10 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         const int64_t ps = (int64_t)l * ldp;
         // the Cholesky reads only the upper triangle of the Gram
         if (P->oz_gram) {
-            const OzOperand op = panel_digits(P, w.ozS1, w.ozE1);
-            PBQ_TRY(launch_oz_panel(rows, l, src, ldp, w.ozE1, w.ozS1, P->ldz, op.slice_stride, cond, s));
-            PBQ_TRY(launch_oz_product(op, op, rows, rows == P->m ? P->og_gm : P->og_gn, w.ozpart, w.G, l, w.status,
-                                      cond, s));
+            const OzOperand op = panel_digits(w.ozS1, w.ozE1, l, rows);
+            PBQ_TRY(launch_oz_panel(rows, l, src, ldp, w.ozE1, w.ozS1, cond, s));
+            PBQ_TRY(launch_oz_product(op, op, rows == P->m ? P->og_gm : P->og_gn, w.ozpart, w.G, l, w.status, cond,
+                                      s));
         } else {
             PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
             PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
@@ -381,29 +375,25 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->off_work = take(sizeof(double) * (2 * l * l + 2 * l));
     P->off_red = take(sizeof(double) * 2048);
     if (P->oz_gram || P->emu) {
-        P->ldz = oz_ld(m > n ? m : n);
         P->og_gm = oz_geometry(l, (int)l, m, true, P->num_sms);
         P->og_gn = oz_geometry(l, (int)l, n, true, P->num_sms);
         int64_t pd = P->og_gm.part_doubles > P->og_gn.part_doubles ? P->og_gm.part_doubles : P->og_gn.part_doubles;
         if (P->emu) {
-            P->ldz_n = oz_ld(n);
-            P->ldz_m = oz_ld(m);
             P->og_nn = oz_geometry(m, (int)l, n, false, P->num_sms);
             P->og_tn = oz_geometry(n, (int)l, m, false, P->num_sms);
             pd = pd > P->og_nn.part_doubles ? pd : P->og_nn.part_doubles;
             pd = pd > P->og_tn.part_doubles ? pd : P->og_tn.part_doubles;
         }
-        const size_t dig = 2 * (size_t)kOzDigits;   // bytes of one element's 8 BF16 digits
         P->off_ozE1 = take(sizeof(int) * 256);
         P->off_ozE2 = take(sizeof(int) * 256);
-        P->off_ozS1 = take(dig * (size_t)l * P->ldz);
-        P->off_ozS2 = take(dig * (size_t)l * P->ldz);
+        P->off_ozS1 = take(oz_digit_bytes(l, m > n ? m : n));
+        P->off_ozS2 = take(oz_digit_bytes(l, m > n ? m : n));
         P->off_ozpart = take(sizeof(double) * (size_t)pd);
         if (P->emu) {
             P->off_ozEr = take(sizeof(int) * (size_t)m);
             P->off_ozEc = take(sizeof(int) * (size_t)n);
-            P->off_ozArow = take(dig * (size_t)m * P->ldz_n);
-            P->off_ozAcol = take(dig * (size_t)n * P->ldz_m);
+            P->off_ozArow = take(oz_digit_bytes(m, n));
+            P->off_ozAcol = take(oz_digit_bytes(n, m));
         }
     }
     if (mode != PBPQLP_MODE_FP64 && mode != PBPQLP_MODE_FP64_EMU) {
@@ -489,10 +479,10 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
     if (P->oz_gram) {
-        const OzOperand qd = panel_digits(P, w.ozS1, w.ozE1), dd = panel_digits(P, w.ozS2, w.ozE2);
-        PBQ_TRY(launch_oz_panel(m, l, w.Xm, ldp, w.ozE1, w.ozS1, P->ldz, qd.slice_stride, nullptr, s));
-        PBQ_TRY(launch_oz_panel(m, l, w.Dm, ldp, w.ozE2, w.ozS2, P->ldz, dd.slice_stride, nullptr, s));
-        PBQ_TRY(launch_oz_product(qd, dd, m, P->og_gm, w.ozpart, w.R, l, w.status, nullptr, s));
+        const OzOperand qd = panel_digits(w.ozS1, w.ozE1, l, m), dd = panel_digits(w.ozS2, w.ozE2, l, m);
+        PBQ_TRY(launch_oz_panel(m, l, w.Xm, ldp, w.ozE1, w.ozS1, nullptr, s));
+        PBQ_TRY(launch_oz_panel(m, l, w.Dm, ldp, w.ozE2, w.ozS2, nullptr, s));
+        PBQ_TRY(launch_oz_product(qd, dd, P->og_gm, w.ozpart, w.R, l, w.status, nullptr, s));
     } else {
         const int64_t ps = (int64_t)l * ldp;
         PBQ_TRY(launch_upper_product(l, m, w.Xm, w.Dm, ldp, w.part, ps, P->S_gm, P->kc_gm, nullptr, s));
