@@ -65,6 +65,13 @@ bool cholesky_cluster_fits(int l);
 cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double* Rpacked, uint32_t* status, int* ctl,
                                     int pass, cudaStream_t s);
 
+// Cholesky G = R^T R with T = R^{-T} (l x l row-major, lower triangular) by
+// an 8-CTA cluster (kernels_cholinv.cu).  Rpacked, ctl, status and the
+// shifted retry as launch_cholesky.  T may be null.
+bool chol_inv_fits(int l);
+cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rpacked, double* T, uint32_t* status,
+                            int* ctl, int pass, cudaStream_t s);
+
 // Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels; f32
 // solves in FP32 (the mixed modes) instead of FP64.
 cudaError_t launch_trsm_rows(int64_t rows, int l, const double* Rpacked, const double* X, int64_t ldx,

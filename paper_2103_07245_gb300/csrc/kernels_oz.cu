@@ -466,7 +466,8 @@ __device__ __forceinline__ double load_a(const Tin* A, int64_t i) {
 // Row and column exponents of A (32 x 32 tiles; block 32 x 8).
 template <typename Tin>
 __global__ void k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, int* __restrict__ er,
-                           int* __restrict__ ec) {
+                           int* __restrict__ ec, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
     __shared__ int cmax[32];
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -490,7 +491,9 @@ __global__ void k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int6
 // both padded contraction lengths, whose digits are zero.
 template <typename Tin>
 __global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, const int* __restrict__ er,
-                             const int* __restrict__ ec, uint16_t* __restrict__ Srow, uint16_t* __restrict__ Scol) {
+                             const int* __restrict__ ec, uint16_t* __restrict__ Srow, uint16_t* __restrict__ Scol,
+                             const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
     __shared__ uint16_t sd[kOzDigits][32][33];
     const int64_t mp = oz_kpad(m), np = oz_kpad(n);
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
@@ -623,19 +626,19 @@ cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, i
 }
 
 cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
-                        void* Scol, cudaStream_t s) {
+                        void* Scol, cudaStream_t s, const int* cond) {
     cudaError_t e = cudaMemsetAsync(er, 0, sizeof(int) * (size_t)m, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ec, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
     if (a_f32) {
-        k_oz_a_exp<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec);
+        k_oz_a_exp<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, cond);
         k_oz_a_slice<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, (uint16_t*)Srow,
-                                                   (uint16_t*)Scol);
+                                                   (uint16_t*)Scol, cond);
     } else {
-        k_oz_a_exp<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec);
+        k_oz_a_exp<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, cond);
         k_oz_a_slice<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, (uint16_t*)Srow,
-                                                    (uint16_t*)Scol);
+                                                    (uint16_t*)Scol, cond);
     }
     count_launches(2);
     return cudaGetLastError();

@@ -51,7 +51,8 @@ cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, i
 // A (m x n, FP64 or FP32, lda) as both operands: A itself (OzOperand {Srow,
 // m, n}, row exponents er) and A^T ({Scol, n, m}, column exponents ec).
 // Either digit set may be null (its exponents are still formed).
+// cond (device, optional): nothing runs when *cond == 0.
 cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
-                        void* Scol, cudaStream_t s);
+                        void* Scol, cudaStream_t s, const int* cond = nullptr);
 
 }  // namespace pbq

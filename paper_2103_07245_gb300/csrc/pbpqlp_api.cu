@@ -44,7 +44,11 @@ struct pbpqlp_plan_s {
     // every mode (oz_gram), the products with A and A^T in MODE_FP64_EMU (emu)
     bool oz_gram = false, emu = false;
     OzGeom og_gm, og_gn, og_nn, og_tn;  // Grams over m / n rows; C = A Y; C = A^T Y
-    size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0;
+    size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0, off_ozEb = 0, off_ozEs = 0;
+    OzGeom og_qb;                       // Qb = Pbar Ptil (n rows, K = l)
+    bool chol_inv = false;              // cluster Cholesky with T = R^{-T}; CholeskyQR solve as a digit product
+    OzGeom og_tr_m, og_tr_n;            // Q = C T^T over m or n rows (K = l)
+    size_t off_T = 0;
     size_t off_ozEr = 0, off_ozEc = 0, off_ozArow = 0, off_ozAcol = 0;
     void* last_ws = nullptr;
     // observability: CUDA event pairs around each A / A^T pass kernel
@@ -62,10 +66,10 @@ struct Ws {
     uint32_t* status;
     int* ctl;
     double* scal;
-    double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red;
+    double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red, *T;
     void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
     float* tcpart;
-    int *ozE1, *ozE2, *ozEr, *ozEc;
+    int *ozE1, *ozE2, *ozEr, *ozEc, *ozEb, *ozEs;
     void *ozS1, *ozS2, *ozArow, *ozAcol;
     double* ozpart;
 };
@@ -88,6 +92,7 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.Pt = (double*)(b + P->off_Pt);
     w.work = (double*)(b + P->off_work);
     w.red = (double*)(b + P->off_red);
+    w.T = P->chol_inv ? (double*)(b + P->off_T) : nullptr;
     const bool mixed = P->nprod > 0, split = P->nprod == 3;
     w.Ahi = mixed ? (void*)(b + P->off_Ahi) : nullptr;
     w.Alo = split ? (void*)(b + P->off_Alo) : nullptr;
@@ -104,6 +109,8 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.ozS1 = oz ? (void*)(b + P->off_ozS1) : nullptr;
     w.ozS2 = oz ? (void*)(b + P->off_ozS2) : nullptr;
     w.ozpart = oz ? (double*)(b + P->off_ozpart) : nullptr;
+    w.ozEb = oz ? (int*)(b + P->off_ozEb) : nullptr;
+    w.ozEs = oz ? (int*)(b + P->off_ozEs) : nullptr;
     w.ozEr = P->emu ? (int*)(b + P->off_ozEr) : nullptr;
     w.ozEc = P->emu ? (int*)(b + P->off_ozEc) : nullptr;
     w.ozArow = P->emu ? (void*)(b + P->off_ozArow) : nullptr;
@@ -266,6 +273,18 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
             PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
             PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
         }
+        if (P->chol_inv) {
+            // dst = src R^{-1} = src T^T as an FP64-accurate digit product
+            PBQ_TRY(launch_chol_inv(l, rows, w.G, w.Rp, w.T, w.status, w.ctl, pass, s));
+            OzOperand xd, yd;
+            xd.S = w.ozS1; xd.rows = rows; xd.K = l; xd.eraw = w.ozEb;
+            yd.S = w.ozS2; yd.rows = l; yd.K = l; yd.eraw = w.ozE2;
+            PBQ_TRY(launch_oz_a(rows, l, src, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s, cond));
+            PBQ_TRY(launch_oz_a(l, l, w.T, 0, l, w.ozE2, w.ozEs, w.ozS2, nullptr, s, cond));
+            PBQ_TRY(launch_oz_product(xd, yd, rows == P->m ? P->og_tr_m : P->og_tr_n, w.ozpart, dst, ldp, w.status,
+                                      cond, s));
+            continue;
+        }
         if (P->cluster_chol) PBQ_TRY(launch_cholesky_cluster(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         else PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s, P->nprod > 0));
@@ -377,7 +396,20 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     if (P->oz_gram || P->emu) {
         P->og_gm = oz_geometry(l, (int)l, m, true, P->num_sms);
         P->og_gn = oz_geometry(l, (int)l, n, true, P->num_sms);
+        P->og_qb = oz_geometry(n, (int)l, l, false, P->num_sms);
         int64_t pd = P->og_gm.part_doubles > P->og_gn.part_doubles ? P->og_gm.part_doubles : P->og_gn.part_doubles;
+        pd = pd > P->og_qb.part_doubles ? pd : P->og_qb.part_doubles;
+        {
+            const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
+            P->chol_inv = P->oz_gram && chol_inv_fits(P->l) && !(nc && nc[0] == '1');
+        }
+        if (P->chol_inv) {
+            P->og_tr_m = oz_geometry(m, (int)l, l, false, P->num_sms);
+            P->og_tr_n = oz_geometry(n, (int)l, l, false, P->num_sms);
+            pd = pd > P->og_tr_m.part_doubles ? pd : P->og_tr_m.part_doubles;
+            pd = pd > P->og_tr_n.part_doubles ? pd : P->og_tr_n.part_doubles;
+            P->off_T = take(sizeof(double) * l * l);
+        }
         if (P->emu) {
             P->og_nn = oz_geometry(m, (int)l, n, false, P->num_sms);
             P->og_tn = oz_geometry(n, (int)l, m, false, P->num_sms);
@@ -386,8 +418,13 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         }
         P->off_ozE1 = take(sizeof(int) * 256);
         P->off_ozE2 = take(sizeof(int) * 256);
-        P->off_ozS1 = take(oz_digit_bytes(l, m > n ? m : n));
-        P->off_ozS2 = take(oz_digit_bytes(l, m > n ? m : n));
+        // a panel as the transposed operand (l rows, K = m or n) or as rows (n rows, K = l)
+        const int64_t mx = m > n ? m : n;
+        const size_t sz = oz_digit_bytes(l, mx) > oz_digit_bytes(mx, l) ? oz_digit_bytes(l, mx) : oz_digit_bytes(mx, l);
+        P->off_ozS1 = take(sz);
+        P->off_ozS2 = take(sz);
+        P->off_ozEb = take(sizeof(int) * (size_t)mx);
+        P->off_ozEs = take(sizeof(int) * 256);
         P->off_ozpart = take(sizeof(double) * (size_t)pd);
         if (P->emu) {
             P->off_ozEr = take(sizeof(int) * (size_t)m);
@@ -491,7 +528,17 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
     if (P->cluster_qr) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
     else PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
-    PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
+    if (P->oz_gram) {
+        // Qb[i][j] = sum_k Pbar[i][k] Ptil[k][j]: Pbar by rows, Ptil^T by rows
+        OzOperand xd, yd;
+        xd.S = w.ozS1; xd.rows = n; xd.K = l; xd.eraw = w.ozEb;
+        yd = panel_digits(w.ozS2, w.ozE2, l, l);
+        PBQ_TRY(launch_oz_a(n, l, w.Xn, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s));
+        PBQ_TRY(launch_oz_panel(l, l, w.Pt, l, w.ozE2, w.ozS2, nullptr, s));
+        PBQ_TRY(launch_oz_product(xd, yd, P->og_qb, w.ozpart, Qb, l, w.status, nullptr, s));
+    } else {
+        PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
+    }
     PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
     return PBPQLP_OK;
 }
