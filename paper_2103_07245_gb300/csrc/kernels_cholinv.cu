@@ -1,15 +1,16 @@
 // Cholesky of the l x l CholeskyQR Gram together with the inverse of its
-// factor, by a thread-block cluster of 8 CTAs: G = R^T R and T = R^{-T}.
+// factor, by a thread-block cluster of 16 CTAs (8 where 16-CTA clusters cannot
+// be scheduled): G = R^T R and T = R^{-T}.
 // With T the CholeskyQR step Q = C R^{-1} = C T^T is one product, which runs
 // on the tensor cores in FP64-accurate digit form (kernels_oz.cu) instead of
 // a row-by-row triangular solve.
 //
 // Method: block right-looking elimination of the augmented matrix [G | I]
 // (row operations with R^{-T} turn it into [R | R^{-T}]), 16-row blocks.
-// Columns of both halves are dealt cyclically over the CTAs (column j lives
-// in CTA j % 8 at local column j / 8, full length l in shared memory), so the
+// Columns of both halves are dealt cyclically over the C CTAs (column j lives
+// in CTA j % C at local column j / C, full length l in shared memory), so the
 // trailing updates, which hold nearly all the l^3 / 3 FMAs, are spread over
-// all 8 SMs.  Block t:
+// all C SMs.  Block t:
 //   (a) every CTA gathers the 16 x 16 diagonal block through distributed
 //       shared memory and factors it (one warp, redundantly: all CTAs take the
 //       same pivot decisions without communicating);
@@ -20,8 +21,14 @@
 //   (c) trailing updates of own columns: S[i][j] -= sum_k R[t,k][i] R[t,k][j]
 //       (a1 <= i <= j) and T[i][j] -= sum_k R[t,k][i] T[t,k][j] (i >= a1);
 //   cluster barrier.
-// Pivot thresholds and the shifted retry (shifted CholeskyQR, Fukaya et al.
-// 2020) follow the one-CTA kernel; ctl / status conventions are the same.
+// FP64 has few lanes per SM on GB300 and long latencies, so the sequential
+// parts are kept short: the diagonal block is factored in LDL^T form (one
+// reciprocal per pivot, an FP32 seed refined by Newton-Raphson steps in FP64;
+// the square roots of all pivots come afterwards, in parallel), and the
+// block-row solve updates all remaining right-hand sides after each unknown
+// (two dependent operations per step).  Pivot thresholds and the shifted retry
+// (shifted CholeskyQR, Fukaya et al. 2020) follow the one-CTA kernel; ctl /
+// status conventions are the same.
 #include <cooperative_groups.h>
 #include <cmath>
 #include <cstdint>
@@ -33,12 +40,52 @@ namespace cg = cooperative_groups;
 namespace pbq {
 
 namespace {
-constexpr int kCiCtas = 8;
+constexpr int kCiCtasMax = 16;
 constexpr int kCiThreads = 512;
 constexpr int kCiNb = 16;
+
+// Latencies measured on GB300: a dependent FP64 FMA takes 64 cycles, an FP64
+// square root ~670 and a division ~430, an FP32 FMA 4.5.  The sequential
+// chains below therefore avoid FP64 square roots and divisions.
+
+// 1/d for a positive normal double: d = m 2^k with m in [1, 2), an FP32 seed
+// for 1/m refined by two Newton-Raphson steps y += y (1 - m y) (each doubles
+// the correct bits: ~24 -> ~48 -> 53), scaled by 2^-k.
+__device__ __forceinline__ double rcp_nr(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF) return 1.0 / d;
+    const int k = eb - 1023;
+    const double m = __longlong_as_double(b - (long long)k * (1LL << 52));
+    double y = (double)__frcp_rn((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+// 1/sqrt(d) for a positive normal double: d = m 4^k with m in [1, 4), an FP32
+// seed for 1/sqrt(m) refined by two Newton-Raphson steps y += y (1 - m y^2) / 2,
+// scaled by 2^-k.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF) return 1.0 / sqrt(d);
+    const int k = (eb - 1023) >> 1;                                   // floor((eb - 1023) / 2)
+    const double m = __longlong_as_double(b - (long long)(2 * k) * (1LL << 52));
+    double y = (double)rsqrtf((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y * y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
 }  // namespace
 
-__global__ void __cluster_dims__(kCiCtas, 1, 1) __launch_bounds__(kCiThreads)
+__global__ void __launch_bounds__(kCiThreads)
 k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
                    double* __restrict__ Tout, uint32_t* __restrict__ status, int* __restrict__ ctl, int pass) {
     if (pass >= 3 && ctl[8 + (pass + 1) / 2] == 0) return;   // uniform over the cluster
@@ -77,14 +124,19 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
         cluster.sync();
         for (int t = 0; t < nblk; ++t) {
             const int a0 = t * kCiNb, a1 = min(l, a0 + kCiNb), nb = a1 - a0;
-            // (a) gather and factor the diagonal block (warp 0 of every CTA)
+            // (a) gather and factor the diagonal block (warp 0 of every CTA).  LDL^T
+            // form: step p needs only 1/d_p (the chain from one pivot to the
+            // next is a reciprocal and two FMAs); the rows of R are scaled by
+            // 1/sqrt(d_p) afterwards, all pivots at once.
             if (warp == 0) {
                 double s[kCiNb];
                 const int j = a0 + lane;
+                double thr_mine = 0.0, d_mine = 1.0;
                 if (lane < nb) {
                     const double* col = cluster.map_shared_rank(Sown, j % C) + (int64_t)(j / C) * l;
 #pragma unroll
                     for (int i = 0; i < kCiNb; ++i) s[i] = (i <= lane) ? col[a0 + i] : 0.0;
+                    if (attempt == 0) thr_mine = tau * G[(int64_t)j * l + j];
                 } else {
 #pragma unroll
                     for (int i = 0; i < kCiNb; ++i) s[i] = 0.0;
@@ -94,49 +146,58 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
                 for (int p = 0; p < kCiNb; ++p) {
                     if (p < nb && f == 0) {
                         const double d = __shfl_sync(0xffffffffu, s[p], p);
-                        const double thr = (attempt == 0) ? tau * G[(int64_t)(a0 + p) * l + a0 + p] : 0.0;
+                        const double thr = __shfl_sync(0xffffffffu, thr_mine, p);
                         f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
                         if (f == 0) {
-                            const double r = sqrt(d);
-                            const double inv = 1.0 / r;
-                            if (lane == p) { s[p] = r; Rinv[p] = inv; }
-                            else if (lane > p) s[p] *= inv;   // R[p][lane]
-                            const double rpk = s[p];
+                            const double c = rcp_nr(d);
+                            if (lane == p) d_mine = d;
+                            const double lk = s[p] * c;   // L[lane][p] = S[p][lane] / d_p
 #pragma unroll
                             for (int i = p + 1; i < kCiNb; ++i) {
-                                const double rpi = __shfl_sync(0xffffffffu, s[p], i);
-                                if (lane >= i) s[i] -= rpi * rpk;
+                                const double spi = __shfl_sync(0xffffffffu, s[p], i);
+                                if (lane >= i) s[i] -= spi * lk;
                             }
                         }
                     }
                 }
-                if (lane < nb) {
+                if (f == 0) {
+                    // R[p][k] = S_p[k] / sqrt(d_p) (p < k), R[k][k] = sqrt(d_k)
+                    const double rs = rsqrt_nr(d_mine);
 #pragma unroll
-                    for (int i = 0; i < kCiNb; ++i) Rtt[i * kCiNb + lane] = (i <= lane) ? s[i] : 0.0;
+                    for (int p = 0; p < kCiNb; ++p) {
+                        const double rsp = __shfl_sync(0xffffffffu, rs, p);
+                        if (lane < nb) Rtt[p * kCiNb + lane] = (p < lane) ? s[p] * rsp : (p == lane ? d_mine * rs : 0.0);
+                    }
+                    if (lane < nb) Rinv[lane] = rs;
                 }
                 if (lane == 0) s_fail = f;
             }
             __syncthreads();
             fail = s_fail;
             if (fail) break;   // every CTA factored the same block: same decision everywhere
-            // (b) block-row solves R_tt^T y = x on own columns (one thread per column)
+            // (b) block-row solves R_tt^T y = x on own columns (one thread per column):
+            // after each unknown all later right-hand sides are updated at once
             if (tid < 2 * ncol) {
                 const bool right = tid >= ncol;
                 const int jl = right ? tid - ncol : tid;
                 const int j = jl * C + rank;
                 if (j < l && (right ? (j < a1) : (j >= a1))) {
                     double* x = (right ? Town : Sown) + (int64_t)jl * l + a0;
-                    double y[kCiNb];
+                    double acc[kCiNb];
 #pragma unroll
-                    for (int k = 0; k < kCiNb; ++k) {
-                        if (k < nb) {
-                            double acc = x[k];
+                    for (int k = 0; k < kCiNb; ++k) acc[k] = (k < nb) ? x[k] : 0.0;
 #pragma unroll
-                            for (int p = 0; p < k; ++p) acc -= Rtt[p * kCiNb + k] * y[p];
-                            y[k] = acc * Rinv[k];
-                            x[k] = y[k];
+                    for (int p = 0; p < kCiNb; ++p) {
+                        if (p < nb) {
+                            const double y = acc[p] * Rinv[p];
+                            acc[p] = y;
+#pragma unroll
+                            for (int k = p + 1; k < kCiNb; ++k) acc[k] -= Rtt[p * kCiNb + k] * y;
                         }
                     }
+#pragma unroll
+                    for (int k = 0; k < kCiNb; ++k)
+                        if (k < nb) x[k] = acc[k];
                 }
             }
             cluster.sync();   // block row t of R is final in its owners
@@ -223,21 +284,73 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-static size_t chol_inv_smem(int l) {
-    const int ncol = (l + kCiCtas - 1) / kCiCtas;
-    return ((size_t)2 * ncol * l + (size_t)kCiNb * l + kCiNb * kCiNb + kCiNb) * sizeof(double);
+// Shared memory of one CTA, at least 120 KB so that no two CTAs of the cluster
+// share an SM (and its FP64 lanes).
+static size_t chol_inv_smem(int l, int C) {
+    const int ncol = (l + C - 1) / C;
+    const size_t need = ((size_t)2 * ncol * l + (size_t)kCiNb * l + kCiNb * kCiNb + kCiNb) * sizeof(double);
+    return need > 120 * 1024 ? need : 120 * 1024;
 }
 
-bool chol_inv_fits(int l) { return l >= 1 && l <= kMaxEll && chol_inv_smem(l) <= 200 * 1024; }
+// Cluster size: 16 CTAs when the device can schedule such clusters with this
+// kernel's shared memory, else the portable 8 (decided once per process).
+static int chol_inv_ctas(int l) {
+    static int best = 0;
+    if (best == 0) {
+        best = 8;
+        cudaFuncAttributes fa;
+        if (cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)chol_inv_smem(kMaxEll, 8)) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, k_chol_inv_cluster) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = kCiCtasMax;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(kCiCtasMax);
+            cfg.blockDim = dim3(kCiThreads);
+            cfg.dynamicSmemBytes = chol_inv_smem(kMaxEll, kCiCtasMax);
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_chol_inv_cluster, &cfg) == cudaSuccess && clusters > 0)
+                best = kCiCtasMax;
+        }
+        cudaGetLastError();
+    }
+    (void)l;
+    return best;
+}
+
+bool chol_inv_fits(int l) { return l >= 1 && l <= kMaxEll && chol_inv_smem(l, 8) <= 200 * 1024; }
 
 cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rp, double* T, uint32_t* status, int* ctl,
                             int pass, cudaStream_t s) {
-    const size_t smem = chol_inv_smem(l);
+    const int C = chol_inv_ctas(l);
+    const size_t smem = chol_inv_smem(l, C);
     cudaError_t e = cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chol_inv_cluster<<<kCiCtas, kCiThreads, smem, s>>>(l, rows, G, Rp, T, status, ctl, pass);
+    if (C > 8 &&
+        (e = cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kCiThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_chol_inv_cluster, l, rows, G, Rp, T, status, ctl, pass);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace pbq
