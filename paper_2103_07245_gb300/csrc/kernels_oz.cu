@@ -463,27 +463,35 @@ __device__ __forceinline__ double load_a(const Tin* A, int64_t i) {
     return (double)A[i];
 }
 
-// Row and column exponents of A (32 x 32 tiles; block 32 x 8).
+// Row and column exponents of A: tiles of 64 rows x 512 columns, one column
+// per thread; row maxima by warp reductions and shared memory, then one
+// atomicMax per row and per column for the tile (maxima are order-free, so
+// the result is deterministic).
 template <typename Tin>
-__global__ void k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, int* __restrict__ er,
-                           int* __restrict__ ec, const int* __restrict__ cond) {
+__global__ void __launch_bounds__(512)
+k_oz_a_exp(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, int* __restrict__ er, int* __restrict__ ec,
+           const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
-    __shared__ int cmax[32];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    if (ty == 0) cmax[tx] = 0;
-    __syncthreads();
+    __shared__ int rmax[16][64];
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c = (int64_t)blockIdx.x * 512 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cm = 0;
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int64_t r = r0 + rr, cc = c0 + tx;
-        const int eb = (r < m && cc < n) ? exp_field(load_a(A, r * lda + cc)) : 0;
+    for (int rr = 0; rr < 64; ++rr) {
+        const int64_t r = r0 + rr;
+        const int eb = (r < m && c < n) ? exp_field(load_a(A, r * lda + c)) : 0;
         cm = max(cm, eb);
-        const int rm = __reduce_max_sync(0xffffffffu, eb);
-        if (tx == 0 && r < m && rm > 0) atomicMax(&er[r], rm);
+        const int w = __reduce_max_sync(0xffffffffu, eb);
+        if (lane == 0) rmax[warp][rr] = w;
     }
-    atomicMax(&cmax[tx], cm);
+    if (c < n && cm > 0) atomicMax(&ec[c], cm);
     __syncthreads();
-    if (ty == 0 && c0 + tx < n && cmax[tx] > 0) atomicMax(&ec[c0 + tx], cmax[tx]);
+    if (threadIdx.x < 64) {
+        int v = 0;
+#pragma unroll
+        for (int w = 0; w < 16; ++w) v = max(v, rmax[w][threadIdx.x]);
+        const int64_t r = r0 + threadIdx.x;
+        if (r < m && v > 0) atomicMax(&er[r], v);
+    }
 }
 
 // Digits of A (row scales; rows m, contraction n) and of A^T (column scales;
@@ -631,12 +639,13 @@ cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t 
     if (e == cudaSuccess) e = cudaMemsetAsync(ec, 0, sizeof(int) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), block(32, 8);
+    dim3 egrid((unsigned)((n + 511) / 512), (unsigned)((m + 63) / 64));
     if (a_f32) {
-        k_oz_a_exp<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, cond);
+        k_oz_a_exp<float><<<egrid, 512, 0, s>>>(m, n, (const float*)A, lda, er, ec, cond);
         k_oz_a_slice<float><<<grid, block, 0, s>>>(m, n, (const float*)A, lda, er, ec, (uint16_t*)Srow,
                                                    (uint16_t*)Scol, cond);
     } else {
-        k_oz_a_exp<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, cond);
+        k_oz_a_exp<double><<<egrid, 512, 0, s>>>(m, n, (const double*)A, lda, er, ec, cond);
         k_oz_a_slice<double><<<grid, block, 0, s>>>(m, n, (const double*)A, lda, er, ec, (uint16_t*)Srow,
                                                     (uint16_t*)Scol, cond);
     }

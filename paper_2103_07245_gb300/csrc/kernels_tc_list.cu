@@ -273,9 +273,16 @@ __global__ void __launch_bounds__(256) k_split_tf32_list(const SplitUnit* __rest
             const int64_t r = u.r0 + k, cc = c0 + tx;
             float h = 0.f, l = 0.f;
             if (r < u.m && cc < u.n) {
-                const double x = u.a_f32 ? (double)((const float*)u.A)[r * u.lda + cc] : ((const double*)u.A)[r * u.lda + cc];
-                h = to_tf32((float)x);
-                l = to_tf32((float)(x - (double)h));
+                // an FP32 A is split in FP32 (x - hi exact); an FP64 A in FP64
+                if (u.a_f32) {
+                    const float x = ((const float*)u.A)[r * u.lda + cc];
+                    h = to_tf32(x);
+                    l = to_tf32(x - h);
+                } else {
+                    const double x = ((const double*)u.A)[r * u.lda + cc];
+                    h = to_tf32((float)x);
+                    l = to_tf32((float)(x - (double)h));
+                }
                 u.hi[r * u.ldh + cc] = h;
                 if (u.lo) u.lo[r * u.ldh + cc] = l;
             }
