@@ -19,6 +19,11 @@ constexpr uint32_t kStTimeout = 8u;    // bounded wait gave up
 // Process-wide launch counter (incremented by every launcher below).
 void count_launches(int64_t n);
 int64_t launch_count();
+// cudaFuncAttributeMaxDynamicSharedMemorySize for func on the current device,
+// set through the driver only when a larger size than before is asked for
+// (the attribute call costs host time on every launch otherwise).
+cudaError_t func_smem_attr(const void* func, size_t bytes);
+
 // Report a failing CUDA call on stderr when PBPQLP_DEBUG=1; returns e.
 cudaError_t debug_report(cudaError_t e, const char* what, const char* file, int line);
 #define PBQ_DBG(expr) ::pbq::debug_report((expr), #expr, __FILE__, __LINE__)

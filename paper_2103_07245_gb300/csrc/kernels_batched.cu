@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(1024) k_cholesky_list(const MatUnit* __restric
 cudaError_t launch_cholesky_list(const MatUnit* units, int nunits, int lmax, cudaStream_t s) {
     if (nunits <= 0) return cudaSuccess;
     const size_t smem = (size_t)(packed_tri(lmax) + 2 * (int64_t)lmax) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_cholesky_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)k_cholesky_list, smem);
     if (e != cudaSuccess) return e;
     // 256 threads: the batched factors are small (l <= 224) and many CTAs share an SM
     k_cholesky_list<<<nunits, 256, smem, s>>>(units);
@@ -90,7 +90,7 @@ static cudaError_t trsm_list_t(const TrsmUnit* units, int nunits, int lmax, cuda
     cudaError_t e = cudaSuccess;
     switch (U) {
 #define PBQ_T(UU) case UU: \
-        e = cudaFuncSetAttribute(k_trsm_list<UU, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = func_smem_attr((const void*)k_trsm_list<UU, T>, smem); \
         if (e != cudaSuccess) return e; \
         k_trsm_list<UU, T><<<nunits, 256, smem, s>>>(units); break;
         PBQ_T(1) PBQ_T(2) PBQ_T(3) PBQ_T(4) PBQ_T(5) PBQ_T(6) PBQ_T(7)
@@ -117,7 +117,7 @@ cudaError_t launch_small_qr_list(const MatUnit* units, int nunits, int lmax, cud
     const size_t smem = 2 * (size_t)lmax * lmax * sizeof(double);
     const bool fits = smem <= 220 * 1024;
     if (fits) {
-        cudaError_t e = cudaFuncSetAttribute(k_small_qr_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = func_smem_attr((const void*)k_small_qr_list, smem);
         if (e != cudaSuccess) return e;
     }
     k_small_qr_list<<<nunits, 256, fits ? smem : 0, s>>>(units, fits ? 1 : 0);

@@ -331,11 +331,9 @@ cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rp, do
                             int pass, cudaStream_t s) {
     const int C = chol_inv_ctas(l);
     const size_t smem = chol_inv_smem(l, C);
-    cudaError_t e = cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)k_chol_inv_cluster, smem);
     if (e != cudaSuccess) return e;
-    if (C > 8 &&
-        (e = cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
-        return e;
+    // (the non-portable cluster size was allowed once, when C = 16 was chosen)
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

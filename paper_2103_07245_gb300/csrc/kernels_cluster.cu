@@ -179,7 +179,7 @@ bool cholesky_cluster_fits(int l) { return l > 64 && chol_cluster_smem(l) <= 200
 cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double* Rp, uint32_t* status, int* ctl,
                                     int pass, cudaStream_t s) {
     const size_t smem = chol_cluster_smem(l);
-    cudaError_t e = cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)k_cholesky_cluster, smem);
     if (e != cudaSuccess) return e;
     k_cholesky_cluster<<<kClusterCtas, kClusterThreads, smem, s>>>(l, rows, G, Rp, status, ctl, pass);
     count_launches(1);
@@ -198,6 +198,39 @@ cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kQrThreads = 512;
+
+// 1/d and 1/sqrt(d) for positive normal d: FP32 seeds refined by two
+// Newton-Raphson steps in FP64 (FP64 division and square root take ~430 and
+// ~670 cycles on GB300, and every reflector waits on them); other inputs take
+// the library operations.
+__device__ __forceinline__ double rcp_newton(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / d;
+    const int k = eb - 1023;
+    const double m = __longlong_as_double(b - (long long)k * (1LL << 52));
+    double y = (double)__frcp_rn((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / sqrt(d);
+    const int k = (eb - 1023) >> 1;
+    const double m = __longlong_as_double(b - (long long)(2 * k) * (1LL << 52));
+    double y = (double)rsqrtf((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y * y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
 }
 
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kQrThreads)
@@ -236,12 +269,13 @@ k_small_qr_cluster(int l, const double* __restrict__ R, double* __restrict__ L, 
         double alpha = 0.0, t2 = 0.0;
         if (lane == 0) {
             const double x0 = wj[j];
-            const double nrm = sqrt(x0 * x0 + t);
-            if (nrm != 0.0) {
+            const double s2 = x0 * x0 + t;
+            if (s2 != 0.0) {
+                const double nrm = s2 * rsqrt_newton(s2);
                 alpha = (x0 >= 0.0) ? -nrm : nrm;
                 const double v0 = x0 - alpha;
                 vj[j] = v0;
-                t2 = 2.0 / (v0 * v0 + t);
+                t2 = 2.0 * rcp_newton(v0 * v0 + t);
             }
             tvv_own[lj] = t2;
         }
@@ -340,7 +374,7 @@ bool small_qr_cluster_fits(int l) {
 cudaError_t launch_small_qr_cluster(int l, const double* R, double* L, double* Ptil, cudaStream_t s) {
     const int nloc = (l + kClusterCtas - 1) / kClusterCtas;
     const size_t smem = ((size_t)2 * nloc * l + 2 * (size_t)l) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_small_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)k_small_qr_cluster, smem);
     if (e != cudaSuccess) return e;
     k_small_qr_cluster<<<kClusterCtas, kQrThreads, smem, s>>>(l, R, L, Ptil);
     count_launches(1);

@@ -15,11 +15,28 @@
 #include "fp64_device.cuh"
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace pbq {
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t func_smem_attr(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{dev, func}];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 
 // With PBPQLP_DEBUG=1 in the environment, failing CUDA calls of the library
 // are reported on stderr (call site and CUDA's error text).
@@ -168,7 +185,7 @@ k_cholesky(int l, int64_t rows, const double* __restrict__ G, double* __restrict
 cudaError_t launch_cholesky(int l, int64_t rows, const double* G, double* Rp, uint32_t* status, int* ctl, int pass,
                             cudaStream_t s) {
     const size_t smem = (size_t)(packed_tri(l) + 2 * (int64_t)l) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)k_cholesky, smem);
     if (e != cudaSuccess) return e;
     k_cholesky<<<1, 1024, smem, s>>>(l, rows, G, Rp, status, ctl, pass);
     count_launches(1);
@@ -205,7 +222,7 @@ static cudaError_t trsm_launch_t(int64_t rows, int l, const double* Rp, const do
     const int U = (l + 31) / 32;
     cudaError_t e = cudaSuccess;
 #define PBQ_TR(UU) case UU: \
-        e = cudaFuncSetAttribute(k_trsm_rows<UU, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = func_smem_attr((const void*)k_trsm_rows<UU, T>, smem); \
         if (e != cudaSuccess) return e; \
         k_trsm_rows<UU, T><<<(unsigned)blocks, 256, smem, s>>>(rows, l, Rp, X, ldx, Y, ldy, cond); break;
     switch (U) {
@@ -240,7 +257,7 @@ cudaError_t launch_small_qr(int l, const double* R, double* L, double* Ptil, dou
     const size_t smem = 2 * (size_t)l * l * sizeof(double);
     const bool fits = smem <= 220 * 1024;
     if (fits) {
-        cudaError_t e = cudaFuncSetAttribute(k_small_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = func_smem_attr((const void*)k_small_qr, smem);
         if (e != cudaSuccess) return e;
     }
     k_small_qr<<<1, 1024, fits ? smem : 0, s>>>(l, R, L, Ptil, work, fits ? 1 : 0);

@@ -597,7 +597,7 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
     if (!make_map_oz(&mx, X, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
     if (!make_map_oz(&my, Y, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
     const size_t smem = (size_t)kOzStages * kOzStageBytes + 1024;
-    cudaError_t e = PBQ_DBG(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaError_t e = PBQ_DBG(func_smem_attr((const void*)k_oz_gemm, smem));
     if (e != cudaSuccess) return e;
     k_oz_gemm<<<g.G, kOzThreads, smem, s>>>(mx, my, g.tiles, g.NT, g.upper, g.KI, g.smax, X.rows, Y.rows, X.eraw,
                                             Y.eraw, part, status, 2000000000ull, cond);

@@ -343,7 +343,7 @@ cudaError_t launch_tc_bn(const CUtensorMap* m, int64_t tiles, int KI, int G, int
     static_assert(STAGES >= 2, "stage ring too small");
     const size_t smem = (size_t)STAGES * STAGE + 1024;
     auto kern = k_tc_gemm<NPROD, BN, STAGES, TF32>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<G, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], tiles, KI, smax, part, status, timeout_ns, stall);
     count_launches(1);

@@ -239,7 +239,7 @@ static cudaError_t launch_tc_list_n(const void* maps, const TcUnit* units, int n
     static_assert(STAGES >= 2, "stage ring too small");
     const size_t smem = (size_t)STAGES * STAGE + 1024;
     auto kern = k_tc_list<NPROD, STAGES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = func_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<G, kLThreads, smem, s>>>((const CUtensorMap*)maps, units, nunits, status, 2000000000ull);
     count_launches(1);
