@@ -22,8 +22,12 @@
 // adds the eight level sums into two 64-bit accumulators per element,
 // hi = sum_{lam<4} I_lam 128^(3-lam) and lo = sum_{lam>=4} I_lam 128^(7-lam),
 // and at the end of a segment writes the FP64 partial
-// 2^(e_i + f_j - 35) hi + 2^(e_i + f_j - 63) lo.  Partials of one tile are
-// added in CTA order (deterministic).
+// (2^28 hi + lo) 2^(e_i + f_j - 63), rounded once to FP64 with integer
+// operations.  A CTA that ran the whole contraction of a tile writes C;
+// otherwise each epilogue warp publishes its 32 x 16 slice of exact int64
+// sums and counts in on a per-slice counter, and the last contributor adds
+// them (exactly, so the result does not depend on the split) and writes C,
+// then clears the counter.
 //
 // MMAs.  The eight Y digit tiles of a stage sit one after the other in shared
 // memory, so X digit s times Y digits t0 .. t0 + c - 1 is one MMA of N = 48 c
@@ -115,14 +119,53 @@ __host__ __device__ inline void oz_tile(int64_t t, int NT, int upper, int64_t* m
     }
 }
 
-// x 2^k for x an integer-valued double (|x| < 2^63) and |k| < 3000: three
-// exact power-of-two factors, each a normal double, rounded once at the end.
+// CTA whose stream-K range holds iteration it.
+__device__ __forceinline__ int64_t sk_owner(int64_t it, int64_t T, int64_t G) {
+    int64_t c = (it * G) / T;
+    while (c + 1 < G && sk_begin(c + 1, T, G) <= it) ++c;
+    while (c > 0 && sk_begin(c, T, G) > it) --c;
+    return c;
+}
+
+// (hi 2^28 + lo) 2^e as the nearest double (ties to even), with integer
+// operations only (FP64 arithmetic runs at 2 lanes per clock per SM on GB300
+// and would dominate the epilogue): the 92-bit magnitude is normalised with a
+// leading-zero count and rounded on its dropped bits.  Results outside the
+// normal range take the FP64 route (x 2^k in exact power-of-two factors).
 __device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
-__device__ __forceinline__ double scale2(double x, int k) {
-    const int k1 = k > 900 ? 900 : (k < -900 ? -900 : k);
-    const int r = k - k1;
-    const int k2 = r > 900 ? 900 : (r < -900 ? -900 : r);
-    return x * pow2i(k1) * pow2i(k2) * pow2i(r - k2);
+__device__ __forceinline__ double oz_to_double(int64_t hi, int64_t lo, int e) {
+    const __int128 N = ((__int128)hi << 28) + (__int128)lo;
+    if (N == 0) return 0.0;
+    const bool neg = N < 0;
+    const unsigned __int128 U = neg ? (unsigned __int128)(-N) : (unsigned __int128)N;
+    const uint64_t uh = (uint64_t)(U >> 64), ul = (uint64_t)U;
+    const int p = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);   // leading 1 at bit p
+    uint64_t m;
+    int pe = p;
+    if (p <= 52) {
+        m = ul << (52 - p);
+    } else {
+        const int sh = p - 52;
+        m = (uint64_t)(U >> sh);
+        const unsigned __int128 rem = U & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (m & 1))) {
+            ++m;
+            if (m >> 53) { m >>= 1; ++pe; }
+        }
+    }
+    const int biased = pe + e + 1023;
+    if (biased <= 0 || biased >= 2047) {
+        // subnormal or overflowing result: m 2^(pe - 52 + e) in exact power-of-two factors
+        const double v = neg ? -(double)m : (double)m;   // m < 2^53: exact
+        int k = pe - 52 + e;
+        const int k1 = k > 900 ? 900 : (k < -900 ? -900 : k);
+        k -= k1;
+        const int k2 = k > 900 ? 900 : (k < -900 ? -900 : k);
+        return v * pow2i(k1) * pow2i(k2) * pow2i(k - k2);
+    }
+    const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (m & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
 }
 
 // BF16 bits of a small integer d (|d| < 2^22): exact through FP32.
@@ -164,8 +207,8 @@ __device__ __forceinline__ void digits8(double x, int e, int* d) {
 __global__ void __maxnreg__(128)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t tiles, int NT,
           int upper, int KI, int smax, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
-          const int* __restrict__ ey_raw, double* __restrict__ part, uint32_t* __restrict__ status,
-          uint64_t timeout_ns, const int* __restrict__ cond) {
+          const int* __restrict__ ey_raw, double* __restrict__ part, int* __restrict__ cnt, double* __restrict__ Cout,
+          int64_t ldc, uint32_t* __restrict__ status, uint64_t timeout_ns, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -335,22 +378,70 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                 // bias added per window to each of hi and lo: kOzMagic (2^21 + 2^14 + 2^7 + 1)
                 const uint64_t bias =
                     (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 21) + (1u << 14) + (1u << 7) + 1u);
-                double* slot = part + ((size_t)c * smax + (size_t)tl) * (size_t)(kOzBM * kOzBN);
+                // exact integer sums of this segment, in units of 2^(e_i + f_j - 63)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int cl = g * 16 + j;
-                    const int64_t col = (int64_t)nt * kOzBN + cl;
-                    const int eyr = col < Ry ? ey_raw[col] : 0;
-                    const int ej = eyr - 1021;
-                    const int64_t h = (int64_t)(hi[j] - bias), l = (int64_t)(lo[j] - bias);
-                    // a row holding Inf or NaN (exponent field 2047) makes its products NaN
-                    const double val = (exr >= 2047 || eyr >= 2047)
-                                           ? __longlong_as_double(0x7FF8000000000000LL)
-                                           : scale2((double)h, ei + ej - 35) + scale2((double)l, ei + ej - 63);
-                    slot[(size_t)cl * kOzBM + rloc] = val;
-                    hi[j] = 0;
-                    lo[j] = 0;
+                    hi[j] -= bias;
+                    lo[j] -= bias;
                 }
+                const int64_t it0 = tile * KI, it1 = it0 + KI - 1;
+                const int64_t col0 = (int64_t)nt * kOzBN + g * 16;
+                double* crow = Cout + row * ldc + col0;
+                const int ncol = (int)min((int64_t)16, Ry - col0);
+                // C from the exact sums; a row holding Inf or NaN (exponent field 2047) gives NaN
+#define OZ_WRITE_C(H, L)                                                                               \
+    if (row < Rx) {                                                                                    \
+        _Pragma("unroll") for (int j = 0; j < 16; ++j) {                                               \
+            if (j < ncol) {                                                                            \
+                const int eyr = ey_raw[col0 + j];                                                      \
+                crow[j] = (exr >= 2047 || eyr >= 2047) ? __longlong_as_double(0x7FF8000000000000LL)    \
+                                                       : oz_to_double((int64_t)(H)[j], (int64_t)(L)[j], \
+                                                                      ei + eyr - 1021 - 63);           \
+            }                                                                                          \
+        }                                                                                              \
+    }
+                if (it_begin <= it0 && it_end > it1) {
+                    // the whole contraction of this tile ran here
+                    OZ_WRITE_C(hi, lo)
+                } else {
+                    // stream-K fix-up per 32 x 16 slice: publish the integer sums; the
+                    // CTA that completes the slice adds all of them (exact, so the
+                    // order is immaterial) and writes C
+                    int64_t* slot = (int64_t*)part + ((size_t)c * smax + (size_t)tl) * (size_t)(2 * kOzBM * kOzBN);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        slot[(size_t)(g * 16 + j) * kOzBM + rloc] = (int64_t)hi[j];
+                        slot[(size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc] = (int64_t)lo[j];
+                    }
+                    __threadfence();
+                    __syncwarp();
+                    int* ctr = cnt + tile * 12 + q * 3 + g;
+                    int old = 0;
+                    if (lane == 0) old = atomicAdd(ctr, 1);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    const int64_t cf = sk_owner(it0, T, G), cl = sk_owner(it1, T, G);
+                    if (old == (int)(cl - cf)) {
+                        __threadfence();
+                        // the published sums are re-read with the others: hi / lo now add them up
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
+                        for (int64_t c2 = cf; c2 <= cl; ++c2) {
+                            const long long* s2 = (const long long*)part +
+                                                  ((size_t)c2 * smax + (size_t)(tile - sk_begin(c2, T, G) / KI)) *
+                                                      (size_t)(2 * kOzBM * kOzBN);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                hi[j] += (uint64_t)__ldcg(s2 + (size_t)(g * 16 + j) * kOzBM + rloc);
+                                lo[j] += (uint64_t)__ldcg(s2 + (size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc);
+                            }
+                        }
+                        OZ_WRITE_C(hi, lo)
+                        if (lane == 0) *ctr = 0;   // ready for the next product
+                    }
+                }
+#undef OZ_WRITE_C
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
                 nwin = 0;
                 ++tl;
                 kc = 0;
@@ -378,37 +469,6 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kOzTmemCols)
                      : "memory");
-    }
-}
-
-// Add the stream-K partials of each tile in CTA order into C (FP64, ldc).
-__global__ void k_oz_reduce(int64_t tiles, int NT, int upper, int KI, int64_t G, int smax, const double* __restrict__ part,
-                            int64_t Mrows, int N, double* __restrict__ C, int64_t ldc, const int* __restrict__ cond) {
-    if (cond && *cond == 0) return;
-    const int64_t T = tiles * (int64_t)KI;
-    const int64_t total = tiles * (int64_t)(kOzBM * kOzBN);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t tile = e / (kOzBM * kOzBN);
-        const int rem = (int)(e - tile * (kOzBM * kOzBN));
-        const int cl = rem / kOzBM, r = rem - cl * kOzBM;
-        int64_t mt;
-        int nt;
-        oz_tile(tile, NT, upper, &mt, &nt);
-        const int64_t i = mt * kOzBM + r;
-        const int64_t j = (int64_t)nt * kOzBN + cl;
-        if (i >= Mrows || j >= N) continue;
-        const int64_t it0 = tile * KI, it1 = it0 + KI - 1;
-        int64_t c = (it0 * G) / T;
-        while (c + 1 < G && sk_begin(c + 1, T, G) <= it0) ++c;
-        while (c > 0 && sk_begin(c, T, G) > it0) --c;
-        double acc = 0.0;
-        for (; c < G && sk_begin(c, T, G) <= it1; ++c) {
-            const int64_t b = sk_begin(c, T, G), en = sk_begin(c + 1, T, G);
-            if (en <= it0) continue;
-            const int64_t ft = b / KI;
-            acc += part[((size_t)c * smax + (size_t)(tile - ft)) * (size_t)(kOzBM * kOzBN) + rem];
-        }
-        C[i * ldc + j] = acc;
     }
 }
 
@@ -582,17 +642,22 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     }
     g.KI = (int)((K + kOzBK - 1) / kOzBK);
     const int64_t T = g.tiles * g.KI;
-    g.G = (int)(T < num_sms ? T : num_sms);
+    // at least 16 iterations (32-deep chunks) per CTA: small products use
+    // fewer CTAs, with fewer partials to fix up
+    const int64_t want = (T + 15) / 16;
+    g.G = (int)(want < num_sms ? want : num_sms);
     if (g.G < 1) g.G = 1;
     const int64_t share = (T + g.G - 1) / g.G;
     g.smax = (int)((share + g.KI - 1) / g.KI + 1);
-    g.part_doubles = (int64_t)g.G * g.smax * kOzBM * kOzBN;
+    g.part_doubles = (int64_t)g.G * g.smax * 2 * kOzBM * kOzBN;   // two int64 sums per element
     return g;
 }
 
-cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, double* C,
-                              int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s, cudaEvent_t after_gemm) {
-    if (g.tiles < 1 || Y.rows > (int64_t)g.NT * kOzBN || !X.eraw || !Y.eraw || X.K != Y.K) return cudaErrorInvalidValue;
+cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, int* cnt,
+                              double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
+                              cudaEvent_t after_gemm) {
+    if (g.tiles < 1 || Y.rows > (int64_t)g.NT * kOzBN || !X.eraw || !Y.eraw || X.K != Y.K || !cnt)
+        return cudaErrorInvalidValue;
     CUtensorMap mx, my;
     if (!make_map_oz(&mx, X, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
     if (!make_map_oz(&my, Y, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
@@ -600,7 +665,7 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
     cudaError_t e = PBQ_DBG(func_smem_attr((const void*)k_oz_gemm, smem));
     if (e != cudaSuccess) return e;
     k_oz_gemm<<<g.G, kOzThreads, smem, s>>>(mx, my, g.tiles, g.NT, g.upper, g.KI, g.smax, X.rows, Y.rows, X.eraw,
-                                            Y.eraw, part, status, 2000000000ull, cond);
+                                            Y.eraw, part, cnt, C, ldc, status, 2000000000ull, cond);
     count_launches(1);
     if ((e = PBQ_DBG(cudaGetLastError())) != cudaSuccess) {
         const char* v = std::getenv("PBPQLP_DEBUG");
@@ -612,13 +677,7 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
         return e;
     }
     if (after_gemm && (e = cudaEventRecord(after_gemm, s)) != cudaSuccess) return e;
-    const int64_t total = g.tiles * (int64_t)(kOzBM * kOzBN);
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_oz_reduce<<<(unsigned)blocks, 256, 0, s>>>(g.tiles, g.NT, g.upper, g.KI, g.G, g.smax, part, X.rows, (int)Y.rows,
-                                                 C, ldc, cond);
-    count_launches(1);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, const int* cond,

@@ -35,11 +35,13 @@ struct OzGeom {
 };
 OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms);
 
-// C[i*ldc + j] = sum_k X[i][k] Y[j][k] (FP64), i < X.rows, j < Y.rows.
+// C[i*ldc + j] = sum_k X[i][k] Y[j][k] (FP64), i < X.rows, j < Y.rows, in one
+// launch.  X.K == Y.K is the contraction length.  part: >= g.part_doubles
+// doubles; cnt: >= 12 g.tiles ints, zero on entry and left zero (a call that
+// timed out may leave them nonzero: clear them before the next one).
 // cond (device, optional): nothing runs when *cond == 0.
-// (X.K == Y.K is the contraction length.)
-cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, double* C,
-                              int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
+cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, int* cnt,
+                              double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,
                               cudaEvent_t after_gemm = nullptr);
 
 // Panel P (rows x N FP64, ld ldp) as the operand P^T (N rows, contraction

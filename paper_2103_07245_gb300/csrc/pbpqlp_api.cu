@@ -45,6 +45,7 @@ struct pbpqlp_plan_s {
     bool oz_gram = false, emu = false;
     OzGeom og_gm, og_gn, og_nn, og_tn;  // Grams over m / n rows; C = A Y; C = A^T Y
     size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0, off_ozEb = 0, off_ozEs = 0;
+    size_t off_ozcnt = 0, ozcnt_bytes = 0;   // stream-K fix-up counters (12 per tile), cleared per call
     OzGeom og_qb;                       // Qb = Pbar Ptil (n rows, K = l)
     bool chol_inv = false;              // cluster Cholesky with T = R^{-T}; CholeskyQR solve as a digit product
     OzGeom og_tr_m, og_tr_n;            // Q = C T^T over m or n rows (K = l)
@@ -69,7 +70,7 @@ struct Ws {
     double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red, *T;
     void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
     float* tcpart;
-    int *ozE1, *ozE2, *ozEr, *ozEc, *ozEb, *ozEs;
+    int *ozE1, *ozE2, *ozEr, *ozEc, *ozEb, *ozEs, *ozcnt;
     void *ozS1, *ozS2, *ozArow, *ozAcol;
     double* ozpart;
 };
@@ -111,6 +112,7 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.ozpart = oz ? (double*)(b + P->off_ozpart) : nullptr;
     w.ozEb = oz ? (int*)(b + P->off_ozEb) : nullptr;
     w.ozEs = oz ? (int*)(b + P->off_ozEs) : nullptr;
+    w.ozcnt = oz ? (int*)(b + P->off_ozcnt) : nullptr;
     w.ozEr = P->emu ? (int*)(b + P->off_ozEr) : nullptr;
     w.ozEc = P->emu ? (int*)(b + P->off_ozEc) : nullptr;
     w.ozArow = P->emu ? (void*)(b + P->off_ozArow) : nullptr;
@@ -240,7 +242,7 @@ int emu_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_
     if (g.part_doubles > cap) return PBPQLP_EINVAL;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-    PBQ_TRY(launch_oz_product(X, Yd, g, w.ozpart, C, ldc, w.status, nullptr, s, ev.second));
+    PBQ_TRY(launch_oz_product(X, Yd, g, w.ozpart, w.ozcnt, C, ldc, w.status, nullptr, s, ev.second));
     return PBPQLP_OK;
 }
 
@@ -267,7 +269,7 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         if (P->oz_gram) {
             const OzOperand op = panel_digits(w.ozS1, w.ozE1, l, rows);
             PBQ_TRY(launch_oz_panel(rows, l, src, ldp, w.ozE1, w.ozS1, cond, s));
-            PBQ_TRY(launch_oz_product(op, op, rows == P->m ? P->og_gm : P->og_gn, w.ozpart, w.G, l, w.status, cond,
+            PBQ_TRY(launch_oz_product(op, op, rows == P->m ? P->og_gm : P->og_gn, w.ozpart, w.ozcnt, w.G, l, w.status, cond,
                                       s));
         } else {
             PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
@@ -281,7 +283,7 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
             yd.S = w.ozS2; yd.rows = l; yd.K = l; yd.eraw = w.ozE2;
             PBQ_TRY(launch_oz_a(rows, l, src, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s, cond));
             PBQ_TRY(launch_oz_a(l, l, w.T, 0, l, w.ozE2, w.ozEs, w.ozS2, nullptr, s, cond));
-            PBQ_TRY(launch_oz_product(xd, yd, rows == P->m ? P->og_tr_m : P->og_tr_n, w.ozpart, dst, ldp, w.status,
+            PBQ_TRY(launch_oz_product(xd, yd, rows == P->m ? P->og_tr_m : P->og_tr_n, w.ozpart, w.ozcnt, dst, ldp, w.status,
                                       cond, s));
             continue;
         }
@@ -426,6 +428,13 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         P->off_ozEb = take(sizeof(int) * (size_t)mx);
         P->off_ozEs = take(sizeof(int) * 256);
         P->off_ozpart = take(sizeof(double) * (size_t)pd);
+        {
+            int64_t mt = 0;
+            for (const OzGeom* g : {&P->og_gm, &P->og_gn, &P->og_qb, &P->og_nn, &P->og_tn, &P->og_tr_m, &P->og_tr_n})
+                mt = mt > g->tiles ? mt : g->tiles;
+            P->ozcnt_bytes = sizeof(int) * 12 * (size_t)mt;
+            P->off_ozcnt = take(P->ozcnt_bytes);
+        }
         if (P->emu) {
             P->off_ozEr = take(sizeof(int) * (size_t)m);
             P->off_ozEc = take(sizeof(int) * (size_t)n);
@@ -489,6 +498,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     const int64_t m = P->m, n = P->n, ldp = P->ldp;
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
     if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
     if (P->emu && (rc = emu_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
     // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
@@ -519,7 +529,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         const OzOperand qd = panel_digits(w.ozS1, w.ozE1, l, m), dd = panel_digits(w.ozS2, w.ozE2, l, m);
         PBQ_TRY(launch_oz_panel(m, l, w.Xm, ldp, w.ozE1, w.ozS1, nullptr, s));
         PBQ_TRY(launch_oz_panel(m, l, w.Dm, ldp, w.ozE2, w.ozS2, nullptr, s));
-        PBQ_TRY(launch_oz_product(qd, dd, P->og_gm, w.ozpart, w.R, l, w.status, nullptr, s));
+        PBQ_TRY(launch_oz_product(qd, dd, P->og_gm, w.ozpart, w.ozcnt, w.R, l, w.status, nullptr, s));
     } else {
         const int64_t ps = (int64_t)l * ldp;
         PBQ_TRY(launch_upper_product(l, m, w.Xm, w.Dm, ldp, w.part, ps, P->S_gm, P->kc_gm, nullptr, s));
@@ -535,7 +545,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         yd = panel_digits(w.ozS2, w.ozE2, l, l);
         PBQ_TRY(launch_oz_a(n, l, w.Xn, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s));
         PBQ_TRY(launch_oz_panel(l, l, w.Pt, l, w.ozE2, w.ozS2, nullptr, s));
-        PBQ_TRY(launch_oz_product(xd, yd, P->og_qb, w.ozpart, Qb, l, w.status, nullptr, s));
+        PBQ_TRY(launch_oz_product(xd, yd, P->og_qb, w.ozpart, w.ozcnt, Qb, l, w.status, nullptr, s));
     } else {
         PBQ_TRY(launch_dgemm_skinny(false, n, l, l, w.Xn, ldp, w.Pt, l, Qb, l, 1, l, 0, nullptr, s));
     }
@@ -558,6 +568,7 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     const Ws w = carve(P, workspace);
     cudaStream_t s = P->stream;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
     (void)rowsY;
     if (P->emu) {
         if ((rc = emu_prepare_a(P, w, A, a_dtype == PBPQLP_F32, lda))) return rc;
