@@ -128,30 +128,40 @@ def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
             "avg_launch_ms": avg_ms}
 
 
+# Kernels whose DRAM traffic is recorded in profiles/: source file and the
+# markers around the device code the figure belongs to.
+KERNEL_SOURCES = {
+    "dgemm_skinny_fp64_8000": ("fp64_device.cuh", "__device__ __forceinline__ void dev_dgemm_tile",
+                               "__device__ __forceinline__ int64_t pidx"),
+    "oz_gemm_fp64emu_8000": ("kernels_oz.cu", "k_oz_gemm(const __grid_constant__",
+                             "// Digit preparation"),
+}
+
+
 def read_traffic(kernel_file_tag):
     """ncu DRAM bytes per launch recorded in profiles/, valid only for the kernel source it was taken on."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", kernel_file_tag + ".md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     mt = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
     ms = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel_file_tag)
     if not mt or not ms or cur is None:
         return None
     return float(mt.group(1)) if cur.startswith(ms.group(1)) else None
 
 
-def kernel_source_hash():
-    """sha256 of the skinny FP64 GEMM's device body (the kernel the traffic figure belongs to)."""
+def kernel_source_hash(kernel_file_tag="dgemm_skinny_fp64_8000"):
+    """sha256 of the device code a recorded traffic figure belongs to."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2103_07245_gb300", "csrc", "fp64_device.cuh")
+    fname, start, end = KERNEL_SOURCES[kernel_file_tag]
+    src = os.path.join(ROOT, "paper_2103_07245_gb300", "csrc", fname)
     if not os.path.exists(src):
         return None
     txt = open(src).read()
-    a = txt.find("__device__ __forceinline__ void dev_dgemm_tile")
-    b = txt.find("__device__ __forceinline__ int64_t pidx", a)
+    a = txt.find(start)
+    b = txt.find(end, a)
     if a < 0 or b < 0:
         return None
     return hashlib.sha256(txt[a:b].encode()).hexdigest()
@@ -584,7 +594,7 @@ def main():
     elif w["mode"] == "FP64_EMU":
         roofline = oz_roofline(max(m, n), min(m, n), l, avg_pass_ms, hbm_peak, bf16_sus) if avg_pass_ms else None
         if roofline:
-            roofline["traffic"] = None
+            roofline["traffic"] = read_traffic("oz_gemm_fp64emu_8000") if (m, n, l) == (8000, 8000, 110) else None
             roofline["peak_source"] = "%s (MEASURED_PEAKS.json: HBM copy GB/s, bf16 sustained TFLOP/s)" % peak_src
             roofline["launches_timed"] = pass_launches
         dtype = "f64-emulated (bf16 digit products, exact sums)"
@@ -666,7 +676,9 @@ def main():
             "tflops_algorithmic": whole_job_rate(1, world, ems) * flops / 1e12,
             "rel_err_rank_k": err_e, "rel_err_rank_k_fp64": err_main,
             "rel_fro_diff_vs_fp64_rank_k": diff, "speedup_vs_fp64": ms / ems, "gpu_launches": elaunch,
-            "roofline": oz_roofline(max(m, n), min(m, n), l, epms / epn, hbm_peak, bf16_sus) if epn else None}
+            "roofline": dict(oz_roofline(max(m, n), min(m, n), l, epms / epn, hbm_peak, bf16_sus),
+                             traffic=read_traffic("oz_gemm_fp64emu_8000") if (m, n, l) == (8000, 8000, 110) else None)
+            if epn else None}
         del eplan, eouts
 
     # ---- CPU baseline: the oracle, rank 0 at N = 1, and parity of the timed result
