@@ -595,6 +595,32 @@ __global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, in
     }
 }
 
+// Digits of a row-major matrix P (rows x K, ld ldp; K up to a few thousand)
+// by rows in one pass: one warp per row takes the row's largest exponent field
+// (warp max) and writes the row's digits, zero up to the padded K.
+__global__ void __launch_bounds__(512)
+k_oz_rows(int64_t rows, int64_t K, const double* __restrict__ P, int64_t ldp, int* __restrict__ er,
+          uint16_t* __restrict__ S, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 16 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const double* pr = P + r * ldp;
+    const int64_t Kp = oz_kpad(K);
+    int mx = 0;
+    for (int64_t k = lane; k < K; k += 32) mx = max(mx, exp_field(pr[k]));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) er[r] = mx;
+    const int e = mx - 1021;
+    for (int64_t k = lane; k < Kp; k += 32) {
+        const double x = k < K ? pr[k] : 0.0;
+        int d[kOzDigits];
+        digits8(x, e, d);
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) S[oz_idx(s, r, k, rows, Kp)] = digit_bf16(d[s]);
+    }
+}
+
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -689,6 +715,14 @@ cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, i
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
     k_oz_panel_slice<<<grid, block, 0, s>>>(rows, N, P, ldp, eraw, (uint16_t*)S, cond);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_rows(int64_t rows, int64_t K, const double* P, int64_t ldp, int* er, void* S, const int* cond,
+                           cudaStream_t s) {
+    if (rows < 1 || K < 1) return cudaErrorInvalidValue;
+    k_oz_rows<<<(unsigned)((rows + 15) / 16), 512, 0, s>>>(rows, K, P, ldp, er, (uint16_t*)S, cond);
+    count_launches(1);
     return cudaGetLastError();
 }
 

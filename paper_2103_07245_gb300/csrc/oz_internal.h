@@ -50,6 +50,11 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
 cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, const int* cond,
                             cudaStream_t s);
 
+// A row-major FP64 matrix P (rows x K, ld ldp) as the operand {S, rows, K}
+// with row exponents er[rows], in one kernel (one warp per row).
+cudaError_t launch_oz_rows(int64_t rows, int64_t K, const double* P, int64_t ldp, int* er, void* S, const int* cond,
+                           cudaStream_t s);
+
 // A (m x n, FP64 or FP32, lda) as both operands: A itself (OzOperand {Srow,
 // m, n}, row exponents er) and A^T ({Scol, n, m}, column exponents ec).
 // Either digit set may be null (its exponents are still formed).

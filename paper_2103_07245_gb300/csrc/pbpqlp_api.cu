@@ -281,8 +281,8 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
             OzOperand xd, yd;
             xd.S = w.ozS1; xd.rows = rows; xd.K = l; xd.eraw = w.ozEb;
             yd.S = w.ozS2; yd.rows = l; yd.K = l; yd.eraw = w.ozE2;
-            PBQ_TRY(launch_oz_a(rows, l, src, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s, cond));
-            PBQ_TRY(launch_oz_a(l, l, w.T, 0, l, w.ozE2, w.ozEs, w.ozS2, nullptr, s, cond));
+            PBQ_TRY(launch_oz_rows(rows, l, src, ldp, w.ozEb, w.ozS1, cond, s));
+            PBQ_TRY(launch_oz_rows(l, l, w.T, l, w.ozE2, w.ozS2, cond, s));
             PBQ_TRY(launch_oz_product(xd, yd, rows == P->m ? P->og_tr_m : P->og_tr_n, w.ozpart, w.ozcnt, dst, ldp, w.status,
                                       cond, s));
             continue;
@@ -543,7 +543,7 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         OzOperand xd, yd;
         xd.S = w.ozS1; xd.rows = n; xd.K = l; xd.eraw = w.ozEb;
         yd = panel_digits(w.ozS2, w.ozE2, l, l);
-        PBQ_TRY(launch_oz_a(n, l, w.Xn, 0, ldp, w.ozEb, w.ozEs, w.ozS1, nullptr, s));
+        PBQ_TRY(launch_oz_rows(n, l, w.Xn, ldp, w.ozEb, w.ozS1, nullptr, s));
         PBQ_TRY(launch_oz_panel(l, l, w.Pt, l, w.ozE2, w.ozS2, nullptr, s));
         PBQ_TRY(launch_oz_product(xd, yd, P->og_qb, w.ozpart, w.ozcnt, Qb, l, w.status, nullptr, s));
     } else {

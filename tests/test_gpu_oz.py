@@ -151,3 +151,25 @@ def test_digit_grams_match_fma_grams(pq, monkeypatch):
     a1, a2 = oracle.reconstruct(*g1, 100), oracle.reconstruct(*g2, 100)
     assert np.linalg.norm(a1 - a2) <= 1e-13 * np.linalg.norm(A_np)
     assert np.max(np.abs(g1[1] - g2[1])) <= 1e-12 * np.max(np.abs(g2[1]))
+
+
+def test_emu_bitwise_repeatable(pq):
+    """Exact integer digit sums make every product independent of the
+    stream-K split and of timing: two runs agree bit for bit."""
+    A_np = synth.exp_decay(8, 1500, 1300, 30.0)
+    g1 = _factor(pq, A_np, 40, 10, 2, 3, pq.PBPQLP_MODE_FP64_EMU)
+    g2 = _factor(pq, A_np, 40, 10, 2, 3, pq.PBPQLP_MODE_FP64_EMU)
+    for a, b in zip(g1, g2):
+        assert np.array_equal(a, b)
+
+
+def test_digit_grams_match_fma_grams_l220(pq, monkeypatch):
+    """l = 220 (16-CTA Cholesky with T = R^-T, cluster QR): digit-form orth
+    products against the FP64 FMA path, and both against the oracle."""
+    A_np = synth.exp_decay(4, 700, 650, 60.0)
+    g1 = _factor(pq, A_np, 200, 20, 1, 6, pq.PBPQLP_MODE_FP64)
+    monkeypatch.setenv("PBPQLP_NO_OZ_GRAM", "1")
+    g2 = _factor(pq, A_np, 200, 20, 1, 6, pq.PBPQLP_MODE_FP64)
+    ref = oracle.pbpqlp(A_np, 220, 1, seed=6)
+    assert _parity(A_np, g1, ref, 200) <= TOL
+    assert _parity(A_np, g2, ref, 200) <= TOL
