@@ -214,9 +214,12 @@ int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
  *   Matrix i draws Phi_i from the Philox stream keyed by seed + i.
  *   mode: PBPQLP_MODE_FP64, or PBPQLP_MODE_TF32 / PBPQLP_MODE_TF32X3 (the
  *   products with A_i on the tensor cores, kind::tf32 with FP32
- *   accumulation, split hi/lo in the X3 form; Gram, Cholesky and the small
- *   QR stay FP64; l_i <= 128 in these modes).  a_dtype PBPQLP_F32 or
- *   PBPQLP_F64 in the TF32 modes, PBPQLP_F64 in FP64 mode.
+ *   accumulation, split hi/lo in the X3 form; Cholesky and the small QR stay
+ *   FP64; l_i <= 128 in these modes).  a_dtype PBPQLP_F32 or PBPQLP_F64 in
+ *   the TF32 modes, PBPQLP_F64 in FP64 mode.  In every mode the Grams of
+ *   the orth (Eq. 4) and R = Q^T D (Eq. 6) are exact-digit products on the
+ *   BF16 tensor cores, FP64-accurate as in pbpqlp_factor (environment
+ *   PBPQLP_NO_OZ_GRAM=1 at plan creation: FP64 FMA Grams instead).
  *   A, lda, Qa, L, Qb (host arrays of count): device pointers / leading
  *   dimensions per matrix, layouts as in pbpqlp_factor.
  *   workspace: device, >= pbpqlp_batch_workspace_bytes(batch), 256-aligned;

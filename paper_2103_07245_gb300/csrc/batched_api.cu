@@ -16,6 +16,7 @@
 #include "../../include/pbpqlp.h"
 #include "batched.h"
 #include "internal.h"
+#include "oz_internal.h"
 #include "tc_internal.h"
 
 using namespace pbq;
@@ -28,9 +29,18 @@ struct MatWs {
     // TF32 modes: split copies of A and A^T, transposed panels
     size_t Ahi, Alo, Athi, Atlo, Bnhi, Bnlo, Bmhi, Bmlo;
     int64_t ldn, ldm;      // their leading dimensions (n, m rounded up to 32)
+    // digit Grams: panel digits of the m side, the n side and of D (kept for R = Q^T D)
+    size_t Z[3];
 };
 
-enum LaunchKind { L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_SPLIT, L_PSPLIT, L_TC };
+// Digit sets of one matrix: 0 = m-side panels, 1 = n-side panels, 2 = D.
+constexpr int kZm = 0, kZn = 1, kZd = 2;
+
+enum LaunchKind {
+    L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_SPLIT, L_PSPLIT, L_TC,
+    L_MEMSET,      // workspace bytes [off, off + n) to zero
+    L_OZEXP, L_OZSLICE, L_OZ
+};
 
 struct Launch {
     int kind;
@@ -57,6 +67,7 @@ struct pbpqlp_batch_s {
     int gram_chunk = 512;           // rows per Gram partial (tuned by pbpqlp_batch_autotune)
     int trsm_rows = 64;             // rows per triangular-solve unit (tuned)
     int tc_sorted = 1;              // grouped products: longest contraction first (tuned)
+    bool oz = false;                // Grams and R = Q^T D as digit products (PBPQLP_NO_OZ_GRAM=1: FP64 FMA)
     bool timing = false;            // event pairs around each grouped product kernel
     std::vector<cudaEvent_t> ev;    // 2 per timed launch
     int ev_used = 0;
@@ -65,6 +76,8 @@ struct pbpqlp_batch_s {
     std::vector<MatWs> mw;
     size_t off_status = 0, off_ctl = 0, off_lists = 0, lists_cap = 0, total = 0;
     size_t maps_off = 0;            // tensor-map table inside the list region
+    size_t oz_maps_off = 0;         // digit tensor maps: 6 per matrix (3 sets x {X, Y} boxes)
+    size_t off_oze = 0;             // column exponents of the digit sets: [3][count][ldp] ints
     // host copy of the work lists and the launch sequence built for the last buffers
     std::vector<unsigned char> host_lists;
     std::vector<Launch> seq;
@@ -109,9 +122,15 @@ size_t lists_bound(const pbpqlp_batch_s* B, int gram_chunk_min) {
             units += (size_t)passes * ((std::max(B->m[i], B->n[i]) + kPanelRowsPerUnit - 1) / kPanelRowsPerUnit) *
                      sizeof(PanelUnit);
         }
+        if (B->oz) {
+            // digit maps; per Gram (and R): panel units twice (exponents, digits) and <= 2 x 5 tiles
+            const int64_t pr = (std::max(B->m[i], B->n[i]) + kOzPanelRows - 1) / kOzPanelRows + 1;
+            units += 6 * 128;
+            units += (size_t)(passes * 6 + 1) * (2 * pr * sizeof(OzPanelUnit) + 10 * sizeof(OzListUnit));
+        }
     }
     // one list per width bucket: up to 14 GEMM and 7 TRSM buckets per step, 256-byte aligned
-    return units + 64 * 1024 + 256 * 64 + (size_t)(2 * B->q + 2) * 6 * 24 * 256 + 64 * 256;
+    return units + 64 * 1024 + 256 * 64 + (size_t)(2 * B->q + 2) * 6 * 28 * 256 + 64 * 256;
 }
 
 class ListBuilder {
@@ -126,6 +145,7 @@ class ListBuilder {
         B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size()});
     }
     void memset_ctl() { B_->seq.push_back(Launch{L_MEMSET_CTL, 0, false, 0, 0}); }
+    void memset_ws(size_t off, size_t bytes) { B_->seq.push_back(Launch{L_MEMSET, 0, false, off, (int)bytes}); }
     // GEMM units bucketed by their own width (16-column groups), one launch per bucket
     void add_gemm(const std::vector<GemmUnit>& units, bool transA) {
         std::vector<GemmUnit> bucket[kMaxEll / 16 + 1];
@@ -205,6 +225,55 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         }
         lb.add(L_SPLIT, su);
     }
+    // digit Grams: maps of the three digit sets of every matrix (X box 128 rows, Y box 48)
+    if (B->oz) {
+        std::vector<CUtensorMap> zm((size_t)6 * cnt);
+        for (int i = 0; i < cnt; ++i)
+            for (int st = 0; st < 3; ++st) {
+                const void* S = pt.ws + B->mw[i].Z[st];
+                const int64_t K = st == kZn ? B->n[i] : B->m[i];
+                if (!make_oz_map(&zm[(size_t)6 * i + 2 * st], S, B->l[i], K, kOzBM) ||
+                    !make_oz_map(&zm[(size_t)6 * i + 2 * st + 1], S, B->l[i], K, kOzBN))
+                    return PBPQLP_EINVAL;
+            }
+        B->oz_maps_off = lb.raw(zm.data(), zm.size() * sizeof(CUtensorMap));
+    }
+    auto oz_exps = [&](int st, int i) {
+        return (int*)(pt.ws + B->off_oze) + ((size_t)st * cnt + (size_t)i) * (size_t)ldp;
+    };
+    // panel P_i of digit set st (rows m_i or n_i) -> its column exponents and digits
+    auto oz_panel_units = [&](int st, int i, const double* P, const int* cond, std::vector<OzPanelUnit>& pu) {
+        const int64_t rows = st == kZn ? B->n[i] : B->m[i];
+        for (int64_t r0 = 0; r0 < oz_kpad(rows); r0 += kOzPanelRows) {
+            OzPanelUnit x{};
+            x.P = P; x.ldp = ldp; x.rows = rows; x.r0 = r0; x.N = B->l[i];
+            x.eraw = oz_exps(st, i); x.S = pt.ws + B->mw[i].Z[st]; x.cond = cond;
+            pu.push_back(x);
+        }
+    };
+    auto oz_add_panels = [&](int st, const std::vector<OzPanelUnit>& pu) {
+        lb.memset_ws(B->off_oze + sizeof(int) * (size_t)st * cnt * ldp, sizeof(int) * (size_t)cnt * ldp);
+        lb.add(L_OZEXP, pu);
+        lb.add(L_OZSLICE, pu);
+    };
+    // C_i (l_i x l_i, ld l_i) = X^T Y for the panels of digit sets sx and sy
+    auto oz_tiles = [&](int i, int sx, int sy, double* C, const int* cond, std::vector<OzListUnit>& ou) {
+        const int64_t rows = sx == kZn ? B->n[i] : B->m[i];
+        for (int m0 = 0; m0 < B->l[i]; m0 += kOzBM)
+            for (int n0 = 0; n0 < B->l[i]; n0 += kOzBN) {
+                OzListUnit u{};
+                u.mapx = 6 * i + 2 * sx; u.mapy = 6 * i + 2 * sy + 1;
+                u.m0 = m0; u.n0 = n0; u.KI = (int)((rows + kOzBK - 1) / kOzBK);
+                u.Rx = B->l[i]; u.Ry = B->l[i]; u.ex = oz_exps(sx, i); u.ey = oz_exps(sy, i);
+                u.C = C; u.ldc = B->l[i]; u.cond = cond;
+                ou.push_back(u);
+            }
+    };
+    auto oz_add_tiles = [&](std::vector<OzListUnit>& ou) {
+        if (B->tc_sorted)
+            std::stable_sort(ou.begin(), ou.end(), [](const OzListUnit& a, const OzListUnit& b) { return a.KI > b.KI; });
+        lb.add(L_OZ, ou);
+    };
     // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i
     {
         std::vector<MatUnit> u;
@@ -270,13 +339,17 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         lb.add_gemm(u, transA);
     };
     // CholeskyQR passes for every matrix's panel (side 0: m x l panels, side 1: n x l)
-    auto orth = [&](int side, auto srcsel, auto xsel, auto ysel) {
+    // (digit Grams: pass 1 of the last orth of D takes digit set D, which R = Q^T D reuses)
+    auto orth = [&](int side, auto srcsel, auto xsel, auto ysel, bool d_digits = false) {
         lb.memset_ctl();
         for (int pass = 1; pass <= 6; ++pass) {
             std::vector<GemmUnit> gu;
             std::vector<ReduceUnit> ru;
             std::vector<MatUnit> cu;
             std::vector<TrsmUnit> tu;
+            std::vector<OzPanelUnit> pu;
+            std::vector<OzListUnit> ou;
+            const int st = (pass == 1 && d_digits) ? kZd : (side == 0 ? kZm : kZn);
             for (int i = 0; i < cnt; ++i) {
                 const int64_t rows = side == 0 ? B->m[i] : B->n[i];
                 const int l = B->l[i];
@@ -287,19 +360,24 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 const int* cond = pass <= 2 ? nullptr : c + 8 + (pass + 1) / 2;
                 double* part = P64(pt, B->mw[i].part);
                 const int64_t ps = (int64_t)l * ldp;
-                for (int s = 0; s < S; ++s)
-                    for (int64_t m0 = 0; m0 < l; m0 += kGemmBM) {
-                        GemmUnit g{};
-                        g.A = src; g.lda = ldp; g.B = src; g.ldb = ldp; g.C = part + s * ps; g.ldc = ldp;
-                        g.M = l; g.m0 = m0; g.kbeg = (int64_t)s * B->gram_chunk;
-                        g.kend = std::min<int64_t>(rows, (int64_t)(s + 1) * B->gram_chunk);
-                        g.N = l; g.transA = 1; g.cond = cond;
-                        gu.push_back(g);
-                    }
-                ReduceUnit r{};
-                r.part = part; r.C = P64(pt, B->mw[i].G); r.ps = ps; r.ldp = ldp; r.ldc = l; r.M = l; r.N = l; r.S = S;
-                r.cond = cond;
-                ru.push_back(r);
+                if (B->oz) {
+                    oz_panel_units(st, i, src, cond, pu);
+                    oz_tiles(i, st, st, P64(pt, B->mw[i].G), cond, ou);
+                } else {
+                    for (int s = 0; s < S; ++s)
+                        for (int64_t m0 = 0; m0 < l; m0 += kGemmBM) {
+                            GemmUnit g{};
+                            g.A = src; g.lda = ldp; g.B = src; g.ldb = ldp; g.C = part + s * ps; g.ldc = ldp;
+                            g.M = l; g.m0 = m0; g.kbeg = (int64_t)s * B->gram_chunk;
+                            g.kend = std::min<int64_t>(rows, (int64_t)(s + 1) * B->gram_chunk);
+                            g.N = l; g.transA = 1; g.cond = cond;
+                            gu.push_back(g);
+                        }
+                    ReduceUnit r{};
+                    r.part = part; r.C = P64(pt, B->mw[i].G); r.ps = ps; r.ldp = ldp; r.ldc = l; r.M = l; r.N = l;
+                    r.S = S; r.cond = cond;
+                    ru.push_back(r);
+                }
                 MatUnit m{};
                 m.l = l; m.pass = pass; m.rows = rows; m.G = P64(pt, B->mw[i].G); m.Rp = P64(pt, B->mw[i].Rp);
                 m.ctl = c; m.status = status + i;
@@ -311,8 +389,13 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                     tu.push_back(t);
                 }
             }
-            lb.add_gemm(gu, true);
-            lb.add(L_REDUCE, ru);
+            if (B->oz) {
+                oz_add_panels(st, pu);
+                oz_add_tiles(ou);
+            } else {
+                lb.add_gemm(gu, true);
+                lb.add(L_REDUCE, ru);
+            }
             lb.add(L_CHOL, cu);
             lb.add_trsm(tu);
         }
@@ -332,8 +415,17 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         orth(1, Xn, Xn, Yn);
     }
     product(false, Xn, Dm);                 // D = A Pbar (Eq. 5)
-    orth(0, Dm, Xm, Ym);                    // Q = orth(D) (Eq. 6), result in Xm
-    {                                       // R = Q^T D
+    orth(0, Dm, Xm, Ym, B->oz);             // Q = orth(D) (Eq. 6), result in Xm
+    if (B->oz) {                            // R = Q^T D from the digits of Q and of D
+        std::vector<OzPanelUnit> pu;
+        std::vector<OzListUnit> ou;
+        for (int i = 0; i < cnt; ++i) {
+            oz_panel_units(kZm, i, Xm(i), nullptr, pu);
+            oz_tiles(i, kZm, kZd, P64(pt, B->mw[i].R), nullptr, ou);
+        }
+        oz_add_panels(kZm, pu);
+        oz_add_tiles(ou);
+    } else {                                // R = Q^T D
         std::vector<GemmUnit> gu;
         std::vector<ReduceUnit> ru;
         for (int i = 0; i < cnt; ++i) {
@@ -413,6 +505,13 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
         const void* u = lists + L.off;
         switch (L.kind) {
             case L_MEMSET_CTL: PBQ_TRY(cudaMemsetAsync(ctl, 0, sizeof(int) * 16 * (size_t)B->count, s)); break;
+            case L_MEMSET: PBQ_TRY(cudaMemsetAsync(ws + L.off, 0, (size_t)L.n, s)); break;
+            case L_OZEXP: PBQ_TRY(launch_oz_panel_exp_list((const OzPanelUnit*)u, L.n, s)); break;
+            case L_OZSLICE: PBQ_TRY(launch_oz_panel_slice_list((const OzPanelUnit*)u, L.n, s)); break;
+            case L_OZ:
+                PBQ_TRY(launch_oz_list(lists + B->oz_maps_off, (const OzListUnit*)u, L.n, B->num_sms,
+                                       (uint32_t*)(ws + B->off_status), s));
+                break;
             case L_GAUSS: PBQ_TRY(launch_gaussian_list((const MatUnit*)u, L.n, s)); break;
             case L_GEMM: PBQ_TRY(launch_dgemm_list(L.TN, L.transA, (const GemmUnit*)u, L.n, s)); break;
             case L_REDUCE: PBQ_TRY(launch_reduce_list((const ReduceUnit*)u, L.n, s)); break;
@@ -477,7 +576,13 @@ void layout(pbpqlp_batch_s* B) {
             w.Bmhi = take(4 * (size_t)(npad * w.ldm));
             w.Bmlo = split ? take(4 * (size_t)(npad * w.ldm)) : 0;
         }
+        if (B->oz) {
+            w.Z[kZm] = take(oz_digit_bytes(l, m));
+            w.Z[kZn] = take(oz_digit_bytes(l, n));
+            w.Z[kZd] = take(oz_digit_bytes(l, m));
+        }
     }
+    if (B->oz) B->off_oze = take(sizeof(int) * 3 * (size_t)B->count * (size_t)ldp);
     B->lists_cap = lists_bound(B, 256);
     B->off_lists = take(B->lists_cap);
     B->total = off;
@@ -539,7 +644,7 @@ int run(pbpqlp_batch_s* B, const Ptrs& pt, size_t ws_bytes) {
     if (B->exec) {
         PBQ_TRY(cudaGraphLaunch(B->exec, B->stream));
         int64_t kernels = 0;
-        for (const Launch& L : B->seq) kernels += (L.kind != L_MEMSET_CTL);
+        for (const Launch& L : B->seq) kernels += (L.kind != L_MEMSET_CTL && L.kind != L_MEMSET);
         count_launches(kernels);
         return PBPQLP_OK;
     }
@@ -581,6 +686,8 @@ int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const 
     B->ldp = round_up(B->lmax, 8);
     const char* env = std::getenv("PBPQLP_BATCH_NO_GRAPH");
     if (env && env[0] == '1') B->use_graph = false;
+    const char* no = std::getenv("PBPQLP_NO_OZ_GRAM");
+    B->oz = !(no && no[0] == '1');
     layout(B);
     *out = B;
     return PBPQLP_OK;

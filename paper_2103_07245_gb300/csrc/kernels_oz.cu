@@ -200,6 +200,74 @@ __device__ __forceinline__ void digits8(double x, int e, int* d) {
     d[7] = (int)F;
 }
 
+// The MMAs of one stage (two 16-deep k-steps): X digit sx times the Y digits
+// t0 .. t0 + c - 1 (c <= 5) into the TMEM columns of levels sx + t0 ..;
+// `fresh` starts new level sums (the first stage of a window).
+__device__ __forceinline__ void oz_stage_mmas(uint32_t tmem_base, uint32_t xa, bool fresh) {
+    const uint64_t dX = sdesc_k_sw64(xa), dY = sdesc_k_sw64(xa + kOzDigits * kOzXTile);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+        for (int sx = 0; sx < kOzDigits; ++sx) {
+#pragma unroll
+            for (int t0 = 0; t0 < kOzDigits - sx; t0 += 5) {
+                const int cnt = (kOzDigits - sx - t0) < 5 ? (kOzDigits - sx - t0) : 5;
+                const uint64_t a = dX + (uint64_t)((sx * kOzXTile + kk * 32) >> 4);
+                const uint64_t b = dY + (uint64_t)((t0 * kOzYTile + kk * 32) >> 4);
+                const uint32_t idesc = idesc_bf16_f32(kOzBM, cnt * kOzBN);
+                tc_mma_bf16(tmem_base + (uint32_t)((sx + t0) * kOzBN), a, b, idesc,
+                            (fresh && kk == 0 && sx == 0) ? 0u : 1u);
+            }
+        }
+    }
+}
+
+// Adds the eight level sums of one window (this thread's row: TMEM lane
+// quarter q; columns 16 g .. 16 g + 15) into the two 64-bit accumulators.
+// The FP32 level value v (an integer, |v| <= 2^22) is read as the bits of
+// v + 1.5 * 2^23, i.e. kOzMagic + v; oz_unbias removes that bias per segment.
+__device__ __forceinline__ void oz_drain(uint32_t tmem_base, int q, int g, uint64_t (&hi)[16], uint64_t (&lo)[16]) {
+#pragma unroll
+    for (int lam = 0; lam < kOzDigits; ++lam) {
+        const uint32_t wgt = 1u << (7 * ((lam < 4 ? 3 : 7) - lam));
+        float v[16];
+        tmem_ld16(tmem_base + (uint32_t)(lam * kOzBN + g * 16) + ((uint32_t)(q * 32) << 16), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t bv = __float_as_uint(v[j] + 12582912.0f);
+            if (lam < 4) hi[j] = mad_wide_u(bv, wgt, hi[j]);
+            else lo[j] = mad_wide_u(bv, wgt, lo[j]);
+        }
+    }
+}
+
+// Removes the bias of nwin drained windows: kOzMagic (2^21 + 2^14 + 2^7 + 1)
+// was added per window to each of hi and lo (unsigned arithmetic wraps exactly).
+__device__ __forceinline__ void oz_unbias(int nwin, uint64_t (&hi)[16], uint64_t (&lo)[16]) {
+    const uint64_t bias = (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 21) + (1u << 14) + (1u << 7) + 1u);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        hi[j] -= bias;
+        lo[j] -= bias;
+    }
+}
+
+// ncol (<= 16) elements of a row of C from the exact sums (units of
+// 2^(e_i + f_j - 63), biased exponent fields exr and ey[j]); a row or column
+// holding Inf or NaN (exponent field 2047) gives NaN.
+__device__ __forceinline__ void oz_store(double* crow, int ncol, int exr, const int* __restrict__ ey,
+                                         const uint64_t (&hi)[16], const uint64_t (&lo)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j < ncol) {
+            const int eyr = ey[j];
+            crow[j] = (exr >= 2047 || eyr >= 2047)
+                          ? __longlong_as_double(0x7FF8000000000000LL)
+                          : oz_to_double((int64_t)hi[j], (int64_t)lo[j], exr + eyr - 2 * 1021 - 63);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The product kernel
 // ---------------------------------------------------------------------------
@@ -295,23 +363,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     }
                 }
                 tc_fence_after();
-                const uint32_t xa = smem_u32(smem + (size_t)s * kOzStageBytes);
-                const uint64_t dX = sdesc_k_sw64(xa), dY = sdesc_k_sw64(xa + kOzDigits * kOzXTile);
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-                    for (int sx = 0; sx < kOzDigits; ++sx) {
-#pragma unroll
-                        for (int t0 = 0; t0 < kOzDigits - sx; t0 += 5) {
-                            const int cnt = (kOzDigits - sx - t0) < 5 ? (kOzDigits - sx - t0) : 5;
-                            const uint64_t a = dX + (uint64_t)((sx * kOzXTile + kk * 32) >> 4);
-                            const uint64_t b = dY + (uint64_t)((t0 * kOzYTile + kk * 32) >> 4);
-                            const uint32_t idesc = idesc_bf16_f32(kOzBM, cnt * kOzBN);
-                            tc_mma_bf16(tmem_base + (uint32_t)((sx + t0) * kOzBN), a, b, idesc,
-                                        (wfirst && kk == 0 && sx == 0) ? 0u : 1u);
-                        }
-                    }
-                }
+                oz_stage_mmas(tmem_base, smem_u32(smem + (size_t)s * kOzStageBytes), wfirst);
                 tc_commit(&empty_bar[s]);
                 if (wlast) tc_commit(&accf_bar);
                 consumed_sh = li + 1;
@@ -325,10 +377,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
             }
         }
     } else {
-        // ---------------- epilogue: exact level sums -> (hi, lo) -> FP64 partials.
-        // The FP32 level value v (an integer, |v| <= 2^22) is read as the bits
-        // of v + 1.5 * 2^23, i.e. kOzMagic + v; the bias kOzMagic * weight is
-        // removed once per segment (unsigned arithmetic wraps exactly).
+        // ---------------- epilogue: exact level sums -> (hi, lo) -> C or int64 partials
         const int q = warp & 3;                 // TMEM lane quarter of this warp
         const int g = (warp - 2) >> 2;          // which 16 of the 48 columns
         const int rloc = q * 32 + lane;
@@ -351,18 +400,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     break;
                 }
                 tc_fence_after();
-#pragma unroll
-                for (int lam = 0; lam < kOzDigits; ++lam) {
-                    const uint32_t wgt = 1u << (7 * ((lam < 4 ? 3 : 7) - lam));
-                    float v[16];
-                    tmem_ld16(tmem_base + (uint32_t)(lam * kOzBN + g * 16) + ((uint32_t)(q * 32) << 16), v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const uint32_t bv = __float_as_uint(v[j] + 12582912.0f);
-                        if (lam < 4) hi[j] = mad_wide_u(bv, wgt, hi[j]);
-                        else lo[j] = mad_wide_u(bv, wgt, lo[j]);
-                    }
-                }
+                oz_drain(tmem_base, q, g, hi, lo);
                 tc_fence_before();
                 mbar_arrive(&acce_bar);
                 ++nwin;
@@ -374,35 +412,14 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                 oz_tile(tile, NT, upper, &mt, &nt);
                 const int64_t row = mt * kOzBM + rloc;
                 const int exr = row < Rx ? ex_raw[row] : 0;
-                const int ei = exr - 1021;
-                // bias added per window to each of hi and lo: kOzMagic (2^21 + 2^14 + 2^7 + 1)
-                const uint64_t bias =
-                    (uint64_t)nwin * (uint64_t)kOzMagic * (uint64_t)((1u << 21) + (1u << 14) + (1u << 7) + 1u);
-                // exact integer sums of this segment, in units of 2^(e_i + f_j - 63)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    hi[j] -= bias;
-                    lo[j] -= bias;
-                }
+                oz_unbias(nwin, hi, lo);   // exact integer sums of this segment, in units of 2^(e_i + f_j - 63)
                 const int64_t it0 = tile * KI, it1 = it0 + KI - 1;
                 const int64_t col0 = (int64_t)nt * kOzBN + g * 16;
                 double* crow = Cout + row * ldc + col0;
                 const int ncol = (int)min((int64_t)16, Ry - col0);
-                // C from the exact sums; a row holding Inf or NaN (exponent field 2047) gives NaN
-#define OZ_WRITE_C(H, L)                                                                               \
-    if (row < Rx) {                                                                                    \
-        _Pragma("unroll") for (int j = 0; j < 16; ++j) {                                               \
-            if (j < ncol) {                                                                            \
-                const int eyr = ey_raw[col0 + j];                                                      \
-                crow[j] = (exr >= 2047 || eyr >= 2047) ? __longlong_as_double(0x7FF8000000000000LL)    \
-                                                       : oz_to_double((int64_t)(H)[j], (int64_t)(L)[j], \
-                                                                      ei + eyr - 1021 - 63);           \
-            }                                                                                          \
-        }                                                                                              \
-    }
                 if (it_begin <= it0 && it_end > it1) {
                     // the whole contraction of this tile ran here
-                    OZ_WRITE_C(hi, lo)
+                    if (row < Rx) oz_store(crow, ncol, exr, ey_raw + col0, hi, lo);
                 } else {
                     // stream-K fix-up per 32 x 16 slice: publish the integer sums; the
                     // CTA that completes the slice adds all of them (exact, so the
@@ -435,11 +452,10 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                                 lo[j] += (uint64_t)__ldcg(s2 + (size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc);
                             }
                         }
-                        OZ_WRITE_C(hi, lo)
+                        if (row < Rx) oz_store(crow, ncol, exr, ey_raw + col0, hi, lo);
                         if (lane == 0) *ctr = 0;   // ready for the next product
                     }
                 }
-#undef OZ_WRITE_C
 #pragma unroll
                 for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
                 nwin = 0;
@@ -448,6 +464,169 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
             } else {
                 ++kc;
             }
+        }
+    }
+
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // wait (bounded) for TMA copies that were issued but never consumed
+        const uint64_t dl = globaltimer() + timeout_ns;
+        for (int li = consumed_sh; li < issued_sh; ++li) {
+            const int s = li % kOzStages;
+            uint32_t spin = 0;
+            while (!mbar_test(&full_bar[s], (uint32_t)((li / kOzStages) & 1))) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) break;
+            }
+        }
+        if (abort_sh) atomicOr(status, kStTimeout);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kOzTmemCols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The grouped product kernel: the same roles, stages and windows as k_oz_gemm,
+// over a list of whole-contraction tiles of many products.  CTA c runs units
+// c, c + G, ...; stage, window and level counters run on across units.
+// ---------------------------------------------------------------------------
+__global__ void __maxnreg__(128)
+k_oz_list(const CUtensorMap* __restrict__ maps, const OzListUnit* __restrict__ units, int nunits,
+          uint32_t* __restrict__ status, uint64_t timeout_ns) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[kOzStages], empty_bar[kOzStages], accf_bar, acce_bar, drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int issued_sh, consumed_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x, c = blockIdx.x;
+    const uint64_t deadline = globaltimer() + timeout_ns;
+    // a unit whose condition is off is skipped by all three roles alike
+    auto skipped = [&](const OzListUnit& U) { return U.cond && *U.cond == 0; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        mbar_init(&accf_bar, 1);
+        mbar_init(&acce_bar, kOzEpiThreads);
+        mbar_init(&drain_bar, 1);
+        abort_sh = 0;
+        issued_sh = 0;
+        consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(kOzTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int li = 0;
+            bool ok = true;
+            for (int u = c; ok && u < nunits; u += G) {
+                const OzListUnit U = units[u];
+                if (skipped(U)) continue;
+                for (int kc = 0; kc < U.KI; ++kc, ++li) {
+                    const int s = li % kOzStages;
+                    if (li >= kOzStages &&
+                        !mbar_wait(&empty_bar[s], (uint32_t)((li / kOzStages - 1) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* st = smem + (size_t)s * kOzStageBytes;
+                    mbar_expect_tx(&full_bar[s], kOzStageBytes);
+                    tma_load_4d(st, &maps[U.mapx], &full_bar[s], 0, U.m0, kc, 0);
+                    tma_load_4d(st + kOzDigits * kOzXTile, &maps[U.mapy], &full_bar[s], 0, U.n0, kc, 0);
+                    issued_sh = li + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: windows of kOzWindow stages within a unit
+        if (lane == 0) {
+            int li = 0, win = -1;
+            bool ok = true;
+            for (int u = c; ok && u < nunits; u += G) {
+                const OzListUnit U = units[u];
+                if (skipped(U)) continue;
+                for (int kc = 0; kc < U.KI; ++kc, ++li) {
+                    const bool wfirst = kc % kOzWindow == 0;
+                    const bool wlast = (kc % kOzWindow == kOzWindow - 1) || (kc + 1 == U.KI);
+                    const int s = li % kOzStages;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((li / kOzStages) & 1), deadline, &abort_sh)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    if (wfirst) {
+                        ++win;
+                        if (win > 0 && !mbar_wait(&acce_bar, (uint32_t)((win - 1) & 1), deadline, &abort_sh)) {
+                            abort_sh = 1;
+                            ok = false;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    oz_stage_mmas(tmem_base, smem_u32(smem + (size_t)s * kOzStageBytes), wfirst);
+                    tc_commit(&empty_bar[s]);
+                    if (wlast) tc_commit(&accf_bar);
+                    consumed_sh = li + 1;
+                }
+            }
+            tc_commit(&drain_bar);
+            const uint64_t dl = globaltimer() + timeout_ns;
+            uint32_t spin = 0;
+            while (!mbar_test(&drain_bar, 0)) {
+                if ((++spin & 255u) == 0 && globaltimer() > dl) { abort_sh = 1; break; }
+            }
+        }
+    } else {
+        // ---------------- epilogue: per unit, level sums -> (hi, lo) -> C
+        const int q = warp & 3;
+        const int g = (warp - 2) >> 2;
+        const int rloc = q * 32 + lane;
+        uint64_t hi[16], lo[16];
+        int win = -1;
+        bool ok = true;
+        for (int u = c; ok && u < nunits; u += G) {
+            const OzListUnit U = units[u];
+            if (skipped(U)) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
+            int nwin = 0;
+            for (int kc = 0; kc < U.KI; ++kc) {
+                if (kc % kOzWindow == 0) ++win;
+                if ((kc % kOzWindow == kOzWindow - 1) || (kc + 1 == U.KI)) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar, (uint32_t)(win & 1), deadline, &abort_sh));
+                    if (!ok) {
+                        abort_sh = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    oz_drain(tmem_base, q, g, hi, lo);
+                    tc_fence_before();
+                    mbar_arrive(&acce_bar);
+                    ++nwin;
+                }
+            }
+            if (!ok) break;
+            oz_unbias(nwin, hi, lo);
+            const int row = U.m0 + rloc, col0 = U.n0 + g * 16;
+            if (row < U.Rx && col0 < U.Ry)
+                oz_store(U.C + (int64_t)row * U.ldc + col0, min(16, U.Ry - col0), U.ex[row], U.ey + col0, hi, lo);
         }
     }
 
@@ -621,6 +800,65 @@ k_oz_rows(int64_t rows, int64_t K, const double* __restrict__ P, int64_t ldp, in
     }
 }
 
+// Column exponents of the panel units: unit b covers rows r0 .. r0 + 127 of
+// its panel; thread (tx, ty) scans columns tx + 32 cg over rows ty, ty + 8, ..
+// and the column maxima go out with one atomicMax each (order-free).
+__global__ void __launch_bounds__(256)
+k_oz_panel_exp_list(const OzPanelUnit* __restrict__ units) {
+    const OzPanelUnit U = units[blockIdx.x];
+    if (U.cond && *U.cond == 0) return;
+    __shared__ int sm[8][256];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t r1 = U.r0 + kOzPanelRows < U.rows ? U.r0 + kOzPanelRows : U.rows;
+    for (int j = tx; j < U.N; j += 32) {
+        int mx = 0;
+        for (int64_t r = U.r0 + ty; r < r1; r += 8) mx = max(mx, exp_field(U.P[r * U.ldp + j]));
+        sm[ty][j] = mx;
+    }
+    __syncthreads();
+    for (int j = ty * 32 + tx; j < U.N; j += 256) {
+        int mx = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) mx = max(mx, sm[t][j]);
+        if (mx > 0) atomicMax(&U.eraw[j], mx);
+    }
+}
+
+// Digits of the panel units (P^T: rows N, contraction over the panel rows):
+// each 32 x 32 block is sliced into shared memory and written transposed,
+// zero digits past the panel rows up to the padded contraction length.
+__global__ void __launch_bounds__(256)
+k_oz_panel_slice_list(const OzPanelUnit* __restrict__ units) {
+    const OzPanelUnit U = units[blockIdx.x];
+    if (U.cond && *U.cond == 0) return;
+    __shared__ uint16_t sd[kOzDigits][32][33];
+    const int64_t Kp = oz_kpad(U.rows);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    uint16_t* S = (uint16_t*)U.S;
+    for (int64_t rb = U.r0; rb < U.r0 + kOzPanelRows && rb < Kp; rb += 32) {
+        for (int j0 = 0; j0 < U.N; j0 += 32) {
+            const int j = j0 + tx;
+            const int e = j < U.N ? U.eraw[j] - 1021 : 0;
+            for (int rr = ty; rr < 32; rr += 8) {
+                const int64_t r = rb + rr;
+                const double x = (r < U.rows && j < U.N) ? U.P[r * U.ldp + j] : 0.0;
+                int d[kOzDigits];
+                digits8(x, e, d);
+#pragma unroll
+                for (int s = 0; s < kOzDigits; ++s) sd[s][tx][rr] = digit_bf16(d[s]);
+            }
+            __syncthreads();
+            for (int jj = ty; jj < 32; jj += 8) {
+                const int jc = j0 + jj;
+                if (jc >= U.N) break;
+#pragma unroll
+                for (int s = 0; s < kOzDigits; ++s) S[oz_idx(s, jc, rb + tx, U.N, Kp)] = sd[s][jj][tx];
+            }
+            __syncthreads();
+        }
+    }
+}
+
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -743,6 +981,39 @@ cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t 
                                                     (uint16_t*)Scol, cond);
     }
     count_launches(2);
+    return cudaGetLastError();
+}
+
+bool make_oz_map(void* map128, const void* S, int64_t rows, int64_t K, int box_rows) {
+    OzOperand op;
+    op.S = S;
+    op.rows = rows;
+    op.K = K;
+    return make_map_oz((CUtensorMap*)map128, op, box_rows);
+}
+
+cudaError_t launch_oz_list(const void* maps, const OzListUnit* units, int n, int G, uint32_t* status, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    if (!maps || !units || !status || G < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kOzStages * kOzStageBytes + 1024;
+    cudaError_t e = PBQ_DBG(func_smem_attr((const void*)k_oz_list, smem));
+    if (e != cudaSuccess) return e;
+    k_oz_list<<<G < n ? G : n, kOzThreads, smem, s>>>((const CUtensorMap*)maps, units, n, status, 2000000000ull);
+    count_launches(1);
+    return PBQ_DBG(cudaGetLastError());
+}
+
+cudaError_t launch_oz_panel_exp_list(const OzPanelUnit* units, int n, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    k_oz_panel_exp_list<<<n, dim3(32, 8), 0, s>>>(units);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_panel_slice_list(const OzPanelUnit* units, int n, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    k_oz_panel_slice_list<<<n, dim3(32, 8), 0, s>>>(units);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -62,4 +62,50 @@ cudaError_t launch_oz_rows(int64_t rows, int64_t K, const double* P, int64_t ldp
 cudaError_t launch_oz_a(int64_t m, int64_t n, const void* A, int a_f32, int64_t lda, int* er, int* ec, void* Srow,
                         void* Scol, cudaStream_t s, const int* cond = nullptr);
 
+// ---------------------------------------------------------------------------
+// Grouped form (many independent products per launch, for the batched path)
+// ---------------------------------------------------------------------------
+// Tensor map (128 bytes at map128) over the digits of the operand {S, rows, K}
+// for tiles of box_rows rows: kOzBM for the X side, kOzBN for the Y side.
+bool make_oz_map(void* map128, const void* S, int64_t rows, int64_t K, int box_rows);
+
+// One 128 x 48 tile C[m0 .. m0 + 127][n0 .. n0 + 47] (clipped to Rx x Ry) of
+// one product C = X Y^T, over the whole contraction (KI chunks of 32) in one
+// CTA, written once: no partials, deterministic.
+struct OzListUnit {
+    int mapx, mapy;        // maps (in the table passed to the launch) of X (box kOzBM) and Y (box kOzBN)
+    int m0, n0;
+    int KI;
+    int Rx, Ry;
+    int pad_;
+    const int* ex;         // biased row exponents of X (Rx) and of Y (Ry)
+    const int* ey;
+    double* C;
+    int64_t ldc;
+    const int* cond;       // skip when *cond == 0 (null: always run)
+};
+
+// Persistent launch of min(G, n) CTAs; CTA c runs units c, c + G, ... (the
+// host sorts them longest first).  status: kStTimeout on a wait that expired.
+cudaError_t launch_oz_list(const void* maps, const OzListUnit* units, int n, int G, uint32_t* status, cudaStream_t s);
+
+// kOzPanelRows rows of one panel P (rows x N FP64, ld ldp, N <= 256) seen as
+// the operand P^T = {S, N, rows}.
+constexpr int kOzPanelRows = 128;
+struct OzPanelUnit {
+    const double* P;
+    int64_t ldp, rows, r0;
+    int N;
+    int pad_;
+    int* eraw;             // column exponents (N)
+    void* S;
+    const int* cond;
+};
+// Column exponents: atomicMax of each unit's column maxima into eraw, which
+// must be zero before the launch.
+cudaError_t launch_oz_panel_exp_list(const OzPanelUnit* units, int n, cudaStream_t s);
+// Digits of every unit's rows, up to the padded contraction length (the
+// units must cover oz_kpad(rows)), from the final eraw.
+cudaError_t launch_oz_panel_slice_list(const OzPanelUnit* units, int n, cudaStream_t s);
+
 }  // namespace pbq

@@ -155,3 +155,45 @@ def test_batched_autotune_keeps_results(pq, tmp_path):
         g = [outs[0][i].cpu().numpy(), outs[1][i].cpu().numpy(), outs[2][i].cpu().numpy()]
         d = np.linalg.norm(oracle.reconstruct(*g, s["k"]) - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], s["k"]))
         assert d / np.linalg.norm(A) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["FP64", "TF32X3"])
+def test_batched_digit_grams_match_fma_grams(pq, monkeypatch, mode):
+    """Grouped exact-digit Grams (default) against the FP64 FMA Grams
+    (PBPQLP_NO_OZ_GRAM=1 at plan creation) on the same batch; in FP64 mode
+    the batch includes l > 128 (two 128-row tiles per Gram column)."""
+    import torch
+    md = getattr(pq, "PBPQLP_MODE_" + mode)
+    if mode == "FP64":
+        shapes = [dict(m=700, n=500, k=150), dict(m=400, n=300, k=60), dict(m=260, n=240, k=200),
+                  dict(m=1500, n=180, k=20)]
+        mats = [synth.poly_decay(900 + i, s["m"], s["n"], 1.5) for i, s in enumerate(shapes)]
+    else:
+        shapes = synth.batched_shapes(13, 8, m_range=(200, 1500), n_lo=100, n_hi=700, k_range=(8, 64))
+        mats = [synth.poly_decay(950 + i, s["m"], s["n"], s["alpha"]) for i, s in enumerate(shapes)]
+    p, q, seed = 8, 1, 15
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    out = []
+    for no_oz in (False, True):
+        if no_oz:
+            monkeypatch.setenv("PBPQLP_NO_OZ_GRAM", "1")
+        B = pq.Batch([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], p, q, seed,
+                     mode=md)
+        Qa, L, Qb = B.factor(As)
+        rc, flags = B.sync_status()
+        assert rc == pq.PBPQLP_OK, flags
+        out.append([[t.cpu().numpy() for t in (Qa[i], L[i], Qb[i])] for i in range(len(shapes))])
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        a1 = oracle.reconstruct(*out[0][i], s["k"])
+        a2 = oracle.reconstruct(*out[1][i], s["k"])
+        ref = oracle.pbpqlp(A, s["k"] + p, q, seed=seed + i)
+        if mode == "FP64":
+            assert np.linalg.norm(a1 - a2) <= 1e-12 * np.linalg.norm(A), (i, s)
+            d = np.linalg.norm(a1 - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], s["k"]))
+            assert d / np.linalg.norm(A) <= TOL, (i, s, d)
+        else:
+            # the FP32 triangular solves of this mode round any last-bit Gram
+            # difference at FP32 level: compare against the mode's error bar
+            e_gpu, e_orc = _errors(A, out[0][i], ref, s["k"])
+            assert e_gpu <= 1.1 * e_orc, (i, s, e_gpu, e_orc)
+            assert np.linalg.norm(a1 - a2) <= 1e-2 * e_orc * np.linalg.norm(A), (i, s)
