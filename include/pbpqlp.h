@@ -239,9 +239,10 @@ int pbpqlp_batch_sync_status(pbpqlp_batch_t batch, uint32_t* flags_host);
 
 /*
  * Autotuner of the batched launch geometry: times the batched factorization
- * on the caller's data for each candidate (Gram row chunk 256/512/1024/2048,
- * triangular-solve rows per unit 64/256, and in the TF32 modes the order of
- * the grouped product units) and keeps the fastest in the plan.  Runs the
+ * on the caller's data for each candidate (Gram row chunk 256/512/1024/2048
+ * for the FP64 FMA Grams only, triangular-solve rows per unit 64/128/256, and
+ * in the TF32 modes the order of the grouped product units) and keeps the
+ * fastest in the plan.  Runs the
  * factorization 2 x (number of candidates) times; outputs hold the last run.
  * table_path (optional): appends one JSON line with the batch signature and
  * the chosen values.  *best_ms (optional) gets the best time per call.

@@ -31,15 +31,22 @@ struct MatWs {
     int64_t ldn, ldm;      // their leading dimensions (n, m rounded up to 32)
     // digit Grams: panel digits of the m side, the n side and of D (kept for R = Q^T D)
     size_t Z[3];
+    // Qb = Pbar Ptil as a digit product: row digits of Pbar (exponents Eq, n of
+    // them) and column digits of Ptil
+    size_t Zq, Zt, Eq;
 };
 
-// Digit sets of one matrix: 0 = m-side panels, 1 = n-side panels, 2 = D.
-constexpr int kZm = 0, kZn = 1, kZd = 2;
+// Digit sets of one matrix: 0 = m-side panels, 1 = n-side panels, 2 = D;
+// exponent row 3 holds the column exponents of Ptil.
+constexpr int kZm = 0, kZn = 1, kZd = 2, kEt = 3;
+constexpr int kOzMaps = 8;          // per matrix: 2 per digit set, then Pbar (X box) and Ptil (Y box)
 
 enum LaunchKind {
     L_GAUSS, L_GEMM, L_REDUCE, L_CHOL, L_TRSM, L_SQR, L_MEMSET_CTL, L_SPLIT, L_PSPLIT, L_TC,
     L_MEMSET,      // workspace bytes [off, off + n) to zero
-    L_OZEXP, L_OZSLICE, L_OZ
+    L_OZEXP, L_OZSLICE, L_OZ, L_OZROWS,
+    L_FORK,        // the side stream waits for the main stream here
+    L_JOIN         // the main stream waits for the side stream here
 };
 
 struct Launch {
@@ -48,6 +55,7 @@ struct Launch {
     bool transA;
     size_t off;            // byte offset of the unit list inside the list region
     int n;
+    bool side = false;     // runs on the side stream (between L_FORK and L_JOIN)
 };
 
 constexpr int64_t kGaussPairsPerUnit = 8192;
@@ -76,19 +84,24 @@ struct pbpqlp_batch_s {
     std::vector<MatWs> mw;
     size_t off_status = 0, off_ctl = 0, off_lists = 0, lists_cap = 0, total = 0;
     size_t maps_off = 0;            // tensor-map table inside the list region
-    size_t oz_maps_off = 0;         // digit tensor maps: 6 per matrix (3 sets x {X, Y} boxes)
-    size_t off_oze = 0;             // column exponents of the digit sets: [3][count][ldp] ints
+    size_t oz_maps_off = 0;         // digit tensor maps: kOzMaps per matrix (3 sets x {X, Y} boxes, Pbar, Ptil)
+    size_t off_oze = 0;             // column exponents of the digit sets and of Ptil: [4][count][ldp] ints
     // host copy of the work lists and the launch sequence built for the last buffers
     std::vector<unsigned char> host_lists;
     std::vector<Launch> seq;
     std::vector<const void*> key;   // pointers the lists were built for
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture_stream = nullptr;   // private stream the graph is recorded on
+    cudaStream_t side_stream = nullptr;      // second branch: the Gaussian draw beside the split of A
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool use_graph = true;
     void* last_ws = nullptr;
     ~pbpqlp_batch_s() {
         if (exec) cudaGraphExecDestroy(exec);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (side_stream) cudaStreamDestroy(side_stream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
 };
@@ -118,32 +131,40 @@ size_t lists_bound(const pbpqlp_batch_s* B, int gram_chunk_min) {
         if (B->nprod) {
             units += 8 * 128;                                                   // tensor maps
             units += (size_t)(passes * ((B->m[i] + 127) / 128 + (B->n[i] + 127) / 128)) * sizeof(TcUnit);
-            units += (size_t)((B->m[i] + 31) / 32) * sizeof(SplitUnit);
+            units += (size_t)((B->m[i] + 63) / 64) * sizeof(SplitUnit);
             units += (size_t)passes * ((std::max(B->m[i], B->n[i]) + kPanelRowsPerUnit - 1) / kPanelRowsPerUnit) *
                      sizeof(PanelUnit);
         }
         if (B->oz) {
             // digit maps; per Gram (and R): panel units twice (exponents, digits) and <= 2 x 5 tiles
             const int64_t pr = (std::max(B->m[i], B->n[i]) + kOzPanelRows - 1) / kOzPanelRows + 1;
-            units += 6 * 128;
+            units += kOzMaps * 128;
             units += (size_t)(passes * 6 + 1) * (2 * pr * sizeof(OzPanelUnit) + 10 * sizeof(OzListUnit));
+            // Qb: Pbar row units, Ptil panel units, tiles; Qa copy blocks
+            units += (size_t)((B->n[i] + kOzRowsPerUnit - 1) / kOzRowsPerUnit + 4) * sizeof(OzPanelUnit);
+            units += (size_t)((B->n[i] + kOzBM - 1) / kOzBM * 5) * sizeof(OzListUnit);
+        }
+        {
+            units += (size_t)((B->m[i] + 255) / 256) * sizeof(ReduceUnit);
         }
     }
-    // one list per width bucket: up to 14 GEMM and 7 TRSM buckets per step, 256-byte aligned
-    return units + 64 * 1024 + 256 * 64 + (size_t)(2 * B->q + 2) * 6 * 28 * 256 + 64 * 256;
+    // one list per width bucket: up to 14 GEMM and 14 TRSM buckets per step, 256-byte aligned
+    return units + 64 * 1024 + 256 * 64 + (size_t)(2 * B->q + 2) * 6 * 36 * 256 + 64 * 256;
 }
 
 class ListBuilder {
   public:
     explicit ListBuilder(pbpqlp_batch_s* B) : B_(B) { B_->host_lists.clear(); B_->seq.clear(); }
     template <typename T>
-    void add(int kind, const std::vector<T>& units, int TN = 0, bool transA = false) {
+    void add(int kind, const std::vector<T>& units, int TN = 0, bool transA = false, bool side = false) {
         if (units.empty()) return;
         size_t off = align_up(B_->host_lists.size(), 256);
         B_->host_lists.resize(off + units.size() * sizeof(T));
         std::memcpy(B_->host_lists.data() + off, units.data(), units.size() * sizeof(T));
-        B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size()});
+        B_->seq.push_back(Launch{kind, TN, transA, off, (int)units.size(), side});
     }
+    void fork() { B_->seq.push_back(Launch{L_FORK, 0, false, 0, 0}); }
+    void join() { B_->seq.push_back(Launch{L_JOIN, 0, false, 0, 0}); }
     void memset_ctl() { B_->seq.push_back(Launch{L_MEMSET_CTL, 0, false, 0, 0}); }
     void memset_ws(size_t off, size_t bytes) { B_->seq.push_back(Launch{L_MEMSET, 0, false, off, (int)bytes}); }
     // GEMM units bucketed by their own width (16-column groups), one launch per bucket
@@ -152,16 +173,17 @@ class ListBuilder {
         for (const GemmUnit& g : units) bucket[(g.N + 15) / 16].push_back(g);
         for (int tn = 1; tn <= kMaxEll / 16; ++tn) add(L_GEMM, bucket[tn], tn, transA);
     }
-    // triangular-solve units bucketed by 32-column groups of their l
-    void add_trsm(const std::vector<TrsmUnit>& units) {
-        std::vector<TrsmUnit> bucket[kMaxEll / 32 + 2];
-        int lm[kMaxEll / 32 + 2] = {};
+    // triangular-solve units bucketed by `width`-column groups of their l
+    // (32: warp-per-row FP64 solves; 16: the unrolled FP32 row solves)
+    void add_trsm(const std::vector<TrsmUnit>& units, int width) {
+        std::vector<TrsmUnit> bucket[kMaxEll / 16 + 2];
+        int lm[kMaxEll / 16 + 2] = {};
         for (const TrsmUnit& t : units) {
-            const int u = (t.l + 31) / 32;
+            const int u = (t.l + width - 1) / width;
             bucket[u].push_back(t);
             lm[u] = std::max(lm[u], t.l);
         }
-        for (int u = 1; u <= kMaxEll / 32 + 1; ++u) add(L_TRSM, bucket[u], lm[u]);
+        for (int u = 1; u <= kMaxEll / width + 1; ++u) add(L_TRSM, bucket[u], lm[u]);
     }
     // raw table at the start of the list region (the tensor maps)
     size_t raw(const void* data, size_t bytes) {
@@ -195,6 +217,22 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     uint32_t* status = (uint32_t*)(pt.ws + B->off_status);
     int* ctl = (int*)(pt.ws + B->off_ctl);
 
+    // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i, on the side stream:
+    // FP64-pipe bound, it runs beside the split of A (HBM bound)
+    {
+        std::vector<MatUnit> u;
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t npairs = (B->m[i] * (int64_t)B->l[i] + 1) / 2;
+            for (int64_t b0 = 0; b0 < npairs; b0 += kGaussPairsPerUnit) {
+                MatUnit x{};
+                x.l = B->l[i]; x.rows = B->m[i]; x.out = P64(pt, B->mw[i].Xm); x.ld = ldp;
+                x.seed = B->seed + (uint64_t)i; x.b0 = b0; x.b1 = b0 + kGaussPairsPerUnit;
+                u.push_back(x);
+            }
+        }
+        lb.fork();
+        lb.add(L_GAUSS, u, 0, false, true);
+    }
     // TF32 modes: the tensor-map table (8 maps per matrix) and the split of every A_i
     if (B->nprod) {
         std::vector<CUtensorMap> maps((size_t)8 * cnt);
@@ -215,27 +253,36 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         std::vector<SplitUnit> su;
         for (int i = 0; i < cnt; ++i) {
             const MatWs& w = B->mw[i];
-            for (int64_t r0 = 0; r0 < B->m[i]; r0 += 32) {
+            for (int64_t r0 = 0; r0 < B->m[i]; r0 += 64) {
                 SplitUnit x{};
                 x.A = pt.A[i]; x.lda = pt.lda[i]; x.a_f32 = B->a_f32; x.m = B->m[i]; x.n = B->n[i]; x.r0 = r0;
                 x.hi = P32(pt, w.Ahi); x.lo = w.Alo ? P32(pt, w.Alo) : nullptr; x.ldh = w.ldn;
                 x.thi = P32(pt, w.Athi); x.tlo = w.Atlo ? P32(pt, w.Atlo) : nullptr; x.ldt = w.ldm;
+                // hi / lo and their transposes sit 256-aligned with ld a multiple of 32 floats
+                x.vec_ok = ((uintptr_t)x.A & 15u) == 0 && (x.lda * (B->a_f32 ? 4 : 8)) % 16 == 0;
                 su.push_back(x);
             }
         }
-        lb.add(L_SPLIT, su);
+        int64_t nmax = 1;
+        for (int i = 0; i < cnt; ++i) nmax = std::max(nmax, B->n[i]);
+        lb.add(L_SPLIT, su, (int)((nmax + 63) / 64));
     }
     // digit Grams: maps of the three digit sets of every matrix (X box 128 rows, Y box 48)
     if (B->oz) {
-        std::vector<CUtensorMap> zm((size_t)6 * cnt);
-        for (int i = 0; i < cnt; ++i)
+        std::vector<CUtensorMap> zm((size_t)kOzMaps * cnt);
+        for (int i = 0; i < cnt; ++i) {
+            CUtensorMap* mp = &zm[(size_t)kOzMaps * i];
             for (int st = 0; st < 3; ++st) {
                 const void* S = pt.ws + B->mw[i].Z[st];
                 const int64_t K = st == kZn ? B->n[i] : B->m[i];
-                if (!make_oz_map(&zm[(size_t)6 * i + 2 * st], S, B->l[i], K, kOzBM) ||
-                    !make_oz_map(&zm[(size_t)6 * i + 2 * st + 1], S, B->l[i], K, kOzBN))
+                if (!make_oz_map(&mp[2 * st], S, B->l[i], K, kOzBM) ||
+                    !make_oz_map(&mp[2 * st + 1], S, B->l[i], K, kOzBN))
                     return PBPQLP_EINVAL;
             }
+            if (!make_oz_map(&mp[6], pt.ws + B->mw[i].Zq, B->n[i], B->l[i], kOzBM) ||
+                !make_oz_map(&mp[7], pt.ws + B->mw[i].Zt, B->l[i], B->l[i], kOzBN))
+                return PBPQLP_EINVAL;
+        }
         B->oz_maps_off = lb.raw(zm.data(), zm.size() * sizeof(CUtensorMap));
     }
     auto oz_exps = [&](int st, int i) {
@@ -262,7 +309,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         for (int m0 = 0; m0 < B->l[i]; m0 += kOzBM)
             for (int n0 = 0; n0 < B->l[i]; n0 += kOzBN) {
                 OzListUnit u{};
-                u.mapx = 6 * i + 2 * sx; u.mapy = 6 * i + 2 * sy + 1;
+                u.mapx = kOzMaps * i + 2 * sx; u.mapy = kOzMaps * i + 2 * sy + 1;
                 u.m0 = m0; u.n0 = n0; u.KI = (int)((rows + kOzBK - 1) / kOzBK);
                 u.Rx = B->l[i]; u.Ry = B->l[i]; u.ex = oz_exps(sx, i); u.ey = oz_exps(sy, i);
                 u.C = C; u.ldc = B->l[i]; u.cond = cond;
@@ -274,20 +321,6 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
             std::stable_sort(ou.begin(), ou.end(), [](const OzListUnit& a, const OzListUnit& b) { return a.KI > b.KI; });
         lb.add(L_OZ, ou);
     };
-    // Gaussian test matrices Phi_i (m_i x l_i) into Xm_i
-    {
-        std::vector<MatUnit> u;
-        for (int i = 0; i < cnt; ++i) {
-            const int64_t npairs = (B->m[i] * (int64_t)B->l[i] + 1) / 2;
-            for (int64_t b0 = 0; b0 < npairs; b0 += kGaussPairsPerUnit) {
-                MatUnit x{};
-                x.l = B->l[i]; x.rows = B->m[i]; x.out = P64(pt, B->mw[i].Xm); x.ld = ldp;
-                x.seed = B->seed + (uint64_t)i; x.b0 = b0; x.b1 = b0 + kGaussPairsPerUnit;
-                u.push_back(x);
-            }
-        }
-        lb.add(L_GAUSS, u);
-    }
     // one product with A_i for every matrix: out_i = op(A_i) Y_i
     auto product = [&](bool transA, auto ysel, auto csel) {
         if (B->nprod) {
@@ -397,7 +430,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
                 lb.add(L_REDUCE, ru);
             }
             lb.add(L_CHOL, cu);
-            lb.add_trsm(tu);
+            lb.add_trsm(tu, B->nprod ? 16 : 32);
         }
     };
     auto Xm = [&](int i) { return P64(pt, B->mw[i].Xm); };
@@ -406,6 +439,7 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     auto Xn = [&](int i) { return P64(pt, B->mw[i].Xn); };
     auto Yn = [&](int i) { return P64(pt, B->mw[i].Yn); };
 
+    lb.join();
     product(true, Xm, Xn);                  // C = A^T Phi (Eq. 3)
     orth(1, Xn, Xn, Yn);                    // Pbar = orth(C) (Eq. 4)
     for (int it = 0; it < B->q; ++it) {     // power iterations (Section III-B)
@@ -460,7 +494,38 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
         }
         lb.add(L_SQR, u);
     }
-    {                                       // Qb = Pbar Ptil (Eq. 8); Qa = Q (copy to ld l)
+    if (B->oz) {                            // Qb = Pbar Ptil (Eq. 8) from the digits of Pbar and Ptil
+        std::vector<OzPanelUnit> ru, pu;
+        std::vector<OzListUnit> ou;
+        for (int i = 0; i < cnt; ++i) {
+            const MatWs& w = B->mw[i];
+            const int l = B->l[i];
+            for (int64_t r0 = 0; r0 < B->n[i]; r0 += kOzRowsPerUnit) {
+                OzPanelUnit x{};
+                x.P = Xn(i); x.ldp = ldp; x.rows = B->n[i]; x.r0 = r0; x.N = l;
+                x.eraw = (int*)(pt.ws + w.Eq); x.S = pt.ws + w.Zq;
+                ru.push_back(x);
+            }
+            for (int64_t r0 = 0; r0 < oz_kpad(l); r0 += kOzPanelRows) {
+                OzPanelUnit y{};
+                y.P = P64(pt, w.Pt); y.ldp = l; y.rows = l; y.r0 = r0; y.N = l; y.eraw = oz_exps(kEt, i);
+                y.S = pt.ws + w.Zt;
+                pu.push_back(y);
+            }
+            for (int m0 = 0; m0 < B->n[i]; m0 += kOzBM)
+                for (int n0 = 0; n0 < l; n0 += kOzBN) {
+                    OzListUnit u{};
+                    u.mapx = kOzMaps * i + 6; u.mapy = kOzMaps * i + 7;
+                    u.m0 = m0; u.n0 = n0; u.KI = (l + kOzBK - 1) / kOzBK;
+                    u.Rx = (int)B->n[i]; u.Ry = l; u.ex = (const int*)(pt.ws + w.Eq); u.ey = oz_exps(kEt, i);
+                    u.C = pt.Qb[i]; u.ldc = l;
+                    ou.push_back(u);
+                }
+        }
+        lb.add(L_OZROWS, ru);
+        oz_add_panels(kEt, pu);
+        oz_add_tiles(ou);
+    } else {                                // Qb = Pbar Ptil (Eq. 8)
         std::vector<GemmUnit> gu;
         for (int i = 0; i < cnt; ++i) {
             const int l = B->l[i];
@@ -472,13 +537,16 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
             }
         }
         lb.add_gemm(gu, false);
-        std::vector<ReduceUnit> cu;          // a one-term "reduction" is a strided copy
-        for (int i = 0; i < cnt; ++i) {
-            ReduceUnit r{};
-            r.part = Xm(i); r.C = pt.Qa[i]; r.ps = 0; r.ldp = ldp; r.ldc = B->l[i]; r.M = B->m[i]; r.N = B->l[i];
-            r.S = 1; r.cond = nullptr;
-            cu.push_back(r);
-        }
+    }
+    {                                       // Qa = Q (copy to ld l; a one-term "reduction"), 256-row blocks
+        std::vector<ReduceUnit> cu;
+        for (int i = 0; i < cnt; ++i)
+            for (int64_t r0 = 0; r0 < B->m[i]; r0 += 256) {
+                ReduceUnit r{};
+                r.part = Xm(i) + r0 * ldp; r.C = pt.Qa[i] + r0 * B->l[i]; r.ps = 0; r.ldp = ldp; r.ldc = B->l[i];
+                r.M = std::min<int64_t>(256, B->m[i] - r0); r.N = B->l[i]; r.S = 1; r.cond = nullptr;
+                cu.push_back(r);
+            }
         lb.add(L_REDUCE, cu);
     }
     if (B->host_lists.size() > B->lists_cap) return PBPQLP_EWORKSPACE;
@@ -501,24 +569,38 @@ int enqueue(pbpqlp_batch_s* B, char* ws, cudaStream_t s) {
             B->ev.push_back(e);
         }
     }
+    if (!B->side_stream && cudaStreamCreateWithFlags(&B->side_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return PBPQLP_ECUDA;
+    if (!B->ev_fork && cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess) return PBPQLP_ECUDA;
+    if (!B->ev_join && cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess) return PBPQLP_ECUDA;
     for (const Launch& L : B->seq) {
         const void* u = lists + L.off;
+        const cudaStream_t ls = L.side ? B->side_stream : s;
         switch (L.kind) {
+            case L_FORK:
+                PBQ_TRY(cudaEventRecord(B->ev_fork, s));
+                PBQ_TRY(cudaStreamWaitEvent(B->side_stream, B->ev_fork, 0));
+                break;
+            case L_JOIN:
+                PBQ_TRY(cudaEventRecord(B->ev_join, B->side_stream));
+                PBQ_TRY(cudaStreamWaitEvent(s, B->ev_join, 0));
+                break;
             case L_MEMSET_CTL: PBQ_TRY(cudaMemsetAsync(ctl, 0, sizeof(int) * 16 * (size_t)B->count, s)); break;
             case L_MEMSET: PBQ_TRY(cudaMemsetAsync(ws + L.off, 0, (size_t)L.n, s)); break;
             case L_OZEXP: PBQ_TRY(launch_oz_panel_exp_list((const OzPanelUnit*)u, L.n, s)); break;
             case L_OZSLICE: PBQ_TRY(launch_oz_panel_slice_list((const OzPanelUnit*)u, L.n, s)); break;
+            case L_OZROWS: PBQ_TRY(launch_oz_rows_list((const OzPanelUnit*)u, L.n, s)); break;
             case L_OZ:
                 PBQ_TRY(launch_oz_list(lists + B->oz_maps_off, (const OzListUnit*)u, L.n, B->num_sms,
                                        (uint32_t*)(ws + B->off_status), s));
                 break;
-            case L_GAUSS: PBQ_TRY(launch_gaussian_list((const MatUnit*)u, L.n, s)); break;
+            case L_GAUSS: PBQ_TRY(launch_gaussian_list((const MatUnit*)u, L.n, ls)); break;
             case L_GEMM: PBQ_TRY(launch_dgemm_list(L.TN, L.transA, (const GemmUnit*)u, L.n, s)); break;
             case L_REDUCE: PBQ_TRY(launch_reduce_list((const ReduceUnit*)u, L.n, s)); break;
             case L_CHOL: PBQ_TRY(launch_cholesky_list((const MatUnit*)u, L.n, B->lmax, s)); break;
             case L_TRSM: PBQ_TRY(launch_trsm_list((const TrsmUnit*)u, L.n, L.TN, s, B->nprod > 0)); break;
             case L_SQR: PBQ_TRY(launch_small_qr_list((const MatUnit*)u, L.n, B->lmax, s)); break;
-            case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, s)); break;
+            case L_SPLIT: PBQ_TRY(launch_split_tf32_list((const SplitUnit*)u, L.n, L.TN, B->a_f32, s)); break;
             case L_PSPLIT: PBQ_TRY(launch_split_panel_tf32_list((const PanelUnit*)u, L.n, s)); break;
             case L_TC: {
                 const bool t = B->timing && evi + 1 < (int)B->ev.size();
@@ -580,9 +662,12 @@ void layout(pbpqlp_batch_s* B) {
             w.Z[kZm] = take(oz_digit_bytes(l, m));
             w.Z[kZn] = take(oz_digit_bytes(l, n));
             w.Z[kZd] = take(oz_digit_bytes(l, m));
+            w.Zq = take(oz_digit_bytes(n, l));
+            w.Zt = take(oz_digit_bytes(l, l));
+            w.Eq = take(sizeof(int) * (size_t)n);
         }
     }
-    if (B->oz) B->off_oze = take(sizeof(int) * 3 * (size_t)B->count * (size_t)ldp);
+    if (B->oz) B->off_oze = take(sizeof(int) * 4 * (size_t)B->count * (size_t)ldp);
     B->lists_cap = lists_bound(B, 256);
     B->off_lists = take(B->lists_cap);
     B->total = off;
@@ -644,7 +729,8 @@ int run(pbpqlp_batch_s* B, const Ptrs& pt, size_t ws_bytes) {
     if (B->exec) {
         PBQ_TRY(cudaGraphLaunch(B->exec, B->stream));
         int64_t kernels = 0;
-        for (const Launch& L : B->seq) kernels += (L.kind != L_MEMSET_CTL && L.kind != L_MEMSET);
+        for (const Launch& L : B->seq)
+            kernels += (L.kind != L_MEMSET_CTL && L.kind != L_MEMSET && L.kind != L_FORK && L.kind != L_JOIN);
         count_launches(kernels);
         return PBPQLP_OK;
     }
@@ -675,6 +761,7 @@ int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const 
         B->lmax = std::max(B->lmax, (int)l);
     }
     B->nprod = mode == PBPQLP_MODE_TF32X3 ? 3 : mode == PBPQLP_MODE_TF32 ? 1 : 0;
+    if (B->nprod) B->trsm_rows = 128;   // the FP32 row solves run 128 rows per CTA
     if (B->nprod && B->lmax > kTcListBNMax) { delete B; return PBPQLP_EUNSUPPORTED; }
     {
         int dev = 0, sms = 0;
@@ -747,7 +834,7 @@ int pbpqlp_batch_autotune(pbpqlp_batch_t B, const void* const* A, const int64_t*
                           double* best_ms) {
     if (!B) return PBPQLP_EINVAL;
     const int chunks[] = {256, 512, 1024, 2048};
-    const int trows[] = {64, 256};
+    const int trows[] = {64, 128, 256};
     const int sorts[] = {1, 0};
     double best = 1e300;
     int bc = B->gram_chunk, bt = B->trsm_rows, bs = B->tc_sorted;
@@ -758,6 +845,7 @@ int pbpqlp_batch_autotune(pbpqlp_batch_t B, const void* const* A, const int64_t*
         for (int tr : trows)
             for (int so : sorts) {
                 if (!B->nprod && so == 0) continue;   // unit order only matters for the grouped products
+                if (B->oz && gc != 512) continue;     // digit Grams take whole contractions: no row chunks
                 B->gram_chunk = gc; B->trsm_rows = tr; B->tc_sorted = so;
                 for (int i = 0; i < B->count; ++i) {
                     B->mw[i].S_m = (int)((B->m[i] + gc - 1) / gc);

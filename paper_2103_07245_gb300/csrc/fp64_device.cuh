@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "newton_device.cuh"
 
 namespace pbq {
 
@@ -148,9 +149,8 @@ __device__ __forceinline__ void dev_cholesky(int l, int64_t rows, const double* 
                 f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
                 if (f) s_fail = f;
                 else {
-                    const double r = sqrt(d);
-                    S[pidx(l, i, i)] = r;
-                    inv = 1.0 / r;
+                    inv = rsqrt_nr(d);   // no FP64 square root or division on the pivot chain
+                    S[pidx(l, i, i)] = d * inv;
                     dinv[i] = inv;
                 }
             }

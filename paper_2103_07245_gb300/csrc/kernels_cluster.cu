@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "newton_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -198,39 +199,6 @@ cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kQrThreads = 512;
-
-// 1/d and 1/sqrt(d) for positive normal d: FP32 seeds refined by two
-// Newton-Raphson steps in FP64 (FP64 division and square root take ~430 and
-// ~670 cycles on GB300, and every reflector waits on them); other inputs take
-// the library operations.
-__device__ __forceinline__ double rcp_newton(double d) {
-    const long long b = __double_as_longlong(d);
-    const int eb = (int)((b >> 52) & 0x7FF);
-    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / d;
-    const int k = eb - 1023;
-    const double m = __longlong_as_double(b - (long long)k * (1LL << 52));
-    double y = (double)__frcp_rn((float)m);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double e = fma(-m, y, 1.0);
-        y = fma(y, e, y);
-    }
-    return y * __longlong_as_double((long long)(1023 - k) << 52);
-}
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    const long long b = __double_as_longlong(d);
-    const int eb = (int)((b >> 52) & 0x7FF);
-    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / sqrt(d);
-    const int k = (eb - 1023) >> 1;
-    const double m = __longlong_as_double(b - (long long)(2 * k) * (1LL << 52));
-    double y = (double)rsqrtf((float)m);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double e = fma(-m, y * y, 1.0);
-        y = fma(0.5 * y, e, y);
-    }
-    return y * __longlong_as_double((long long)(1023 - k) << 52);
-}
 }
 
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kQrThreads)
@@ -271,11 +239,11 @@ k_small_qr_cluster(int l, const double* __restrict__ R, double* __restrict__ L, 
             const double x0 = wj[j];
             const double s2 = x0 * x0 + t;
             if (s2 != 0.0) {
-                const double nrm = s2 * rsqrt_newton(s2);
+                const double nrm = s2 * rsqrt_nr(s2);
                 alpha = (x0 >= 0.0) ? -nrm : nrm;
                 const double v0 = x0 - alpha;
                 vj[j] = v0;
-                t2 = 2.0 * rcp_newton(v0 * v0 + t);
+                t2 = 2.0 * rcp_nr(v0 * v0 + t);
             }
             tvv_own[lj] = t2;
         }

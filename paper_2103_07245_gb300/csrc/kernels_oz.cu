@@ -774,16 +774,12 @@ __global__ void k_oz_a_slice(int64_t m, int64_t n, const Tin* __restrict__ A, in
     }
 }
 
-// Digits of a row-major matrix P (rows x K, ld ldp; K up to a few thousand)
-// by rows in one pass: one warp per row takes the row's largest exponent field
-// (warp max) and writes the row's digits, zero up to the padded K.
-__global__ void __launch_bounds__(512)
-k_oz_rows(int64_t rows, int64_t K, const double* __restrict__ P, int64_t ldp, int* __restrict__ er,
-          uint16_t* __restrict__ S, const int* __restrict__ cond) {
-    if (cond && *cond == 0) return;
+// Digits of row r of a row-major matrix P (rows x K, ld ldp; K up to a few
+// thousand) in one pass by one warp: the row's largest exponent field (warp
+// max), then the row's digits, zero up to the padded K.
+__device__ __forceinline__ void oz_row_digits(int64_t r, int64_t rows, int64_t K, const double* __restrict__ P,
+                                              int64_t ldp, int* __restrict__ er, uint16_t* __restrict__ S) {
     const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * 16 + (threadIdx.x >> 5);
-    if (r >= rows) return;
     const double* pr = P + r * ldp;
     const int64_t Kp = oz_kpad(K);
     int mx = 0;
@@ -798,6 +794,22 @@ k_oz_rows(int64_t rows, int64_t K, const double* __restrict__ P, int64_t ldp, in
 #pragma unroll
         for (int s = 0; s < kOzDigits; ++s) S[oz_idx(s, r, k, rows, Kp)] = digit_bf16(d[s]);
     }
+}
+
+__global__ void __launch_bounds__(512)
+k_oz_rows(int64_t rows, int64_t K, const double* __restrict__ P, int64_t ldp, int* __restrict__ er,
+          uint16_t* __restrict__ S, const int* __restrict__ cond) {
+    if (cond && *cond == 0) return;
+    const int64_t r = (int64_t)blockIdx.x * 16 + (threadIdx.x >> 5);
+    if (r < rows) oz_row_digits(r, rows, K, P, ldp, er, S);
+}
+
+// Row digits of the units: unit b covers rows r0 .. r0 + 15 of its matrix.
+__global__ void __launch_bounds__(512) k_oz_rows_list(const OzPanelUnit* __restrict__ units) {
+    const OzPanelUnit& U = units[blockIdx.x];
+    if (U.cond && *U.cond == 0) return;
+    const int64_t r = U.r0 + (threadIdx.x >> 5);
+    if (r < U.rows) oz_row_digits(r, U.rows, U.N, U.P, U.ldp, U.eraw, (uint16_t*)U.S);
 }
 
 // Column exponents of the panel units: unit b covers rows r0 .. r0 + 127 of
@@ -1006,6 +1018,13 @@ cudaError_t launch_oz_list(const void* maps, const OzListUnit* units, int n, int
 cudaError_t launch_oz_panel_exp_list(const OzPanelUnit* units, int n, cudaStream_t s) {
     if (n < 1) return cudaSuccess;
     k_oz_panel_exp_list<<<n, dim3(32, 8), 0, s>>>(units);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_rows_list(const OzPanelUnit* units, int n, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    k_oz_rows_list<<<n, 512, 0, s>>>(units);
     count_launches(1);
     return cudaGetLastError();
 }

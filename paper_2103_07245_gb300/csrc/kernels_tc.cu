@@ -31,6 +31,7 @@
 
 #include "internal.h"
 #include "tc_internal.h"
+#include "split_device.cuh"
 #include "tc_device.cuh"
 
 namespace pbq {
@@ -407,40 +408,7 @@ cudaError_t launch_tc_product(int nprod, const TcOperands& op, const TcGeom& g, 
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Operand preparation: hi/lo splits (row-major and transposed) into BF16
-// (hi = RN_bf16(x), lo = RN_bf16(x - hi)) or TF32 held in FP32
-// (hi = RN_tf32(x), lo = RN_tf32(x - hi), rounding by cvt.rna.tf32).
-// ---------------------------------------------------------------------------
-// Splits are formed in the input's own precision: for x in FP32, hi = RN(x)
-// and x - hi are exact in FP32 (no FP64 work, which GB300 runs at a small
-// fraction of the FP32 rate); an FP64 input (the panels, or an FP64 A) is
-// split in FP64 so that hi = RN(x) is the correctly rounded value of x.
-struct SplitBf16 {
-    using T = __nv_bfloat16;
-    static __device__ __forceinline__ T rn(float x) { return __float2bfloat16_rn(x); }
-    static __device__ __forceinline__ T rn(double x) { return __double2bfloat16(x); }
-    static __device__ __forceinline__ float back(T h) { return __bfloat162float(h); }
-    static __device__ __forceinline__ T zero() { return __float2bfloat16_rn(0.f); }
-};
-struct SplitTf32 {
-    using T = float;
-    static __device__ __forceinline__ T rn(float x) {
-        uint32_t r;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-        return __uint_as_float(r);
-    }
-    // hi = RNA_tf32(RN_fp32(x)): the split needs hi + lo to carry x to about
-    // 2^-22 relative, which this two-step rounding provides
-    static __device__ __forceinline__ T rn(double x) { return rn((float)x); }
-    static __device__ __forceinline__ float back(T h) { return h; }
-    static __device__ __forceinline__ T zero() { return 0.f; }
-};
-
-// 64 x 64 tiles, 256 threads: a thread converts 16 consecutive elements of a
-// row (16-byte vector loads and stores when the tile is whole and the
-// pointers allow it), and writes 16 consecutive elements of a transposed row
-// from shared memory.  Partial tiles take the same path element by element.
+// 64 x 64 tiles of A, one per CTA (split_tile64).
 template <typename Tin, typename SP>
 __global__ void __launch_bounds__(256)
 k_split_a(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, typename SP::T* __restrict__ hi,
@@ -450,88 +418,8 @@ k_split_a(int64_t m, int64_t n, const Tin* __restrict__ A, int64_t lda, typename
     constexpr int PAD = 16 / (int)sizeof(T);
     __shared__ __align__(16) T sh[64][64 + PAD];
     __shared__ __align__(16) T sl[64][64 + PAD];
-    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
-    const int tid = threadIdx.x, rr = tid >> 2, cq = (tid & 3) * 16;
-    const bool full = vec_ok && r0 + 64 <= m && c0 + 64 <= n;
-    const int64_t r = r0 + rr;
-    __align__(16) T h[16];
-    __align__(16) T lw[16];
-    Tin x[16];
-    if (full) {
-        const Tin* src = A + r * lda + c0 + cq;
-        if (sizeof(Tin) == 4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 v = ((const float4*)src)[q];
-                x[4 * q] = (Tin)v.x; x[4 * q + 1] = (Tin)v.y; x[4 * q + 2] = (Tin)v.z; x[4 * q + 3] = (Tin)v.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const double2 v = ((const double2*)src)[q];
-                x[2 * q] = v.x; x[2 * q + 1] = v.y;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int64_t c = c0 + cq + k;
-            x[k] = (r < m && c < n) ? A[r * lda + c] : (Tin)0;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        h[k] = SP::rn(x[k]);
-        lw[k] = SP::rn(x[k] - (Tin)SP::back(h[k]));
-    }
-    constexpr int NV = 16 * (int)sizeof(T) / 16;   // 16-byte vectors per 16 elements
-    if (full) {
-        uint4* dh = (uint4*)(hi + r * ldh + c0 + cq);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) dh[q] = ((const uint4*)h)[q];
-        if (lo) {
-            uint4* dl = (uint4*)(lo + r * ldh + c0 + cq);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) dl[q] = ((const uint4*)lw)[q];
-        }
-    } else if (r < m) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int64_t c = c0 + cq + k;
-            if (c < n) {
-                hi[r * ldh + c] = h[k];
-                if (lo) lo[r * ldh + c] = lw[k];
-            }
-        }
-    }
-    if (!thi) return;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        sh[cq + k][rr] = h[k];
-        sl[cq + k][rr] = lw[k];
-    }
-    __syncthreads();
-    // transposed: row c0 + rr of A^T, columns r0 + cq .. r0 + cq + 15
-    const int64_t ct = c0 + rr;
-    if (full) {
-        uint4* dh = (uint4*)(thi + ct * ldt + r0 + cq);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) dh[q] = ((const uint4*)&sh[rr][cq])[q];
-        if (tlo) {
-            uint4* dl = (uint4*)(tlo + ct * ldt + r0 + cq);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) dl[q] = ((const uint4*)&sl[rr][cq])[q];
-        }
-    } else if (ct < n) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int64_t rt = r0 + cq + k;
-            if (rt < m) {
-                thi[ct * ldt + rt] = sh[rr][cq + k];
-                if (tlo) tlo[ct * ldt + rt] = sl[rr][cq + k];
-            }
-        }
-    }
+    split_tile64<Tin, SP>((int64_t)blockIdx.y * 64, (int64_t)blockIdx.x * 64, m, n, A, lda, hi, lo, ldh, thi, tlo, ldt,
+                          vec_ok, sh, sl);
 }
 
 template <typename SP>

@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "split_device.cuh"
 #include "tc_device.cuh"
 #include "tc_internal.h"
 
@@ -264,46 +265,25 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
+// Unit: rows r0 .. r0 + 63 of one matrix; CTA (unit, y) takes its 64 x 64
+// tile y (split_tile64), CTAs past the matrix's width exit at once.
+template <typename Tin>
 __global__ void __launch_bounds__(256) k_split_tf32_list(const SplitUnit* __restrict__ units) {
-    __shared__ float sh[32][33], sl[32][33];
-    const SplitUnit u = units[blockIdx.x];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int64_t c0 = 0; c0 < u.n; c0 += 32) {
-        for (int k = ty; k < 32; k += 8) {
-            const int64_t r = u.r0 + k, cc = c0 + tx;
-            float h = 0.f, l = 0.f;
-            if (r < u.m && cc < u.n) {
-                // an FP32 A is split in FP32 (x - hi exact); an FP64 A in FP64
-                if (u.a_f32) {
-                    const float x = ((const float*)u.A)[r * u.lda + cc];
-                    h = to_tf32(x);
-                    l = to_tf32(x - h);
-                } else {
-                    const double x = ((const double*)u.A)[r * u.lda + cc];
-                    h = to_tf32((float)x);
-                    l = to_tf32((float)(x - (double)h));
-                }
-                u.hi[r * u.ldh + cc] = h;
-                if (u.lo) u.lo[r * u.ldh + cc] = l;
-            }
-            sh[k][tx] = h;
-            sl[k][tx] = l;
-        }
-        __syncthreads();
-        for (int k = ty; k < 32; k += 8) {
-            const int64_t cc = c0 + k, r = u.r0 + tx;
-            if (cc < u.n && r < u.m) {
-                u.thi[cc * u.ldt + r] = sh[tx][k];
-                if (u.tlo) u.tlo[cc * u.ldt + r] = sl[tx][k];
-            }
-        }
-        __syncthreads();
-    }
+    __shared__ __align__(16) float sh[64][68];
+    __shared__ __align__(16) float sl[64][68];
+    const SplitUnit& u = units[blockIdx.x];
+    const int64_t c0 = (int64_t)blockIdx.y * 64;
+    if (c0 >= u.n) return;
+    split_tile64<Tin, SplitTf32>(u.r0, c0, u.m, u.n, (const Tin*)u.A, u.lda, u.hi, u.lo, u.ldh, u.thi, u.tlo, u.ldt,
+                                 u.vec_ok, sh, sl);
 }
 
-cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, cudaStream_t s) {
+cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, int col_tiles, int a_f32, cudaStream_t s) {
     if (nunits <= 0) return cudaSuccess;
-    k_split_tf32_list<<<nunits, 256, 0, s>>>(units);
+    if (col_tiles < 1 || col_tiles > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)nunits, (unsigned)col_tiles);
+    if (a_f32) k_split_tf32_list<float><<<grid, 256, 0, s>>>(units);
+    else k_split_tf32_list<double><<<grid, 256, 0, s>>>(units);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,0 +1,47 @@
+// 1/d and 1/sqrt(d) in FP64 without FP64 division or square root, for the
+// sequential pivot chains of the Cholesky and QR kernels: a dependent FP64
+// FMA takes 64 cycles on GB300, an FP64 square root ~670 and a division ~430.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+namespace pbq {
+
+// 1/d for a positive normal double: d = m 2^k with m in [1, 2), an FP32 seed
+// for 1/m refined by two Newton-Raphson steps y += y (1 - m y) (each doubles
+// the correct bits: ~24 -> ~48 -> 53), scaled by 2^-k.  Other inputs take the
+// library division.
+__device__ __forceinline__ double rcp_nr(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / d;
+    const int k = eb - 1023;
+    const double m = __longlong_as_double(b - (long long)k * (1LL << 52));
+    double y = (double)__frcp_rn((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+// 1/sqrt(d) for a positive normal double: d = m 4^k with m in [1, 4), an FP32
+// seed for 1/sqrt(m) refined by two Newton-Raphson steps y += y (1 - m y^2) / 2,
+// scaled by 2^-k.  Other inputs take the library operations.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    const long long b = __double_as_longlong(d);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / sqrt(d);
+    const int k = (eb - 1023) >> 1;   // floor((eb - 1023) / 2)
+    const double m = __longlong_as_double(b - (long long)(2 * k) * (1LL << 52));
+    double y = (double)rsqrtf((float)m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-m, y * y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y * __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+}  // namespace pbq

@@ -107,5 +107,9 @@ cudaError_t launch_oz_panel_exp_list(const OzPanelUnit* units, int n, cudaStream
 // Digits of every unit's rows, up to the padded contraction length (the
 // units must cover oz_kpad(rows)), from the final eraw.
 cudaError_t launch_oz_panel_slice_list(const OzPanelUnit* units, int n, cudaStream_t s);
+// Row form: rows r0 .. r0 + 15 of a row-major P (rows x N, ld ldp) as the
+// operand {S, rows, N}, row exponents into eraw (one warp per row, no zeroing needed).
+constexpr int kOzRowsPerUnit = 16;
+cudaError_t launch_oz_rows_list(const OzPanelUnit* units, int n, cudaStream_t s);
 
 }  // namespace pbq

@@ -68,10 +68,13 @@ bool make_map_f32(void* map128, const void* base, int64_t rows, int64_t cols, in
 struct SplitUnit {
     const void* A;
     float *hi, *lo, *thi, *tlo;
-    int64_t lda, ldh, ldt, m, n, r0;
+    int64_t lda, ldh, ldt, m, n, r0;   // rows r0 .. r0 + 63
     int a_f32;
+    int vec_ok;                        // 16-byte aligned pointers and leading dimensions
 };
-cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, cudaStream_t s);
+// col_tiles: 64-column tiles of the widest matrix; a_f32: element type of
+// every unit's A (one launch handles one type)
+cudaError_t launch_split_tf32_list(const SplitUnit* units, int nunits, int col_tiles, int a_f32, cudaStream_t s);
 // A row block of one panel: Y (rows x N FP64, ld ldy) into transposed TF32 hi/lo (N x rows, ld ldt).
 struct PanelUnit {
     const double* Y;
