@@ -133,8 +133,8 @@ def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
 KERNEL_SOURCES = {
     "dgemm_skinny_fp64_8000": ("fp64_device.cuh", "__device__ __forceinline__ void dev_dgemm_tile",
                                "__device__ __forceinline__ int64_t pidx"),
-    "oz_gemm_fp64emu_8000": ("kernels_oz.cu", "k_oz_gemm(const __grid_constant__",
-                             "// Digit preparation"),
+    "oz_gemm_fp64emu_8000": ("kernels_oz.cu", "// The MMAs of one stage (two 16-deep k-steps)",
+                             "// The grouped product kernel"),
 }
 
 
