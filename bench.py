@@ -45,6 +45,11 @@ WORKLOADS = {
                          mode="FP64_EMU", compare=None,
                          desc="FP64-accurate products as exact BF16 digit sums on the tensor cores, "
                               "A = U diag(exp(-i/40)) V^T, Haar U V, 8000x8000, k=100 p=10 q=2"),
+    "csr_100k": dict(sparse=True, m=100000, n=100000, k=100, p=10, q=2, nnz_per_row=100.0, rank=110, support=150,
+                     mode="FP64",
+                     desc="sparse FP64 (CSR, Section III-C): 100000x100000, ~100 N(0,1) entries per row at uniform "
+                          "columns plus 110 sparse rank-one terms e^(-i/20) sqrt(mn) u_i v_i^T on 150x150 "
+                          "supports (12.4M nonzeros), k=100 p=10 q=2"),
     "bf16x3_10000": dict(m=10000, n=10000, k=200, p=20, q=2, gen="xyt", rank=200, eps=1e-3, mode="BF16X3",
                          compare=None,
                          desc="split-BF16 mixed, A = X Y^T + 1e-3 E (FP32), 10000x10000, k=200 p=20 q=2 (profiling size)"),
@@ -248,10 +253,159 @@ def dist_setup():
     return world, rank, local
 
 
+def sparse_matrix(w, seed):
+    """The CSR workload (host numpy arrays): rowptr int64, colind int32, values FP64."""
+    import synth
+    return synth.sparse_csr(seed, w["m"], w["n"], w["nnz_per_row"], rank=w["rank"], support=w["support"])
+
+
+def run_reference_sparse(args, w, world, rank):
+    """The oracle's CSR form timed on the host cores (reference arm of the sparse workload)."""
+    if rank != 0:
+        return 0
+    import oracle
+    rp, ci, va = sparse_matrix(w, 1000)
+    l = w["k"] + w["p"]
+    for _ in range(args.warmup):
+        oracle.pbpqlp_csr(rp, ci, va, (w["m"], w["n"]), l, w["q"], seed=7)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pbpqlp_csr(rp, ci, va, (w["m"], w["n"]), l, w["q"], seed=7)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
+                   "nnz": int(rp[-1]), "mode": w["mode"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "one full FP64 oracle factorization (CSR form) per step on the same workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sparse(args, w, world, rank, local):
+    """Sparse A: value = factorizations/s; roofline of the SpMM launches (FP64 ALU bound)."""
+    import numpy as np
+    import torch
+    import paper_2103_07245_gb300 as pq
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pq.load(build_if_missing=True)
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    l = k + p
+    rp, ci, va = sparse_matrix(w, 1000 + rank)
+    nnz = int(rp[-1])
+    d_rp, d_ci, d_va = (torch.from_numpy(x).to(dev) for x in (rp, ci, va))
+    stream = torch.cuda.current_stream(dev)
+    plan = pq.Plan(m, n, k, p, q, seed=7 + rank, mode=pq.PBPQLP_MODE_FP64, stream=stream, device=dev)
+    outs = plan.outputs(dev)
+    for _ in range(args.warmup):
+        plan.factor_csr(d_rp, d_ci, d_va, out=outs)
+    rc, flags = plan.sync_status()
+    if rc != pq.PBPQLP_OK:
+        raise RuntimeError("device status %d flags %d" % (rc, flags))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(vis) if vis.isdigit() else local)
+    pq.pbpqlp_set_timing(plan.handle, True)
+    pq.pbpqlp_read_timing(plan.handle)
+    l0 = pq.pbpqlp_kernel_launch_count()
+    dist_barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.factor_csr(d_rp, d_ci, d_va, out=outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist_barrier()
+    clocks = sampler.stop()
+    launches = pq.pbpqlp_kernel_launch_count() - l0
+    pass_ms, pass_n = pq.pbpqlp_read_timing(plan.handle)
+    pq.pbpqlp_set_timing(plan.handle, False)
+    rc, flags = plan.sync_status()
+    if rc != pq.PBPQLP_OK:
+        raise RuntimeError("device status %d flags %d" % (rc, flags))
+    ms = dist_max(e0.elapsed_time(e1) / args.steps, dev)
+    value = whole_job_rate(1, world, ms)
+    # end to end: the CSR arrays from pinned host memory every step, the factors back
+    h = [torch.from_numpy(x).pin_memory() for x in (rp, ci, va)]
+    ho = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+    h2d = sum(t.numel() * t.element_size() for t in h)
+    d2h = sum(t.numel() * t.element_size() for t in ho)
+    dist_barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for d, s_ in zip((d_rp, d_ci, d_va), h):
+            d.copy_(s_, non_blocking=True)
+        plan.factor_csr(d_rp, d_ci, d_va, out=outs)
+        for d, s_ in zip(ho, outs):
+            d.copy_(s_, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist_barrier()
+    e2e_ms = dist_max(e0.elapsed_time(e1) / args.steps, dev)
+    # roofline of the SpMM launches: 2 nnz l flop each, FP64 FMA issue rate
+    avg = pass_ms / max(pass_n, 1)
+    achieved = 2.0 * nnz * l / (avg * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q, "nnz": nnz, "mode": "FP64",
+                   "l2": "the n x l panel the SpMM gathers from (%d MB) fits L2; the CSR arrays (%d MB) do not"
+                         % (n * plan.l * 8 // 2 ** 20, (12 * nnz + 8 * m) // 2 ** 20),
+                   "parallelism": "single GPU" if world == 1 else "one factorization per GPU"},
+        "tflops_algorithmic": value * (2 * q + 2) * 2.0 * nnz * l / 1e12,
+        "roofline": {"kernel": "k_csr_spmm (CSR A times an l-column panel, FP64 FMA, warp per row)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz",
+                     "launches_timed": pass_n, "avg_launch_ms": avg},
+        "e2e": {"value": whole_job_rate(1, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.pbpqlp_csr(rp, ci, va, (m, n), l, q, seed=7)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "one full FP64 oracle factorization (CSR form) of the same matrix"}
+        Q, L, P = (t.cpu().numpy() for t in outs)
+        # parity at full size without a dense A: the rank-k difference to the
+        # oracle's factors through 16 Gaussian probes, E||D G||_F^2 / 16 = ||D||_F^2
+        import scipy.sparse
+        import scipy.sparse.linalg
+        G = np.random.default_rng(5).standard_normal((n, 16))
+        D = Q[:, :k] @ (L[:k, :k] @ (P[:, :k].T @ G)) - ref["Q"][:, :k] @ (ref["L"][:k, :k] @ (ref["P"][:, :k].T @ G))
+        S = scipy.sparse.csr_matrix((va, ci, rp), shape=(m, n))
+        S.sum_duplicates()
+        line["parity"] = {"rel_fro_diff_rank_k_probe_estimate": float(np.linalg.norm(D) / 4.0 /
+                                                                      scipy.sparse.linalg.norm(S)),
+                          "tol": 1e-11, "probes": 16}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, w, world, rank):
     """The FP64 CPU oracle timed on the host cores (reference arm)."""
     if rank != 0:
         return 0
+    if w.get("sparse"):
+        return run_reference_sparse(args, w, world, rank)
     import numpy as np
     import oracle
     import torch
@@ -492,6 +646,8 @@ def main():
         return run_reference(args, w, world, rank)
     if w.get("batched"):
         return run_batched(args, w, world, rank, local)
+    if w.get("sparse"):
+        return run_sparse(args, w, world, rank, local)
 
     import numpy as np
     import torch

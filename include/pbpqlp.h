@@ -195,11 +195,34 @@ int pbpqlp_rank_revealing(pbpqlp_plan_t plan, const double* L, double tol, doubl
                           void* workspace, size_t ws_bytes, double* norm2_est, int* rank_est);
 
 /*
+ * Sparse A (Section III-C: with z nonzeros the products with A and A^T cost
+ * O(z d) instead of O(m n d)).  Same factorization, outputs and status as
+ * pbpqlp_factor, for A (plan's m x n) in CSR form on the device (or in
+ * pinned host memory mapped at the same address):
+ *   rowptr[m + 1] (int64): rowptr[0] = 0, nondecreasing, rowptr[m] = nnz;
+ *   colind[nnz] (int32): 0 <= colind < n, any order within a row, repeated
+ *   (row, column) pairs add;  values[nnz] (FP64).
+ * A^T is built as a second CSR in the workspace on every call (its rows keep
+ * the order of A's entries), so both products are deterministic.  The
+ * structure is checked on the device before anything indexes through it: a
+ * violation makes pbpqlp_sync_status return PBPQLP_EINVAL (status bit 16)
+ * and the outputs hold no meaningful values.  The plan's mode must be
+ * PBPQLP_MODE_FP64 (PBPQLP_EUNSUPPORTED otherwise); workspace >=
+ * pbpqlp_csr_workspace_bytes(plan, nnz) bytes, 256-aligned (the plan's
+ * workspace plus 24 bytes per nonzero and 12 per column).
+ */
+size_t pbpqlp_csr_workspace_bytes(pbpqlp_plan_t plan, int64_t nnz);
+int pbpqlp_factor_csr(pbpqlp_plan_t plan, const int64_t* rowptr, const int32_t* colind, const double* values,
+                      int64_t nnz, void* workspace, size_t ws_bytes, const double* omega, double* Qa,
+                      double* L, double* Qb);
+
+/*
  * Wait for the plan's stream and return the latched device status of the
- * last pbpqlp_factor on this plan's workspace (PBPQLP_OK, _ENONFINITE,
- * _EBREAKDOWN or _ETIMEOUT), then clear it.  *flags_host (optional) gets the
- * raw status bits: 1 = a shifted Cholesky retry was used, 2 = breakdown after
- * all retries, 4 = non-finite value, 8 = timeout.
+ * last pbpqlp_factor (or pbpqlp_factor_csr) on this plan's workspace
+ * (PBPQLP_OK, _EINVAL for a bad CSR structure, _ENONFINITE, _EBREAKDOWN or
+ * _ETIMEOUT), then clear it.  *flags_host (optional) gets the raw status
+ * bits: 1 = a shifted Cholesky retry was used, 2 = breakdown after all
+ * retries, 4 = non-finite value, 8 = timeout, 16 = bad CSR structure.
  */
 int pbpqlp_sync_status(pbpqlp_plan_t plan, uint32_t* flags_host);
 

@@ -5,8 +5,9 @@ baseline may import this package.  The library's product path never loads it.
 It shares no code with the CUDA sources.
 
 The arithmetic lives in ``pbpqlp_oracle.c`` (plain C, FP64): Philox4x32-10 +
-Box-Muller Gaussians, plain GEMM loops, Householder QR with diag(R) >= 0, and
-Algorithm 3 of the paper executed step by step.  This module only marshals
+Box-Muller Gaussians, plain GEMM loops, a plain CSR product for sparse A
+(Section III-C), Householder QR with diag(R) >= 0, and Algorithm 3 of the
+paper executed step by step (dense or CSR A).  This module only marshals
 numpy arrays to it and adds the plain numpy formulas for the reconstruction
 and error of Eq. 8.  The learned-proposer MLP reference lives in
 ``oracle/mlp.py``.
@@ -40,6 +41,12 @@ def lib():
         L.orc_qr.restype = ctypes.c_int
         L.orc_pbpqlp.argtypes = [i64, i64, d, i64, i64, ctypes.c_int, d, d, d, d, d, d, d]
         L.orc_pbpqlp.restype = ctypes.c_int
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        L.orc_csr_mult.argtypes = [ctypes.c_int, i64, i64, pi64, pi32, d, i64, d, i64, d, i64]
+        L.orc_csr_mult.restype = None
+        L.orc_pbpqlp_csr.argtypes = [i64, i64, pi64, pi32, d, i64, ctypes.c_int, d, d, d, d, d, d, d]
+        L.orc_pbpqlp_csr.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -128,6 +135,48 @@ def pbpqlp(A, ell: int, q: int, phi=None, seed: int = None):
     if rc != 0:
         raise ValueError("orc_pbpqlp failed: need 1 <= ell <= min(m, n), q >= 0")
     return {"Q": Q, "L": L, "P": P, "R": R, "Pbar": Pbar, "D": D, "Phi": phi}
+
+
+def _csr_arrays(rowptr, colind, values):
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    va = _f64c(values)
+    assert ci.shape == va.shape and rp[-1] == ci.size
+    return rp, ci, va
+
+
+def csr_mult(rowptr, colind, values, shape, B, trans: bool = False) -> np.ndarray:
+    """A @ B (or A.T @ B) for A (shape m x n) in CSR form, with plain loops."""
+    m, n = shape
+    rp, ci, va = _csr_arrays(rowptr, colind, values)
+    B = _f64c(B)
+    N = B.shape[1]
+    assert B.shape[0] == (m if trans else n)
+    C = np.empty((n if trans else m, N), dtype=np.float64)
+    lib().orc_csr_mult(1 if trans else 0, m, n, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                       ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(va), N, _dp(B), N, _dp(C), N)
+    return C
+
+
+def pbpqlp_csr(rowptr, colind, values, shape, ell: int, q: int, phi=None, seed: int = None):
+    """Algorithm 3 for a sparse A (m x n) in CSR form; same outputs as ``pbpqlp``."""
+    m, n = shape
+    rp, ci, va = _csr_arrays(rowptr, colind, values)
+    if phi is None:
+        if seed is None:
+            raise ValueError("give phi or seed")
+        phi = gaussian(seed, (m, ell))
+    phi = _f64c(phi)
+    out = {k: np.empty(s) for k, s in (("Q", (m, ell)), ("L", (ell, ell)), ("P", (n, ell)), ("R", (ell, ell)),
+                                        ("Pbar", (n, ell)), ("D", (m, ell)))}
+    rc = lib().orc_pbpqlp_csr(m, n, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(va), ell, q, _dp(phi),
+                              _dp(out["Q"]), _dp(out["L"]), _dp(out["P"]), _dp(out["R"]), _dp(out["Pbar"]),
+                              _dp(out["D"]))
+    if rc != 0:
+        raise ValueError("orc_pbpqlp_csr failed: need 1 <= ell <= min(m, n), q >= 0")
+    out["Phi"] = phi
+    return out
 
 
 def reconstruct(Q, L, P, r: int) -> np.ndarray:

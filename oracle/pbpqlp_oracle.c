@@ -191,19 +191,62 @@ int orc_qr(int64_t rows, int64_t cols, const double* X, int64_t ldx,
 }
 
 /* ------------------------------------------------------------------ */
-/* Algorithm 3, step by step.                                          */
-/* In : A (m x n, lda, row-major), l = k + p (the paper's d), q >= 0,   */
+/* Plain sparse product.  A (m x n) in CSR form: the entries of row i    */
+/* are (colind[e], values[e]) for rowptr[i] <= e < rowptr[i+1];          */
+/* repeated (row, column) pairs add.  C = A B (m x N, B n x N) or        */
+/* C = A^T B (n x N, B m x N); B and C row-major (ldb, ldc).  Each       */
+/* entry of C sums its terms in ascending e.                            */
+/* ------------------------------------------------------------------ */
+void orc_csr_mult(int trans, int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                  const double* values, int64_t N, const double* B, int64_t ldb, double* C, int64_t ldc)
+{
+    const int64_t rowsC = trans ? n : m;
+    for (int64_t i = 0; i < rowsC; ++i)
+        for (int64_t j = 0; j < N; ++j) C[i * ldc + j] = 0.0;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int64_t c = colind[e];
+            const double a = values[e];
+            /* A: C[i] += a B[c];  A^T: C[c] += a B[i] */
+            const double* b = B + (trans ? i : c) * ldb;
+            double* o = C + (trans ? c : i) * ldc;
+            for (int64_t j = 0; j < N; ++j) o[j] += a * b[j];
+        }
+}
+
+/* The operand A of Algorithm 3: dense (lda) or CSR. */
+typedef struct {
+    int64_t m, n;
+    const double* A; int64_t lda;                                   /* dense */
+    const int64_t* rowptr; const int32_t* colind; const double* values; /* CSR   */
+} orc_amat;
+
+/* C (rows x l) = A B (trans = 0) or A^T B (trans = 1). */
+static void amat_mult(const orc_amat* a, int trans, int64_t l, const double* B, double* C)
+{
+    if (a->A) {
+        if (trans) orc_gemm(1, a->n, l, a->m, a->A, a->lda, B, l, C, l);
+        else orc_gemm(0, a->m, l, a->n, a->A, a->lda, B, l, C, l);
+    } else {
+        orc_csr_mult(trans, a->m, a->n, a->rowptr, a->colind, a->values, l, B, l, C, l);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3 (PbP-QLP with power iterations, Section III-B).          */
+/* In : A (m x n; dense or CSR), l = k + p (the paper's d), q >= 0,     */
 /*      Phi (m x l, row-major, contiguous).                             */
 /* Out: Q (m x l), L (l x l, lower), P (n x l); optional R (l x l, the  */
 /*      first-stage factor of Eq. 6), Pbar (n x l, final basis before   */
 /*      the projection), D (m x l, Eq. 5).  All contiguous row-major.   */
 /* Returns 0, or -1 on bad sizes / allocation failure.                  */
 /* ------------------------------------------------------------------ */
-int orc_pbpqlp(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, int q,
-               const double* Phi, double* Q, double* L, double* P,
-               double* R_out, double* Pbar_out, double* D_out)
+static int pbpqlp_steps(const orc_amat* a, int64_t l, int q,
+                        const double* Phi, double* Q, double* L, double* P,
+                        double* R_out, double* Pbar_out, double* D_out)
 {
-    if (l < 1 || l > m || l > n || q < 0 || lda < n) return -1;
+    const int64_t m = a->m, n = a->n;
+    if (l < 1 || l > m || l > n || q < 0) return -1;
     int rc = 0;
     double* Cn = (double*)malloc(sizeof(double) * (size_t)n * (size_t)l);  /* n x l panel */
     double* Cm = (double*)malloc(sizeof(double) * (size_t)m * (size_t)l);  /* m x l panel */
@@ -216,17 +259,17 @@ int orc_pbpqlp(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, in
     if (!Cn || !Cm || !Pb || !Pm || !R || !RT || !Pt || !Rt) { rc = -1; goto done; }
 
     /* C = A^T Phi (Eq. 3), Pbar = orth(C) (Eq. 4) */
-    orc_gemm(1, n, l, m, A, lda, Phi, l, Cn, l);
+    amat_mult(a, 1, l, Phi, Cn);
     if (orc_qr(n, l, Cn, l, Pb, l, NULL)) { rc = -1; goto done; }
     /* power iterations, an orth after every product (Section III-B) */
     for (int it = 0; it < q; ++it) {
-        orc_gemm(0, m, l, n, A, lda, Pb, l, Cm, l);                 /* C = A Pbar   */
+        amat_mult(a, 0, l, Pb, Cm);                                 /* C = A Pbar   */
         if (orc_qr(m, l, Cm, l, Pm, l, NULL)) { rc = -1; goto done; }
-        orc_gemm(1, n, l, m, A, lda, Pm, l, Cn, l);                 /* C = A^T Pbar */
+        amat_mult(a, 1, l, Pm, Cn);                                 /* C = A^T Pbar */
         if (orc_qr(n, l, Cn, l, Pb, l, NULL)) { rc = -1; goto done; }
     }
     /* D = A Pbar (Eq. 5), [Q, R] = qr(D) (Eq. 6) */
-    orc_gemm(0, m, l, n, A, lda, Pb, l, Cm, l);
+    amat_mult(a, 0, l, Pb, Cm);
     if (D_out) memcpy(D_out, Cm, sizeof(double) * (size_t)m * (size_t)l);
     if (orc_qr(m, l, Cm, l, Q, l, R)) { rc = -1; goto done; }
     /* [Ptil, Rtil] = qr(R^T) (Eq. 7); L = Rtil^T, P = Pbar Ptil (Eq. 8) */
@@ -241,6 +284,25 @@ int orc_pbpqlp(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, in
 done:
     free(Cn); free(Cm); free(Pb); free(Pm); free(R); free(RT); free(Pt); free(Rt);
     return rc;
+}
+
+/* Dense A (m x n, lda, row-major). */
+int orc_pbpqlp(int64_t m, int64_t n, const double* A, int64_t lda, int64_t l, int q,
+               const double* Phi, double* Q, double* L, double* P,
+               double* R_out, double* Pbar_out, double* D_out)
+{
+    if (lda < n) return -1;
+    orc_amat a = {m, n, A, lda, NULL, NULL, NULL};
+    return pbpqlp_steps(&a, l, q, Phi, Q, L, P, R_out, Pbar_out, D_out);
+}
+
+/* Sparse A (Section III-C): CSR as in orc_csr_mult. */
+int orc_pbpqlp_csr(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* values,
+                   int64_t l, int q, const double* Phi, double* Q, double* L, double* P,
+                   double* R_out, double* Pbar_out, double* D_out)
+{
+    orc_amat a = {m, n, NULL, 0, rowptr, colind, values};
+    return pbpqlp_steps(&a, l, q, Phi, Q, L, P, R_out, Pbar_out, D_out);
 }
 
 /* Number of OpenMP threads a parallel region here uses (1 without OpenMP). */

@@ -77,6 +77,10 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_generate_omega.restype = ci
     L.pbpqlp_factor.argtypes = [vp, vp, i64, ci, vp, sz, vp, vp, vp, vp]
     L.pbpqlp_factor.restype = ci
+    L.pbpqlp_csr_workspace_bytes.argtypes = [vp, i64]
+    L.pbpqlp_csr_workspace_bytes.restype = sz
+    L.pbpqlp_factor_csr.argtypes = [vp, vp, vp, vp, i64, vp, sz, vp, vp, vp, vp]
+    L.pbpqlp_factor_csr.restype = ci
     L.pbpqlp_sketch.argtypes = [vp, vp, i64, ci, ci, vp, i64, ci, vp, i64, vp, sz]
     L.pbpqlp_sketch.restype = ci
     L.pbpqlp_reconstruct.argtypes = [vp, vp, vp, vp, ci, vp, i64, vp, sz]
@@ -194,6 +198,15 @@ def pbpqlp_generate_omega(plan, omega):
 def pbpqlp_factor(plan, A, lda, a_dtype, workspace, ws_bytes, omega, Qa, L, Qb):
     _check(load().pbpqlp_factor(plan, _ptr(A), int(lda), int(a_dtype), _ptr(workspace), int(ws_bytes),
                                 _ptr(omega), _ptr(Qa), _ptr(L), _ptr(Qb)), "pbpqlp_factor")
+
+
+def pbpqlp_csr_workspace_bytes(plan, nnz) -> int:
+    return int(load().pbpqlp_csr_workspace_bytes(plan, int(nnz)))
+
+
+def pbpqlp_factor_csr(plan, rowptr, colind, values, nnz, workspace, ws_bytes, omega, Qa, L, Qb):
+    _check(load().pbpqlp_factor_csr(plan, _ptr(rowptr), _ptr(colind), _ptr(values), int(nnz), _ptr(workspace),
+                                    int(ws_bytes), _ptr(omega), _ptr(Qa), _ptr(L), _ptr(Qb)), "pbpqlp_factor_csr")
 
 
 def pbpqlp_sketch(plan, A, lda, a_dtype, trans, Y, ldy, ncols, C, ldc, workspace, ws_bytes):
@@ -386,6 +399,18 @@ class Plan:
         # outputs live on the plan's device even when A is pinned host memory
         Qa, L, Qb = out if out is not None else self.outputs(self.workspace.device)
         pbpqlp_factor(self.handle, A, A.stride(0), a_dtype, self.workspace, self.ws_bytes, omega, Qa, L, Qb)
+        return Qa, L, Qb
+
+    def factor_csr(self, rowptr, colind, values, omega=None, out=None):
+        """Sparse A in CSR form (rowptr int64 [m+1], colind int32 [nnz], values FP64 [nnz], on the device)."""
+        import torch
+        nnz = int(colind.numel())
+        need = pbpqlp_csr_workspace_bytes(self.handle, nnz)
+        if getattr(self, "_csr_ws", None) is None or self._csr_ws.numel() < need:
+            self._csr_ws = torch.empty(need, dtype=torch.uint8, device=self.workspace.device)
+        Qa, L, Qb = out if out is not None else self.outputs(self.workspace.device)
+        pbpqlp_factor_csr(self.handle, rowptr, colind if nnz else None, values if nnz else None, nnz, self._csr_ws,
+                          self._csr_ws.numel(), omega, Qa, L, Qb)
         return Qa, L, Qb
 
     def omega(self, device="cuda"):

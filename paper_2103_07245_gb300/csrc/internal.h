@@ -15,6 +15,7 @@ constexpr uint32_t kStShifted = 1u;    // a shifted Cholesky retry was used
 constexpr uint32_t kStBreakdown = 2u;  // Cholesky failed even with the shift
 constexpr uint32_t kStNonFinite = 4u;  // NaN/Inf met
 constexpr uint32_t kStTimeout = 8u;    // bounded wait gave up
+constexpr uint32_t kStBadInput = 16u;  // a sparse A's CSR structure failed the device check
 
 // Process-wide launch counter (incremented by every launcher below).
 void count_launches(int64_t n);
@@ -30,6 +31,28 @@ cudaError_t debug_report(cudaError_t e, const char* what, const char* file, int 
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t packed_tri(int l) { return (int64_t)l * (l + 1) / 2; }
+
+// ---- Sparse A (kernels_sparse.cu) ---------------------------------------
+// A CSR matrix on the device: ptr[rows + 1], idx[nnz], val[nnz].
+struct CsrT {
+    const int64_t* ptr = nullptr;
+    const int32_t* idx = nullptr;
+    const double* val = nullptr;
+};
+// Scratch bytes of launch_csr_transpose for an A with n columns and nnz entries.
+size_t csr_transpose_bytes(int64_t n, int64_t nnz);
+// Checks A's CSR structure (kStBadInput in *status on a violation) and builds
+// A^T as a CSR in `scratch` (*out points into it), each row of A^T in
+// ascending position of A's CSR.  After a violation no kernel reads through
+// the structure.
+cudaError_t launch_csr_transpose(int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+                                 const double* values, void* scratch, CsrT* out, uint32_t* status, int num_sms,
+                                 cudaStream_t s);
+// C (rows x l, ldc) = S X for a CSR S with `rows` rows and X row-major (ldx);
+// zeros after a structure violation (kStBadInput in *status).
+cudaError_t launch_csr_spmm(int64_t rows, const int64_t* ptr, const int32_t* idx, const double* val, const double* X,
+                            int64_t ldx, int l, double* C, int64_t ldc, const uint32_t* status, int num_sms,
+                            cudaStream_t s);
 
 // ---- FP64 kernels (kernels_fp64.cu) -------------------------------------
 // Phi[i*ld + j] = sample (i*l + j) of the Philox4x32-10 / Box-Muller stream.

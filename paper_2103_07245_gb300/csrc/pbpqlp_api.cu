@@ -2,7 +2,9 @@
 // Chen).  The plan holds sizes, split-K choices and the workspace layout; all
 // device memory comes from the caller.  Every step of the factorization runs
 // in this library's kernels on the plan's stream.
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -482,32 +484,19 @@ int pbpqlp_generate_omega(pbpqlp_plan_t P, double* omega) {
     return cuda_err(launch_gaussian(P->seed, P->m, P->l, omega, P->l, P->stream));
 }
 
-int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
-                  const double* omega, double* Qa, double* L, double* Qb) {
-    if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
-    const bool mixed = P->nprod > 0;
-    if ((mixed || P->emu) ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64)
-        return PBPQLP_EUNSUPPORTED;
-    int rc = check_ws(P, workspace, ws_bytes);
-    if (rc) return rc;
-    if ((rc = check_device_addressable(Av))) return rc;
-    P->last_ws = workspace;
-    const Ws w = carve(P, workspace);
+}  // extern "C"
+
+namespace {
+
+// Algorithm 3 on the plan's workspace, with `product(transA, Y, C)` forming
+// C = A Y (transA false, m rows) or C = A^T Y (n rows) for the plan's A.
+template <class Product>
+int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* omega, double* Qa, double* L,
+               double* Qb) {
     cudaStream_t s = P->stream;
-    const double* A = (const double*)Av;
     const int64_t m = P->m, n = P->n, ldp = P->ldp;
     const int l = P->l;
-    PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
-    if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
-    if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
-    if (P->emu && (rc = emu_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
-    // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
-    auto product = [&](bool transA, const double* Y, double* C) -> int {
-        if (mixed) return tc_pass(P, w, transA, Y, ldp, l, C, ldp, true);
-        if (P->emu) return emu_pass(P, w, transA, Y, ldp, l, C, ldp, true);
-        return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
-                      : gemm_pass(P, w, false, m, n, A, lda, Y, ldp, C, ldp, l, P->S_nn, P->kc_nn, true);
-    };
+    int rc = PBPQLP_OK;
     // Phi (m x l)
     if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
     else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
@@ -551,6 +540,78 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
     }
     PBQ_TRY(copy2d(w.Xm, ldp, Qa, l, m, l, s));
     return PBPQLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
+                  const double* omega, double* Qa, double* L, double* Qb) {
+    if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
+    const bool mixed = P->nprod > 0;
+    if ((mixed || P->emu) ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64)
+        return PBPQLP_EUNSUPPORTED;
+    int rc = check_ws(P, workspace, ws_bytes);
+    if (rc) return rc;
+    if ((rc = check_device_addressable(Av))) return rc;
+    P->last_ws = workspace;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    const double* A = (const double*)Av;
+    const int64_t m = P->m, n = P->n, ldp = P->ldp;
+    const int l = P->l;
+    PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
+    if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
+    if (P->emu && (rc = emu_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
+    // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
+    auto product = [&](bool transA, const double* Y, double* C) -> int {
+        if (mixed) return tc_pass(P, w, transA, Y, ldp, l, C, ldp, true);
+        if (P->emu) return emu_pass(P, w, transA, Y, ldp, l, C, ldp, true);
+        return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
+                      : gemm_pass(P, w, false, m, n, A, lda, Y, ldp, C, ldp, l, P->S_nn, P->kc_nn, true);
+    };
+    return run_factor(P, w, product, omega, Qa, L, Qb);
+}
+
+size_t pbpqlp_csr_workspace_bytes(pbpqlp_plan_t P, int64_t nnz) {
+    if (!P || nnz < 0) return 0;
+    return (P->total + 255) / 256 * 256 + csr_transpose_bytes(P->n, nnz);
+}
+
+int pbpqlp_factor_csr(pbpqlp_plan_t P, const int64_t* rowptr, const int32_t* colind, const double* values,
+                      int64_t nnz, void* workspace, size_t ws_bytes, const double* omega, double* Qa, double* L,
+                      double* Qb) {
+    if (!P || !rowptr || !Qa || !L || !Qb || nnz < 0 || (nnz > 0 && (!colind || !values))) return PBPQLP_EINVAL;
+    if (P->n > INT32_MAX) return PBPQLP_EUNSUPPORTED;   // column indices are int32
+    if (P->nprod > 0 || P->emu) return PBPQLP_EUNSUPPORTED;   // sparse products run in FP64
+    if (!workspace || ((uintptr_t)workspace & 255u) || ws_bytes < pbpqlp_csr_workspace_bytes(P, nnz))
+        return PBPQLP_EWORKSPACE;
+    int rc = check_device_addressable(rowptr);
+    if (!rc && nnz > 0) rc = check_device_addressable(colind);
+    if (!rc && nnz > 0) rc = check_device_addressable(values);
+    if (rc) return rc;
+    P->last_ws = workspace;
+    const Ws w = carve(P, workspace);
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n, ldp = P->ldp;
+    const int l = P->l;
+    PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
+    if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
+    // A^T as a CSR (checks the structure first), once per call
+    CsrT at;
+    void* scratch = (char*)workspace + (P->total + 255) / 256 * 256;
+    PBQ_TRY(launch_csr_transpose(m, n, nnz, rowptr, colind, values, scratch, &at, w.status, P->num_sms, s));
+    auto product = [&](bool transA, const double* Y, double* C) -> int {
+        const auto ev = next_events(P);
+        if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+        if (transA) PBQ_TRY(launch_csr_spmm(n, at.ptr, at.idx, at.val, Y, ldp, l, C, ldp, w.status, P->num_sms, s));
+        else PBQ_TRY(launch_csr_spmm(m, rowptr, colind, values, Y, ldp, l, C, ldp, w.status, P->num_sms, s));
+        if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
+        return PBPQLP_OK;
+    };
+    return run_factor(P, w, product, omega, Qa, L, Qb);
 }
 
 int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int trans, const double* Y, int64_t ldy,
@@ -605,6 +666,7 @@ int pbpqlp_sync_status(pbpqlp_plan_t P, uint32_t* flags_host) {
             return PBPQLP_ECUDA;
     }
     if (flags_host) *flags_host = st;
+    if (st & kStBadInput) return PBPQLP_EINVAL;
     if (st & kStNonFinite) return PBPQLP_ENONFINITE;
     if (st & kStTimeout) return PBPQLP_ETIMEOUT;
     if (st & kStBreakdown) return PBPQLP_EBREAKDOWN;

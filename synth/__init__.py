@@ -90,6 +90,67 @@ def xyt_plus_noise(seed: int, m: int, n: int, r: int, eps: float, dtype=np.float
     return (X @ Y.T + dtype(eps) * E).astype(dtype)
 
 
+def sparse_csr(seed: int, m: int, n: int, nnz_per_row: float, *, rank: int = 0, support: int = 0,
+               decay: float = 20.0, dup_frac: float = 0.0, shuffle: bool = False, empty_rows: int = 0,
+               empty_cols: int = 0):
+    """Seeded sparse m x n matrix in CSR form: (rowptr int64, colind int32, values FP64).
+
+    Noise part: about ``nnz_per_row`` N(0,1) entries per row at uniform
+    columns.  Optional low-rank part: ``rank`` terms s_i u_i v_i^T with
+    s_i = exp(-i / decay) * sqrt(m n) and u_i, v_i unit vectors supported on
+    ``support`` random rows / columns.  ``dup_frac`` of the entries are split
+    into two repeated (row, column) pairs that add up to the value;
+    ``shuffle`` permutes the entries within each row; the first
+    ``empty_rows`` rows and the last ``empty_cols`` columns hold nothing.
+    """
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    live_r = np.arange(empty_rows, m)
+    ncols_live = n - empty_cols
+    cnt = rng.poisson(nnz_per_row, size=live_r.size)
+    rows.append(np.repeat(live_r, cnt))
+    cols.append(rng.integers(0, ncols_live, size=int(cnt.sum())))
+    vals.append(rng.standard_normal(int(cnt.sum())))
+    for i in range(rank):
+        su = min(support, live_r.size)
+        sv = min(support, ncols_live)
+        ri = rng.choice(live_r, size=su, replace=False)
+        cj = rng.choice(ncols_live, size=sv, replace=False)
+        u = rng.standard_normal(su)
+        v = rng.standard_normal(sv)
+        u /= np.linalg.norm(u)
+        v /= np.linalg.norm(v)
+        s_i = math.exp(-i / decay) * math.sqrt(m * n)
+        rows.append(np.repeat(ri, sv))
+        cols.append(np.tile(cj, su))
+        vals.append((s_i * np.outer(u, v)).ravel())
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals)
+    if dup_frac > 0 and r.size:
+        pick = rng.random(r.size) < dup_frac
+        part = rng.random(int(pick.sum()))
+        base = v.copy()
+        base[pick] *= 1.0 - part          # the two copies add up to the value
+        r = np.concatenate([r, r[pick]])
+        c = np.concatenate([c, c[pick]])
+        v = np.concatenate([base, v[pick] * part])
+    order = np.lexsort((rng.random(r.size) if shuffle else c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, c.astype(np.int32), v.astype(np.float64)
+
+
+def csr_to_dense(rowptr, colind, values, m: int, n: int) -> np.ndarray:
+    """Dense FP64 copy of a CSR matrix (repeated pairs add)."""
+    A = np.zeros((m, n))
+    r = np.repeat(np.arange(m), np.diff(rowptr))
+    np.add.at(A, (r, colind.astype(np.int64)), values)
+    return A
+
+
 def batched_shapes(seed: int, count: int = 512, m_range=(256, 4096), n_lo: int = 128,
                    n_hi: int = 2048, k_range=(8, 64), alpha_range=(1.0, 3.0)):
     """Shapes and spectra of the uneven batch: m ~ U[256,4096],
