@@ -110,16 +110,24 @@ __global__ void k_csr_order_cols(int64_t n, const int64_t* __restrict__ colptr, 
 }
 
 // C (rows x l, ld ldc) = S X for a CSR S (ptr, idx, val) and a row-major X
-// (ld ldx): one warp per row, lanes over the l columns (T chunks of 32).  A
+// (ld ldx): one warp per row, lanes over the l columns in T chunks of 32.  A
 // row's nonzeros are taken 32 at a time (one coalesced load per lane, then
-// broadcast by shuffles) and every output sums them in CSR order.
-template <int T>
+// broadcast by shuffles).  The last chunk holds only r = l - 32 (T - 1)
+// columns; with P = 2 (r <= 16) or 4 (r <= 8) it serves P nonzeros per
+// instruction, lane group g = lane / (32 / P) taking the nonzeros j = g mod P
+// (GB300 has 2 FP64 lanes per SM per clock, and a masked lane costs the same
+// as a busy one).  Every output sums in CSR order, except that the last
+// chunk's P interleaved partial sums are added at the end: deterministic.
+template <int T, int P>
 __global__ void __launch_bounds__(256)
 k_csr_spmm(int64_t rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
            const double* __restrict__ val, const double* __restrict__ X, int64_t ldx, int l, double* __restrict__ C,
            int64_t ldc, const uint32_t* __restrict__ status) {
+    constexpr int GW = 32 / P;   // lanes per nonzero in the last chunk
     const bool bad = bad_input(status);
     const int lane = threadIdx.x & 31;
+    const int grp = lane / GW, glane = lane % GW;
+    const int lastcol = 32 * (T - 1) + (P == 1 ? lane : glane);
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < rows; r += nw) {
@@ -137,24 +145,32 @@ k_csr_spmm(int64_t rows, const int64_t* __restrict__ ptr, const int32_t* __restr
                     vl = val[e];
                 }
                 const int cntj = e1 - e0 < 32 ? (int)(e1 - e0) : 32;
-                for (int j = 0; j < cntj; ++j) {
-                    const int32_t cj = __shfl_sync(0xffffffffu, cl, j);
-                    const double vj = __shfl_sync(0xffffffffu, vl, j);
-                    const double* xr = X + (int64_t)cj * ldx;
+                for (int j = 0; j < cntj; j += P) {
 #pragma unroll
-                    for (int t = 0; t < T; ++t) {
-                        const int col = lane + 32 * t;
-                        if (col < l) acc[t] = fma(vj, xr[col], acc[t]);
+                    for (int u = 0; u < P; ++u) {   // full chunks: one nonzero at a time
+                        if (T > 1 && j + u < cntj) {
+                            const int32_t cj = __shfl_sync(0xffffffffu, cl, j + u);
+                            const double vj = __shfl_sync(0xffffffffu, vl, j + u);
+                            const double* xr = X + (int64_t)cj * ldx;
+#pragma unroll
+                            for (int t = 0; t < T - 1; ++t) acc[t] = fma(vj, xr[lane + 32 * t], acc[t]);
+                        }
                     }
+                    // last chunk: nonzero j + grp for this lane group
+                    const int jj = j + grp;
+                    const int32_t cj = __shfl_sync(0xffffffffu, cl, jj & 31);
+                    const double vj = __shfl_sync(0xffffffffu, vl, jj & 31);
+                    if (jj < cntj && lastcol < l) acc[T - 1] = fma(vj, X[(int64_t)cj * ldx + lastcol], acc[T - 1]);
                 }
             }
+            // add the last chunk's interleaved partial sums (group 0 keeps the total)
+#pragma unroll
+            for (int off = GW; off < 32; off <<= 1) acc[T - 1] += __shfl_xor_sync(0xffffffffu, acc[T - 1], off);
         }
         double* cr = C + r * ldc;
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int col = lane + 32 * t;
-            if (col < l) cr[col] = acc[t];
-        }
+        for (int t = 0; t < T - 1; ++t) cr[lane + 32 * t] = acc[t];
+        if (grp == 0 && lastcol < l) cr[lastcol] = acc[T - 1];
     }
 }
 
@@ -209,9 +225,14 @@ cudaError_t launch_csr_spmm(int64_t rows, const int64_t* ptr, const int32_t* idx
                             cudaStream_t s) {
     if (l < 1 || l > kMaxEll) return cudaErrorInvalidValue;
     const unsigned grid = grid_for(rows * 32, 256, num_sms);
-    switch ((l + 31) / 32) {
-#define PBQ_S(TT) case TT: k_csr_spmm<TT><<<grid, 256, 0, s>>>(rows, ptr, idx, val, X, ldx, l, C, ldc, status); break;
-        PBQ_S(1) PBQ_S(2) PBQ_S(3) PBQ_S(4) PBQ_S(5) PBQ_S(6) PBQ_S(7)
+    const int T = (l + 31) / 32, rem = l - 32 * (T - 1);
+    const int P = rem <= 8 ? 4 : (rem <= 16 ? 2 : 1);
+    switch (T * 8 + P) {
+#define PBQ_S(TT, PP) case TT * 8 + PP: \
+        k_csr_spmm<TT, PP><<<grid, 256, 0, s>>>(rows, ptr, idx, val, X, ldx, l, C, ldc, status); break;
+        PBQ_S(1, 1) PBQ_S(1, 2) PBQ_S(1, 4) PBQ_S(2, 1) PBQ_S(2, 2) PBQ_S(2, 4) PBQ_S(3, 1) PBQ_S(3, 2) PBQ_S(3, 4)
+        PBQ_S(4, 1) PBQ_S(4, 2) PBQ_S(4, 4) PBQ_S(5, 1) PBQ_S(5, 2) PBQ_S(5, 4) PBQ_S(6, 1) PBQ_S(6, 2) PBQ_S(6, 4)
+        PBQ_S(7, 1) PBQ_S(7, 2) PBQ_S(7, 4)
 #undef PBQ_S
         default: return cudaErrorInvalidValue;
     }

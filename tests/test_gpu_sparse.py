@@ -32,13 +32,16 @@ def _factor_csr(pq, plan, rp, ci, va):
     return rc, flags, [t.cpu().numpy() for t in out]
 
 
+# l chosen so that the SpMM's last 32-column chunk takes 1, 2 or 4 nonzeros per instruction
 @pytest.mark.parametrize("m,n,k,p,q,kw", [
-    (1000, 1000, 20, 5, 1, dict(nnz_per_row=8.0, rank=30, support=120)),
-    (700, 333, 15, 4, 2, dict(nnz_per_row=3.0, rank=20, support=60, dup_frac=0.2, shuffle=True, empty_rows=17,
-                              empty_cols=9)),
-    (300, 1100, 40, 10, 1, dict(nnz_per_row=25.0, rank=60, support=80)),
-    (2500, 1800, 100, 20, 2, dict(nnz_per_row=12.0, rank=150, support=200)),   # l = 120
-    (260, 240, 200, 24, 0, dict(nnz_per_row=40.0)),                             # l = 224, q = 0
+    (1000, 1000, 20, 5, 1, dict(nnz_per_row=8.0, rank=30, support=120)),          # l = 25: one chunk
+    (700, 333, 8, 4, 2, dict(nnz_per_row=3.0, rank=20, support=60, dup_frac=0.2, shuffle=True, empty_rows=17,
+                             empty_cols=9)),                                      # l = 12: 2 per chunk
+    (500, 400, 3, 3, 1, dict(nnz_per_row=5.0, rank=6, support=50)),               # l = 6: 4 per chunk
+    (300, 1100, 32, 8, 1, dict(nnz_per_row=25.0, rank=60, support=80)),           # l = 40: 1 + 8 columns
+    (2500, 1800, 100, 10, 2, dict(nnz_per_row=12.0, rank=150, support=200)),      # l = 110: 3 + 14 columns
+    (1200, 900, 100, 20, 1, dict(nnz_per_row=9.0, rank=130, support=120)),        # l = 120: 3 + 24 columns
+    (260, 240, 200, 24, 0, dict(nnz_per_row=40.0)),                               # l = 224, q = 0
 ])
 def test_csr_parity_with_oracle(pq, m, n, k, p, q, kw):
     rp, ci, va = synth.sparse_csr(100 + m, m, n, **kw)
