@@ -45,7 +45,7 @@ enum {
     PBPQLP_ENONFINITE = 4,   /* NaN/Inf met in A or in an intermediate panel */
     PBPQLP_EBREAKDOWN = 5,   /* orthonormalisation failed even after the shifted retries */
     PBPQLP_ETIMEOUT = 6,     /* a bounded device wait gave up */
-    PBPQLP_EUNSUPPORTED = 7, /* mode / size not supported by this build */
+    PBPQLP_EUNSUPPORTED = 7, /* mode / size combination the library does not support */
     PBPQLP_EWORKSPACE = 8    /* workspace missing or smaller than pbpqlp_workspace_bytes() */
 };
 
