@@ -23,10 +23,13 @@ _lib = None
 
 
 def lib():
-    """Load (building first if needed) the oracle shared library."""
+    """Load (building first if needed) the oracle shared library.
+
+    PBPQLP_ORACLE_LIB names another build of the same source to load instead
+    (the mutation tests load copies with a planted mistake this way)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("PBPQLP_ORACLE_LIB") or _build.build()
         L = ctypes.CDLL(path)
         d = ctypes.POINTER(ctypes.c_double)
         i64 = ctypes.c_int64
