@@ -76,6 +76,7 @@ struct pbpqlp_batch_s {
     int trsm_rows = 64;             // rows per triangular-solve unit (tuned)
     int tc_sorted = 1;              // grouped products: longest contraction first (tuned)
     bool oz = false;                // Grams and R = Q^T D as digit products (PBPQLP_NO_OZ_GRAM=1: FP64 FMA)
+    bool fault_producer = false;    // PBPQLP_FAULT=batch_producer at plan creation (failure-detection test)
     bool timing = false;            // event pairs around each grouped product kernel
     std::vector<cudaEvent_t> ev;    // 2 per timed launch
     int ev_used = 0;
@@ -440,6 +441,9 @@ int build_lists(pbpqlp_batch_s* B, const Ptrs& pt) {
     auto Yn = [&](int i) { return P64(pt, B->mw[i].Yn); };
 
     lb.join();
+    // failure-detection hook: the host producer gives up half-way through the
+    // launch sequence, as a failing host call would; nothing has been launched
+    if (B->fault_producer) return PBPQLP_ECUDA;
     product(true, Xm, Xn);                  // C = A^T Phi (Eq. 3)
     orth(1, Xn, Xn, Yn);                    // Pbar = orth(C) (Eq. 4)
     for (int it = 0; it < B->q; ++it) {     // power iterations (Section III-B)
@@ -688,6 +692,8 @@ int run(pbpqlp_batch_s* B, const Ptrs& pt, size_t ws_bytes) {
         if (rc) return rc;
         B->key = key;
     }
+    // from here on this workspace holds the batch's status words
+    B->last_ws = pt.ws;
     // the lists live in the caller's workspace: refresh them on every call
     // (a pageable-memory copy is staged before the call returns)
     PBQ_TRY(cudaMemcpyAsync(pt.ws + B->off_lists, B->host_lists.data(), B->host_lists.size(),
@@ -775,6 +781,8 @@ int pbpqlp_plan_batched(pbpqlp_batch_t* out, int count, const int64_t* m, const 
     if (env && env[0] == '1') B->use_graph = false;
     const char* no = std::getenv("PBPQLP_NO_OZ_GRAM");
     B->oz = !(no && no[0] == '1');
+    const char* fault = std::getenv("PBPQLP_FAULT");
+    B->fault_producer = fault && std::strcmp(fault, "batch_producer") == 0;
     layout(B);
     *out = B;
     return PBPQLP_OK;
@@ -800,7 +808,6 @@ int pbpqlp_factor_batched(pbpqlp_batch_t B, const void* const* A, const int64_t*
         if (at.type == cudaMemoryTypeUnregistered || (at.type == cudaMemoryTypeHost && at.devicePointer != A[i]))
             return PBPQLP_EINVAL;
     }
-    B->last_ws = workspace;
     if (B->a_f32 != (a_dtype == PBPQLP_F32)) { B->a_f32 = a_dtype == PBPQLP_F32; B->key.clear(); }
     Ptrs pt{(char*)workspace, A, lda, Qa, L, Qb};
     return run(B, pt, ws_bytes);

@@ -197,3 +197,32 @@ def test_batched_digit_grams_match_fma_grams(pq, monkeypatch, mode):
             e_gpu, e_orc = _errors(A, out[0][i], ref, s["k"])
             assert e_gpu <= 1.1 * e_orc, (i, s, e_gpu, e_orc)
             assert np.linalg.norm(a1 - a2) <= 1e-2 * e_orc * np.linalg.norm(A), (i, s)
+
+
+def test_batched_host_producer_fault_is_reported_without_launches(pq, monkeypatch):
+    """Failure detection on the host: with PBPQLP_FAULT=batch_producer (read
+    at plan creation) the work-list producer gives up half-way, the call
+    returns an error having launched nothing, and a plan without the hook
+    factors the same batch cleanly."""
+    import torch
+    shapes, mats = _batch(8, 3)
+    args = ([s["m"] for s in shapes], [s["n"] for s in shapes], [s["k"] for s in shapes], 8, 1, 4)
+    monkeypatch.setenv("PBPQLP_FAULT", "batch_producer")
+    Bf = pq.Batch(*args)
+    monkeypatch.delenv("PBPQLP_FAULT")
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    torch.cuda.synchronize()
+    n0 = pq.pbpqlp_kernel_launch_count()
+    with pytest.raises(pq.PbpqlpError) as ei:
+        Bf.factor(As)
+    assert ei.value.status == pq.PBPQLP_ECUDA
+    assert pq.pbpqlp_kernel_launch_count() == n0
+    B = pq.Batch(*args)
+    Qa, L, Qb = B.factor(As)
+    rc, flags = B.sync_status()
+    assert rc == pq.PBPQLP_OK, flags
+    for i, (s, A) in enumerate(zip(shapes, mats)):
+        ref = oracle.pbpqlp(A, s["k"] + 8, 1, seed=4 + i)
+        g = [Qa[i].cpu().numpy(), L[i].cpu().numpy(), Qb[i].cpu().numpy()]
+        d = np.linalg.norm(oracle.reconstruct(*g, s["k"]) - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], s["k"]))
+        assert d / np.linalg.norm(A) <= TOL
