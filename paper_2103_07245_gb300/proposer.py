@@ -201,15 +201,64 @@ def make_matrices(seed, count, m_range=(512, 2048), k_range=(8, 64), fixed=None,
     return As, ks, tails
 
 
-def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0):
-    """Minibatch AdamW on the labelled features; returns the loss history."""
+def labelled_chunks(chunks, make_chunk, shard_dir=None):
+    """Features and labels of `chunks` chunks, make_chunk(c) -> (F, yq, yp).
+
+    With shard_dir, chunk c is kept in shard_dir/chunk_<c>.npz once made and
+    read back instead of being made again, so an interrupted label run
+    resumes where it stopped (a shard is written whole through a temporary
+    file, never half).  Returns lists of numpy arrays."""
+    F_all, yq_all, yp_all = [], [], []
+    for c in range(chunks):
+        path = os.path.join(shard_dir, "chunk_%05d.npz" % c) if shard_dir else None
+        if path and os.path.exists(path):
+            d = np.load(path)
+            F, yq, yp = d["F"], d["yq"], d["yp"]
+        else:
+            F, yq, yp = make_chunk(c)
+            F = F.cpu().numpy() if hasattr(F, "cpu") else np.asarray(F)
+            yq, yp = np.asarray(yq), np.asarray(yp)
+            if path:
+                os.makedirs(shard_dir, exist_ok=True)
+                tmp = path + ".tmp.npz"
+                np.savez(tmp, F=F, yq=yq, yp=yp)
+                os.replace(tmp, path)
+        F_all.append(F)
+        yq_all.append(yq)
+        yp_all.append(yp)
+    return F_all, yq_all, yp_all
+
+
+def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0, ckpt=None, ckpt_every=0):
+    """Minibatch AdamW on the labelled features; returns the loss history.
+
+    With ckpt (a path) the weights, AdamW state, epoch and loss history are
+    saved every ckpt_every epochs and at the end; a run started with an
+    existing checkpoint continues from it and reaches exactly the weights of
+    an uninterrupted run (the epoch permutations of the skipped epochs are
+    drawn and discarded)."""
     import torch
     rng = np.random.default_rng(seed)
     n = F.shape[0]
     yq_t = torch.as_tensor(yq, dtype=torch.int32, device=F.device)
     yp_t = torch.as_tensor(yp, dtype=torch.int32, device=F.device)
-    hist = []
-    for ep in range(epochs):
+    hist, start = [], 0
+    if ckpt and os.path.exists(ckpt):
+        prop.load(ckpt)
+        d = np.load(ckpt)
+        start = int(d["epoch"])
+        hist = [float(x) for x in d["hist"]]
+        for _ in range(start):
+            rng.permutation(n)
+
+    def save(ep):
+        tmp = ckpt + ".tmp.npz"
+        prop.save(tmp)
+        d = dict(np.load(tmp))
+        np.savez(tmp, epoch=ep, hist=np.asarray(hist, dtype=np.float64), **d)
+        os.replace(tmp, ckpt)
+
+    for ep in range(start, epochs):
         perm = torch.as_tensor(rng.permutation(n), device=F.device)
         tot = 0.0
         for b0 in range(0, n - batch + 1, batch):
@@ -217,6 +266,10 @@ def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0):
             loss = prop.step(F[idx].contiguous(), yq_t[idx].contiguous(), yp_t[idx].contiguous(), lr=lr)
             tot += float(loss)
         hist.append(tot / max(1, n // batch))
+        if ckpt and ckpt_every and (ep + 1) % ckpt_every == 0:
+            save(ep + 1)
+    if ckpt:
+        save(epochs)
     return hist
 
 
@@ -277,23 +330,26 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--save", default=None)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--shards", default=None, help="directory of label shards (resumable label generation)")
+    ap.add_argument("--ckpt", default=None, help="training checkpoint (resumable training)")
+    ap.add_argument("--ckpt-every", type=int, default=20)
     args = ap.parse_args(argv)
     pq.load(build_if_missing=True)
     t0 = time.time()
-    F_all, yq_all, yp_all = [], [], []
-    for c in range(args.chunks):
+
+    def make_chunk(c):
         As, ks, tails = make_matrices(1000 * args.seed + c, args.chunk, m_range=(512, args.max_dim))
         F, err, yq, yp = label(As, ks, tails, seed=c)
-        F_all.append(F)
-        yq_all.append(yq)
-        yp_all.append(yp)
-        del As
+        return F, yq, yp
+
+    F_all, yq_all, yp_all = labelled_chunks(args.chunks, make_chunk, args.shards)
     t_label = time.time() - t0
-    F = torch.cat(F_all)
+    F = torch.from_numpy(np.concatenate(F_all)).to("cuda")
     yq = np.concatenate(yq_all)
     yp = np.concatenate(yp_all)
     prop = Proposer(seed=args.seed + 1)
-    hist = train(prop, F, yq, yp, epochs=args.epochs, batch=128, lr=2e-3, seed=args.seed)
+    hist = train(prop, F, yq, yp, epochs=args.epochs, batch=128, lr=2e-3, seed=args.seed, ckpt=args.ckpt,
+                 ckpt_every=args.ckpt_every)
     t_train = time.time() - t0 - t_label
     if args.save:
         prop.save(args.save)
