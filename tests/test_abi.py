@@ -90,3 +90,14 @@ def test_batched_plan_validates(pq):
         assert pq.pbpqlp_batch_workspace_bytes(h) > 8 * (100 + 500) * 32
     finally:
         pq.pbpqlp_batch_destroy(h)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every entry point raises."""
+    import paper_2103_07245_gb300 as pq
+    monkeypatch.setattr(pq._build, "LIB", str(tmp_path / "absent" / "libpbpqlp.so"))
+    monkeypatch.setattr(pq, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pq.load()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pq.pbpqlp_version()
