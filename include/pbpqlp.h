@@ -96,7 +96,7 @@ const char* pbpqlp_strerror(int status);
  * Create a plan for one factorization shape (Algorithm 3 inputs).
  *   m, n   : rows / columns of A (m, n >= 1).
  *   k, p   : target rank and oversampling; l = k + p must satisfy
- *            1 <= k <= l <= min(m, n) and l <= 256.
+ *            1 <= k <= l <= min(m, n) and l <= 224.
  *   q      : power iterations, q >= 0 (q = 0 is the basic form, Eqs. 3-8).
  *   seed   : seed of the Philox4x32-10 Gaussian stream of Phi.
  *   mode   : PBPQLP_MODE_*.
@@ -331,21 +331,26 @@ int pbpqlp_propose(const float* features, int count, const float* params, int* q
  * inference-engine plugin, or a path that must not pay cudaMalloc's implicit
  * synchronisation).  It takes the same inputs and outputs as pbpqlp_factor
  * but no workspace: the scratch is a fixed array of
- * PBPQLP_STATIC_SCRATCH_BYTES inside the library, which every GPU that loads
- * the library reserves until the process exits.
+ * PBPQLP_STATIC_SCRATCH_BYTES inside the library.  Once reserved on a GPU,
+ * the array stays reserved there until the process exits.
  *   - Plans with pbpqlp_workspace_bytes(plan) > PBPQLP_STATIC_SCRATCH_BYTES
  *     are rejected with PBPQLP_EWORKSPACE before anything is enqueued.
- *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.  The current device must own the plan's stream and
- *     the buffers.
+ *   - The first call on a device does a one-time set-up with that device
+ *     current: it looks up the array's device address and caches it.  Under
+ *     CUDA's default lazy module loading that lookup is also what loads the
+ *     array's module, so the 32 MiB are reserved (an implicit device
+ *     allocation that may synchronise) at that first call, not when the
+ *     library is loaded; with CUDA_MODULE_LOADING=EAGER they are reserved at
+ *     load time.  Make that first call as a warm-up, outside any path that
+ *     must not allocate or synchronise, and before any stream capture.
+ *     Later calls allocate nothing.  The current device must own the plan's
+ *     stream and the buffers.
  *   - Every call shares the one array, so calls whose work overlaps on the
  *     GPU (other streams, other plans, other host threads) race and corrupt
  *     each other; serialise them.  State that must start at zero is cleared
  *     by each call.
- *   - It allocates nothing (no cudaMalloc, cudaFree or allocating library
- *     call).  pbpqlp_sync_status reports its device status like
- *     pbpqlp_factor's.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *     pbpqlp_sync_status reports its device status like pbpqlp_factor's.
  */
 #define PBPQLP_STATIC_SCRATCH_BYTES (32u << 20)
 int pbpqlp_factor_static(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
@@ -365,6 +370,19 @@ int pbpqlp_read_timing(pbpqlp_plan_t plan, double* pass_ms_total, int64_t* pass_
 
 /* Process-wide count of CUDA kernels this library has launched so far. */
 int64_t pbpqlp_kernel_launch_count(void);
+
+/*
+ * Diagnostic of the library's internal FP64 helpers (not part of the paper's
+ * method): for each of the n doubles d[i] (device), writes the Newton-refined
+ * reciprocal rcp[i] ~ 1/d[i] and reciprocal square root rsqrt[i] ~
+ * 1/sqrt(d[i]) (device outputs) that the Cholesky and QR kernels use in
+ * place of FP64 division and square root.  Positive normal inputs are within
+ * 2 ulp of the correctly rounded results; every other input (zero, subnormal,
+ * negative, Inf, NaN, and d >= 2^1023 for the reciprocal) takes CUDA's own
+ * division / square root.  Asynchronous on `stream`; PBPQLP_EINVAL for n < 0
+ * or null pointers with n > 0.
+ */
+int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, void* stream);
 
 #ifdef __cplusplus
 }

@@ -140,6 +140,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_read_timing.restype = ci
     L.pbpqlp_kernel_launch_count.argtypes = []
     L.pbpqlp_kernel_launch_count.restype = ctypes.c_int64
+    L.pbpqlp_newton_check.argtypes = [vp, i64, vp, vp, vp]
+    L.pbpqlp_newton_check.restype = ci
     _lib = L
     return L
 
@@ -309,6 +311,12 @@ def pbpqlp_read_timing(plan):
 
 def pbpqlp_kernel_launch_count() -> int:
     return int(load().pbpqlp_kernel_launch_count())
+
+
+def pbpqlp_newton_check(d, n, rcp, rsqrt, stream=None):
+    """The library's Newton-refined 1/d and 1/sqrt(d) for n device doubles (a diagnostic)."""
+    _check(load().pbpqlp_newton_check(_ptr(d), int(n), _ptr(rcp), _ptr(rsqrt), _stream(stream)),
+           "pbpqlp_newton_check")
 
 
 def _ptr_array(xs):

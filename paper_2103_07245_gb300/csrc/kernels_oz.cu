@@ -1,6 +1,6 @@
 // FP64-accurate products on the BF16 tensor cores by exact integer digits
 // (the error-free splitting of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
-// 2012, with balanced base-256 digits held in BF16 and exact FP32 sums).
+// 2012, with eight balanced base-128 digits held in BF16 and exact FP32 sums).
 // They serve the products of Algorithm 3 that must carry FP64 accuracy: the
 // Grams of CholeskyQR (the orth of Eq. 4), R = Q^T D (Eq. 6) and, in the
 // emulated-FP64 mode, the products with A and A^T (Eqs. 3 and 5).

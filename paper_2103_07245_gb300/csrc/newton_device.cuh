@@ -9,12 +9,14 @@ namespace pbq {
 
 // 1/d for a positive normal double: d = m 2^k with m in [1, 2), an FP32 seed
 // for 1/m refined by two Newton-Raphson steps y += y (1 - m y) (each doubles
-// the correct bits: ~24 -> ~48 -> 53), scaled by 2^-k.  Other inputs take the
-// library division.
+// the correct bits: ~24 -> ~48 -> 53), scaled by 2^-k.  The scale 2^-k is a
+// normal double only for k <= 1022; d >= 2^1023 (biased exponent 2046, a
+// subnormal result), subnormal, zero, negative and non-finite d take the
+// library division.  Within 2 ulp of the correctly rounded 1/d.
 __device__ __forceinline__ double rcp_nr(double d) {
     const long long b = __double_as_longlong(d);
     const int eb = (int)((b >> 52) & 0x7FF);
-    if (eb == 0 || eb == 0x7FF || b < 0) return 1.0 / d;
+    if (eb == 0 || eb >= 0x7FE || b < 0) return 1.0 / d;
     const int k = eb - 1023;
     const double m = __longlong_as_double(b - (long long)k * (1LL << 52));
     double y = (double)__frcp_rn((float)m);
@@ -28,7 +30,9 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 // 1/sqrt(d) for a positive normal double: d = m 4^k with m in [1, 4), an FP32
 // seed for 1/sqrt(m) refined by two Newton-Raphson steps y += y (1 - m y^2) / 2,
-// scaled by 2^-k.  Other inputs take the library operations.
+// scaled by 2^-k (k in [-511, 511], always a normal scale).  Subnormal, zero,
+// negative and non-finite d take the library operations.  Within 2 ulp of
+// the correctly rounded 1/sqrt(d).
 __device__ __forceinline__ double rsqrt_nr(double d) {
     const long long b = __double_as_longlong(d);
     const int eb = (int)((b >> 52) & 0x7FF);

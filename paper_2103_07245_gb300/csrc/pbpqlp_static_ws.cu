@@ -4,8 +4,13 @@
 // or on a path where cudaMalloc's implicit device synchronisation is not
 // acceptable; they cannot provide the workspace pbpqlp_factor needs.  This
 // entry point uses a fixed scratch array that is part of the library image
-// instead: every GPU that loads the library reserves it until the process
-// exits, so its size is kept modest and larger plans are rejected.
+// instead.  Under CUDA's default lazy module loading the array is reserved on
+// a GPU when the first call there looks up its address (that lookup loads
+// this file's module); with CUDA_MODULE_LOADING=EAGER it is reserved when the
+// library is loaded.  Either way it stays reserved until the process exits,
+// so its size is kept modest and larger plans are rejected.  Callers make
+// the first call per device as a warm-up, outside the path that must not
+// allocate; later calls allocate nothing.
 #include <mutex>
 
 #include "../../include/pbpqlp.h"

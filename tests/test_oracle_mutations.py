@@ -9,6 +9,8 @@ import sys
 
 import pytest
 
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pbpqlp_oracle.c")
 
@@ -40,3 +42,46 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "mistake %r passed every pin:\n%s" % (name, r.stdout[-2000:])
     assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+# Planted mistakes in the Python parts of the oracle: AdamW (oracle/mlp.py)
+# and the probe estimator (oracle/__init__.py).  Each copy is loaded as a
+# module of its own and must fail the closed-form pins of test_oracle_aux_pins.
+PY_MUTANTS = {
+    "adamw_no_bias_correction": ("mlp.py", "(m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)",
+                                 "m / (np.sqrt(v) + eps)"),
+    "adamw_coupled_l2": ("mlp.py", "    m = b1 * m + (1 - b1) * g\n",
+                         "    g = g + wd * p\n    m = b1 * m + (1 - b1) * g\n"),
+    "adamw_bias_exponent_off_by_one": ("mlp.py", "(1 - b1 ** t)", "(1 - b1 ** (t + 1))"),
+    "probe_no_sqrt": ("__init__.py", "np.sqrt(np.sum(EW * EW) / np.sum(AW * AW))",
+                      "np.sum(EW * EW) / np.sum(AW * AW)"),
+    "probe_sign_of_reconstruction": ("__init__.py", "EW = AW - Q[:, :r]", "EW = AW + Q[:, :r]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_pins_catch_planted_mistake(name, tmp_path, orc):
+    import importlib.util
+    import types
+
+    fname, old, new = PY_MUTANTS[name]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / ("mutant_" + fname)
+    path.write_text(src.replace(old, new))
+    import test_oracle_aux_pins as pins
+    if fname == "mlp.py":
+        spec = importlib.util.spec_from_file_location("mlp_mutant", str(path))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        with pytest.raises(AssertionError):
+            pins.check_adamw(mod)
+    else:
+        # only the estimator is taken from the mutant; the factorization stays the oracle's
+        ns = {}
+        code = src.replace(old, new)
+        start = code.index("def probe_error_estimate")
+        exec(compile("import numpy as np\n" + code[start:], str(path), "exec"), ns)
+        mod = types.SimpleNamespace(pbpqlp=orc.pbpqlp, probe_error_estimate=ns["probe_error_estimate"])
+        with pytest.raises(AssertionError):
+            pins.check_probe_estimate(mod)

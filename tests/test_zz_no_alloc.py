@@ -1,8 +1,10 @@
 """pbpqlp_factor_static: the factorization entry point for callers that cannot
 allocate device memory (their host framework owns every device allocation, or
 they must not pay cudaMalloc's implicit synchronisation).  It runs in the
-library's fixed device scratch array; its results must equal those of
-pbpqlp_factor with a caller workspace.
+library's fixed device scratch array; its results must equal, bit for bit,
+those of pbpqlp_factor with a caller workspace (the same deterministic
+kernels), match the oracle to the parity bar, and leave free device memory
+unchanged once the first call on the device has made its one-time set-up.
 
 This file is collected last on purpose, and passes both alone in a fresh
 process and after the rest of the suite."""
@@ -31,7 +33,15 @@ def test_static_scratch_matches_workspace_entry_point(pq):
     m, n, k, p, q = 1000, 1000, 20, 5, 1
     plan = pq.Plan(m, n, k, p, q, seed=2)
     assert plan.ws_bytes <= pq.PBPQLP_STATIC_SCRATCH_BYTES
-    # two calls in a row, on two different matrices, each against the workspace entry point
+    # a warm-up call makes the one-time per-device set-up (the array's address
+    # lookup, which may load the module and reserve the array) before anything
+    # is measured
+    A0 = torch.from_numpy(synth.poly_decay(9, m, n, 2.0)).cuda()
+    Qa, L, Qb = plan.outputs()
+    pq.pbpqlp_factor_static(plan.handle, A0, A0.stride(0), pq.PBPQLP_F64, None, Qa, L, Qb)
+    assert plan.sync_status()[0] == pq.PBPQLP_OK
+    # two calls in a row, on two different matrices, each against the workspace
+    # entry point (the same deterministic kernels: bitwise equal) and the oracle
     for call, seed in enumerate((1, 5)):
         A_np = synth.poly_decay(seed, m, n, 2.0)
         A = torch.from_numpy(A_np).cuda()
@@ -39,14 +49,21 @@ def test_static_scratch_matches_workspace_entry_point(pq):
         rc, flags = plan.sync_status()
         assert rc == pq.PBPQLP_OK, flags
         Qa, L, Qb = plan.outputs()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        launches0 = pq.pbpqlp_kernel_launch_count()
         pq.pbpqlp_factor_static(plan.handle, A, A.stride(0), pq.PBPQLP_F64, None, Qa, L, Qb)
         rc, flags = plan.sync_status()
         assert rc == pq.PBPQLP_OK, (call, flags)
+        assert torch.cuda.mem_get_info()[0] == free0, "the static entry point changed free device memory"
+        assert pq.pbpqlp_kernel_launch_count() > launches0
+        for got, ref in ((Qa, Qa_w), (L, L_w), (Qb, Qb_w)):
+            assert torch.equal(got, ref), call
+        ref = oracle.pbpqlp(A_np, k + p, q, seed=2)
         got = [t.cpu().numpy() for t in (Qa, L, Qb)]
-        ref = [t.cpu().numpy() for t in (Qa_w, L_w, Qb_w)]
-        diff = np.linalg.norm(oracle.reconstruct(*got, k) - oracle.reconstruct(*ref, k)) / np.linalg.norm(A_np)
+        diff = np.linalg.norm(oracle.reconstruct(*got, k) - oracle.reconstruct(ref["Q"], ref["L"], ref["P"], k)) \
+            / np.linalg.norm(A_np)
         assert diff <= TOL, (call, diff)
-        assert np.max(np.abs(got[1] - ref[1])) <= 1e-12 * np.max(np.abs(ref[1]))
 
 
 def test_static_scratch_rejects_plans_above_its_size(pq):
