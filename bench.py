@@ -134,6 +134,9 @@ def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
             "achieved_basis": "tensor-pipe MMA flops (36 digit products, N padded to %d)" % (nt * 48)
             if tensor else "bytes of the digits of A per column tile + panel digits + partials",
             "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
+            # the same launch on the algorithmic bytes of the FP64 product it replaces
+            # (A once in FP64, the panels): what the digit re-reads cost
+            "frac_algorithmic_bytes": (8.0 * rows * K + 8.0 * (rows + K) * l) / t / 1e9 / hbm_peak,
             "avg_launch_ms": avg_ms}
 
 
@@ -257,6 +260,23 @@ def dist_setup():
     return world, rank, local
 
 
+def dense_config(w, world):
+    """The `config` object of a dense workload; both arms print this same dict."""
+    abytes = (4 if w["gen"] == "xyt" else 8) * w["m"] * w["n"]
+    return {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
+            "mode": w["mode"], "l2": "inputs larger than L2 (A is %d MB), no flush" % (abytes // 2 ** 20),
+            "parallelism": "independent factorizations per GPU" if world > 1 else "single GPU"}
+
+
+def sparse_config(w, world, nnz):
+    l = w["k"] + w["p"]
+    return {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"], "nnz": nnz,
+            "mode": "FP64",
+            "l2": "the n x l panel the SpMM gathers from (%d MB) fits L2; the CSR arrays (%d MB) do not"
+                  % (w["n"] * l * 8 // 2 ** 20, (12 * nnz + 8 * w["m"]) // 2 ** 20),
+            "parallelism": "one factorization per GPU" if world > 1 else "single GPU"}
+
+
 def sparse_matrix(w, seed):
     """The CSR workload (host numpy arrays): rowptr int64, colind int32, values FP64."""
     import synth
@@ -281,8 +301,7 @@ def run_reference_sparse(args, w, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
-                   "nnz": int(rp[-1]), "mode": w["mode"]},
+        "config": sparse_config(w, world, int(rp[-1])),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": "one full FP64 oracle factorization (CSR form) per step on the same workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -297,11 +316,7 @@ def run_sparse(args, w, world, rank, local):
     import torch
     import paper_2103_07245_gb300 as pq
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     pq.load(build_if_missing=True)
     m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
     l = k + p
@@ -366,10 +381,7 @@ def run_sparse(args, w, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q, "nnz": nnz, "mode": "FP64",
-                   "l2": "the n x l panel the SpMM gathers from (%d MB) fits L2; the CSR arrays (%d MB) do not"
-                         % (n * plan.l * 8 // 2 ** 20, (12 * nnz + 8 * m) // 2 ** 20),
-                   "parallelism": "single GPU" if world == 1 else "one factorization per GPU"},
+        "config": sparse_config(w, world, nnz),
         "tflops_algorithmic": value * (2 * q + 2) * 2.0 * nnz * l / 1e12,
         "roofline": {"kernel": "k_csr_spmm (CSR A times an l-column panel, FP64 FMA, warp per row)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -399,9 +411,7 @@ def run_sparse(args, w, world, rank, local):
         line["parity"] = {"rel_fro_diff_rank_k_probe_estimate": float(np.linalg.norm(D) / 4.0 /
                                                                       scipy.sparse.linalg.norm(S)),
                           "tol": 1e-11, "probes": 16}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_reference(args, w, world, rank):
@@ -428,8 +438,7 @@ def run_reference(args, w, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "p": w["p"], "q": w["q"],
-                   "mode": w["mode"], "l2": "inputs larger than L2 (A is %d MB)" % (w["m"] * w["n"] * 8 // 2 ** 20)},
+        "config": dense_config(w, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle factorization per step on the same workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -446,11 +455,7 @@ def run_batched(args, w, world, rank, local):
     import paper_2103_07245_gb300 as pq
     import synth
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     pq.load(build_if_missing=True)
     hbm_peak, bf16_peak, bf16_sus, peak_src = measured_peaks()
     shapes = synth.batched_shapes(2024 + rank, w["count"])
@@ -654,45 +659,82 @@ def run_batched(args, w, world, rank, local):
                                 % (len(sample), max(1, count // 6))}
         line["parity"] = {"error_ratio_vs_oracle": {"max": float(np.max(ratios)), "median": float(np.median(ratios))},
                           "tol_ratio": 1.1, "matrices": len(sample)}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fp64_8000", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-out-of-core", action="store_true")
-    args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
-        args.warmup = 3
-    w = WORKLOADS[args.workload]
-    world, rank, local = dist_setup()
-    if args.impl == "reference":
-        return run_reference(args, w, world, rank)
-    if w.get("batched"):
-        return run_batched(args, w, world, rank, local)
-    if w.get("sparse"):
-        return run_sparse(args, w, world, rank, local)
+def class_breakdown(pq, pl, A, outs, reps=2):
+    """Milliseconds per factorization of each timing class (events around every
+    launch group), from `reps` extra factorizations outside the timed region."""
+    ncls = len(pq.TIME_CLASSES)
+    pq.pbpqlp_set_timing_classes(pl.handle, (1 << ncls) - 1)
+    for c in range(ncls):
+        pq.pbpqlp_read_timing_class(pl.handle, c)
+    for _ in range(reps):
+        pl.factor(A, out=outs)
+    res = {}
+    for c, name in enumerate(pq.TIME_CLASSES):
+        msc, nc = pq.pbpqlp_read_timing_class(pl.handle, c)
+        res[name] = {"ms": msc / reps, "groups": nc // reps}
+    pq.pbpqlp_set_timing_classes(pl.handle, 0)
+    return res
 
+
+CLASS_KERNELS = {
+    "chol": "k_chol_inv_cluster (Cholesky of the CholeskyQR Gram with T = R^-T, FP64, one thread-block cluster)",
+    "gram": "CholeskyQR Grams (upper triangle of X^T X, FP64-accurate digit products on the tensor cores)",
+    "solve": "CholeskyQR solve Q = C T^T (FP64-accurate digit product)",
+    "smallqr": "k_small_qr_cluster (Householder QR of R^T, Eq. 7, FP64, one thread-block cluster)",
+    "other": "R = Q^T D and Qb = Pbar Ptil (digit products)",
+}
+
+
+def class_roofline(name, bd, m, n, l, q):
+    """Roofline of a non-pass class: its algorithmic FP64 flops per factorization
+    (FP64-equivalent for the digit forms) over its measured time, against the
+    FP64 issue rate of the whole GPU."""
+    orth_rows = [n] + [m, n] * q + [m]          # the orths of Algorithm 3, two CholeskyQR passes each
+    eff = 2 * len(orth_rows)                     # passes that run (the retry pairs exit at once)
+    if name == "chol":
+        flops = eff * (2.0 / 3.0) * l ** 3       # l^3/6 FMA each for R and for T = R^-T
+        per = eff
+    elif name == "gram":
+        flops = sum(2 * r * l * (l + 1) / 2.0 for r in orth_rows) * 2
+        per = eff
+    elif name == "solve":
+        flops = sum(r * l * l for r in orth_rows) * 2
+        per = eff
+    elif name == "smallqr":
+        flops = (8.0 / 3.0) * l ** 3
+        per = 1
+    else:
+        flops = m * l * (l + 1) + 2.0 * n * l * l
+        per = 2
+    t = bd[name]["ms"] / 1e3
+    ach = flops / t / 1e12 if t > 0 else None
+    return {"kernel": CLASS_KERNELS[name], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS if ach else None, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (FP64-equivalent algorithmic flops)",
+            "launches_timed": per, "avg_launch_ms": bd[name]["ms"] / per,
+            "share_of_step": None}
+
+
+def dominant_roofline(bd, pass_roofline, m, n, l, q, step_ms):
+    """The roofline of the class that takes the most time per factorization."""
+    name = max(bd, key=lambda c: bd[c]["ms"])
+    r = dict(pass_roofline) if name == "pass" else class_roofline(name, bd, m, n, l, q)
+    r["share_of_step"] = bd[name]["ms"] / step_ms if step_ms else None
+    r["class"] = name
+    return r
+
+
+def run_dense(args, w, world, rank, local):
+    """One dense workload: value = factorizations/s; every leg's roofline points at
+    its dominant kernel class (timed live by class of launch)."""
     import numpy as np
     import torch
     import paper_2103_07245_gb300 as pq
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     pq.load(build_if_missing=True)
 
     m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
@@ -796,6 +838,9 @@ def main():
         roofline["peak_source"] = "%s (MEASURED_PEAKS.json: HBM copy GB/s, bf16 sustained TFLOP/s)" % peak_src
         roofline["launches_timed"] = pass_launches
         dtype = "bf16x3" if nprod == 3 else "bf16"
+    bd = class_breakdown(pq, plan, A, (Qa, L, Qb))
+    pass_roofline = roofline
+    roofline = dominant_roofline(bd, roofline, m, n, l, q, ms) if roofline else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -804,12 +849,12 @@ def main():
         # Core i7 at 1.8 GHz), as factorizations/s: context, another machine
         "vs_baseline": value * w["paper_seconds"] if w.get("paper_seconds") else None,
         "dtype": dtype, "data": "synthetic",
-        "config": {"workload": w["desc"], "m": m, "n": n, "k": k, "p": p, "q": q, "mode": w["mode"],
-                   "l2": "inputs larger than L2 (A is %d MB), no flush" % (A.numel() * A.element_size() // 2 ** 20),
-                   "parallelism": "independent factorizations per GPU" if world > 1 else "single GPU"},
+        "config": dense_config(w, world),
         "tflops_algorithmic": value * flops / 1e12,
         "rel_err_rank_k": err_main,
         "roofline": roofline,
+        "pass_roofline": pass_roofline,
+        "breakdown_ms_per_step": {c: round(v["ms"], 4) for c, v in bd.items()},
         "e2e": {"value": world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -843,12 +888,15 @@ def main():
         cms, cpms, cpn, _, _ = timed_run(cplan, couts, args.steps)
         err_c = cplan.error(A, *couts, k, method=pq.PBPQLP_ERR_RESIDUAL)
         nprod = 3 if w["compare"] == "BF16X3" else 1
+        cpass = tc_roofline(max(m, n), min(m, n), l, nprod, cpms / cpn, hbm_peak, bf16_sus) if cpn else None
+        cbd = class_breakdown(pq, cplan, A, couts)
         line["mixed"] = {"mode": w["compare"], "value": world / (cms / 1e3), "unit": UNIT, "ms_per_step": cms,
                          "tflops_algorithmic": world / (cms / 1e3) * flops / 1e12,
                          "rel_err_rank_k": err_c, "rel_err_rank_k_fp64": err_main,
                          "error_ratio_vs_fp64": err_c / err_main, "speedup_vs_fp64": ms / cms,
-                         "roofline": tc_roofline(max(m, n), min(m, n), l, nprod, cpms / cpn if cpn else None,
-                                                 hbm_peak, bf16_sus) if cpn else None}
+                         "roofline": dominant_roofline(cbd, cpass, m, n, l, q, cms) if cpass else None,
+                         "pass_roofline": cpass,
+                         "breakdown_ms_per_step": {c: round(v["ms"], 4) for c, v in cbd.items()}}
         del cplan
 
     # ---- the same matrix with the products emulated in FP64 accuracy on the tensor cores
@@ -869,10 +917,14 @@ def main():
             "dtype": "bf16 digit products summed exactly (FP64-accurate)",
             "tflops_algorithmic": whole_job_rate(1, world, ems) * flops / 1e12,
             "rel_err_rank_k": err_e, "rel_err_rank_k_fp64": err_main,
-            "rel_fro_diff_vs_fp64_rank_k": diff, "speedup_vs_fp64": ms / ems, "gpu_launches": elaunch,
-            "roofline": dict(oz_roofline(max(m, n), min(m, n), l, epms / epn, hbm_peak, bf16_sus),
-                             traffic=read_traffic("oz_gemm_fp64emu_8000") if (m, n, l) == (8000, 8000, 110) else None)
-            if epn else None}
+            "rel_fro_diff_vs_fp64_rank_k": diff, "speedup_vs_fp64": ms / ems, "gpu_launches": elaunch}
+        epass = dict(oz_roofline(max(m, n), min(m, n), l, epms / epn, hbm_peak, bf16_sus),
+                     traffic=read_traffic("oz_gemm_fp64emu_8000") if (m, n, l) == (8000, 8000, 110) else None) \
+            if epn else None
+        ebd = class_breakdown(pq, eplan, A, eouts)
+        line["fp64_emulated"]["roofline"] = dominant_roofline(ebd, epass, m, n, l, q, ems) if epass else None
+        line["fp64_emulated"]["pass_roofline"] = epass
+        line["fp64_emulated"]["breakdown_ms_per_step"] = {c: round(v["ms"], 4) for c, v in ebd.items()}
         del eplan, eouts
 
     # ---- CPU baseline: the oracle, rank 0 at N = 1, and parity of the timed result
@@ -896,6 +948,57 @@ def main():
             e_orc = float(np.linalg.norm(A_np - Ac) / np.linalg.norm(A_np))
             line["parity"] = {"rel_err_rank_k": e_gpu, "rel_err_rank_k_oracle": e_orc,
                               "error_ratio": e_gpu / e_orc, "tol_ratio": 1.1}
+    return line
+
+
+DEFAULT_WORKLOAD = "fp64_8000"
+# Sub-legs of the default run: the split-BF16 20000^2 workload and the 512-matrix batch.
+DEFAULT_SUBLEGS = (("mixed_c3", "bf16x3_20000"), ("batched", "batched_512"))
+SUBLEG_KEYS = ("value", "unit", "ms_per_step", "dtype", "config", "tflops_algorithmic", "rel_err_rank_k", "roofline",
+               "breakdown_ms_per_step", "e2e", "e2e_staged", "gpu_launches", "clocks", "cpu_baseline", "parity",
+               "fp64_batched")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-out-of-core", action="store_true")
+    ap.add_argument("--no-sublegs", action="store_true", help="default workload only: skip the c3 and batched legs")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if w.get("batched"):
+        line = run_batched(args, w, world, rank, local)
+    elif w.get("sparse"):
+        line = run_sparse(args, w, world, rank, local)
+    else:
+        line = run_dense(args, w, world, rank, local)
+    if args.workload == DEFAULT_WORKLOAD and not args.no_sublegs:
+        for key, name in DEFAULT_SUBLEGS:
+            torch.cuda.empty_cache()
+            wl = WORKLOADS[name]
+            sub = run_batched(args, wl, world, rank, local) if wl.get("batched") else \
+                run_dense(args, wl, world, rank, local)
+            line[key] = {kk: sub[kk] for kk in SUBLEG_KEYS if kk in sub}
+            # the sub-legs' kernels count toward this run's launches too
+            line["gpu_launches"] = line.get("gpu_launches", 0) + sub.get("gpu_launches", 0)
+            line.setdefault("gpu_launches_by_leg", {})[key] = sub.get("gpu_launches", 0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -368,6 +368,29 @@ int pbpqlp_factor_static(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_d
 int pbpqlp_set_timing(pbpqlp_plan_t plan, int enable);
 int pbpqlp_read_timing(pbpqlp_plan_t plan, double* pass_ms_total, int64_t* pass_launches);
 
+/*
+ * Timing by class of launch (observability, not part of the method): bit c
+ * of mask enables event pairs around every launch group of class c on later
+ * pbpqlp_factor calls (mask 0 disables all; pbpqlp_set_timing toggles bit
+ * PBPQLP_TIME_PASS only).  Classes: the products with A or A^T (Eqs. 3 and 5
+ * and the power iterations); the Cholesky of the CholeskyQR Gram (with
+ * T = R^-T where used); the Grams of CholeskyQR (Eq. 4); the CholeskyQR
+ * solve Q = C R^-1; the l x l QR of R^T (Eq. 7); the rest (R = Q^T D and
+ * Qb = Pbar Ptil).  pbpqlp_read_timing_class waits for the stream, returns
+ * the summed milliseconds and number of groups of class cls since its last
+ * read, and clears them.  PBPQLP_EINVAL for an unknown class or mask bit.
+ */
+enum {
+    PBPQLP_TIME_PASS = 0,
+    PBPQLP_TIME_CHOL = 1,
+    PBPQLP_TIME_GRAM = 2,
+    PBPQLP_TIME_SOLVE = 3,
+    PBPQLP_TIME_SMALLQR = 4,
+    PBPQLP_TIME_OTHER = 5
+};
+int pbpqlp_set_timing_classes(pbpqlp_plan_t plan, unsigned mask);
+int pbpqlp_read_timing_class(pbpqlp_plan_t plan, int cls, double* ms_total, int64_t* groups);
+
 /* Process-wide count of CUDA kernels this library has launched so far. */
 int64_t pbpqlp_kernel_launch_count(void);
 

@@ -35,6 +35,14 @@ PBPQLP_ERR_IDENTITY = 0
 PBPQLP_ERR_RESIDUAL = 1
 PBPQLP_ERR_PROBES = 2
 
+PBPQLP_TIME_PASS = 0
+PBPQLP_TIME_CHOL = 1
+PBPQLP_TIME_GRAM = 2
+PBPQLP_TIME_SOLVE = 3
+PBPQLP_TIME_SMALLQR = 4
+PBPQLP_TIME_OTHER = 5
+TIME_CLASSES = ("pass", "chol", "gram", "solve", "smallqr", "other")
+
 PBPQLP_STATIC_SCRATCH_BYTES = 32 << 20
 
 MAX_ELL = 224
@@ -140,6 +148,10 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_read_timing.restype = ci
     L.pbpqlp_kernel_launch_count.argtypes = []
     L.pbpqlp_kernel_launch_count.restype = ctypes.c_int64
+    L.pbpqlp_set_timing_classes.argtypes = [vp, ctypes.c_uint]
+    L.pbpqlp_set_timing_classes.restype = ci
+    L.pbpqlp_read_timing_class.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.pbpqlp_read_timing_class.restype = ci
     L.pbpqlp_newton_check.argtypes = [vp, i64, vp, vp, vp]
     L.pbpqlp_newton_check.restype = ci
     _lib = L
@@ -306,6 +318,19 @@ def pbpqlp_read_timing(plan):
     ms = ctypes.c_double(0.0)
     n = ctypes.c_int64(0)
     _check(load().pbpqlp_read_timing(plan, ctypes.byref(ms), ctypes.byref(n)), "pbpqlp_read_timing")
+    return ms.value, int(n.value)
+
+
+def pbpqlp_set_timing_classes(plan, mask):
+    _check(load().pbpqlp_set_timing_classes(plan, int(mask)), "pbpqlp_set_timing_classes")
+
+
+def pbpqlp_read_timing_class(plan, cls):
+    """Returns (milliseconds summed over the timed groups of class cls, number of groups)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().pbpqlp_read_timing_class(plan, int(cls), ctypes.byref(ms), ctypes.byref(n)),
+           "pbpqlp_read_timing_class")
     return ms.value, int(n.value)
 
 

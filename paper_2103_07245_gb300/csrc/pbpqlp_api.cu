@@ -18,6 +18,8 @@
 
 using namespace pbq;
 
+constexpr int kTimeClasses = 6;   // PBPQLP_TIME_PASS .. PBPQLP_TIME_OTHER
+
 struct pbpqlp_plan_s {
     int64_t m = 0, n = 0;
     int k = 0, p = 0, q = 0, l = 0;
@@ -54,12 +56,14 @@ struct pbpqlp_plan_s {
     size_t off_T = 0;
     size_t off_ozEr = 0, off_ozEc = 0, off_ozArow = 0, off_ozAcol = 0;
     void* last_ws = nullptr;
-    // observability: CUDA event pairs around each A / A^T pass kernel
-    bool timing = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    size_t ev_used = 0;
+    // observability: CUDA event pairs around the launches of each timing
+    // class (PBPQLP_TIME_*): bit c of timing_mask enables class c
+    unsigned timing_mask = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kTimeClasses];
+    size_t ev_used[kTimeClasses] = {};
     ~pbpqlp_plan_s() {
-        for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        for (auto& v : ev)
+            for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     }
 };
 
@@ -147,16 +151,33 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA
 
 #define PBQ_TRY(expr) do { cudaError_t e_ = PBQ_DBG(expr); if (e_ != cudaSuccess) return PBPQLP_ECUDA; } while (0)
 
-// Event pair for the next timed pass kernel (nullptr pair when timing is off).
-std::pair<cudaEvent_t, cudaEvent_t> next_events(pbpqlp_plan_s* P) {
-    if (!P->timing) return {nullptr, nullptr};
-    if (P->ev_used == P->ev.size()) {
+// Event pair for the next timed launch group of class cls (nullptr pair when
+// that class is not timed).
+std::pair<cudaEvent_t, cudaEvent_t> next_events(pbpqlp_plan_s* P, int cls = PBPQLP_TIME_PASS) {
+    if (!(P->timing_mask & (1u << cls))) return {nullptr, nullptr};
+    auto& v = P->ev[cls];
+    if (P->ev_used[cls] == v.size()) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return {nullptr, nullptr};
-        P->ev.emplace_back(a, b);
+        v.emplace_back(a, b);
     }
-    return P->ev[P->ev_used++];
+    return v[P->ev_used[cls]++];
 }
+
+// Brackets the launches of one timing class between construction and end().
+struct TimedGroup {
+    cudaEvent_t b = nullptr;
+    cudaStream_t s;
+    TimedGroup(pbpqlp_plan_s* P, int cls) : s(P->stream) {
+        const auto ev = next_events(P, cls);
+        if (ev.first && cudaEventRecord(ev.first, s) == cudaSuccess) b = ev.second;
+    }
+    void end() {
+        if (b) cudaEventRecord(b, s);
+        b = nullptr;
+    }
+    ~TimedGroup() { end(); }
+};
 
 // C (M x l) = op(A) B through the split-K partial buffer when S > 1.  With
 // `timed`, the GEMM kernel launch is bracketed by a plan event pair.
@@ -257,7 +278,7 @@ int emu_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32,
 // Orthonormalise X (rows x l, ld ldp) in place: CholeskyQR in pass pairs
 // (X -> Y -> X).  Pair 1 is CholeskyQR2; pairs 2 and 3 run on the device
 // only if a pass of the previous pair needed the shifted retry.
-int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y, int Sg, int64_t kcg) {
+int orth(pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y, int Sg, int64_t kcg) {
     cudaStream_t s = P->stream;
     const int l = P->l;
     const int64_t ldp = P->ldp;
@@ -268,6 +289,7 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
         const int* cond = pass <= 2 ? nullptr : w.ctl + 8 + (pass + 1) / 2;
         const int64_t ps = (int64_t)l * ldp;
         // the Cholesky reads only the upper triangle of the Gram
+        TimedGroup tg(P, PBPQLP_TIME_GRAM);
         if (P->oz_gram) {
             const OzOperand op = panel_digits(w.ozS1, w.ozE1, l, rows);
             PBQ_TRY(launch_oz_panel(rows, l, src, ldp, w.ozE1, w.ozS1, cond, s));
@@ -277,9 +299,13 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
             PBQ_TRY(launch_upper_product(l, rows, src, src, ldp, w.part, ps, Sg, kcg, cond, s));
             PBQ_TRY(launch_reduce_partials(l, l, Sg, w.part, ps, ldp, w.G, l, cond, s, true));
         }
+        tg.end();
         if (P->chol_inv) {
             // dst = src R^{-1} = src T^T as an FP64-accurate digit product
+            TimedGroup tc(P, PBPQLP_TIME_CHOL);
             PBQ_TRY(launch_chol_inv(l, rows, w.G, w.Rp, w.T, w.status, w.ctl, pass, s));
+            tc.end();
+            TimedGroup ts(P, PBPQLP_TIME_SOLVE);
             OzOperand xd, yd;
             xd.S = w.ozS1; xd.rows = rows; xd.K = l; xd.eraw = w.ozEb;
             yd.S = w.ozS2; yd.rows = l; yd.K = l; yd.eraw = w.ozE2;
@@ -289,8 +315,11 @@ int orth(const pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y
                                       cond, s));
             continue;
         }
+        TimedGroup tc(P, PBPQLP_TIME_CHOL);
         if (P->cluster_chol) PBQ_TRY(launch_cholesky_cluster(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
         else PBQ_TRY(launch_cholesky(l, rows, w.G, w.Rp, w.status, w.ctl, pass, s));
+        tc.end();
+        TimedGroup ts(P, PBPQLP_TIME_SOLVE);
         PBQ_TRY(launch_trsm_rows(rows, l, w.Rp, src, ldp, dst, ldp, cond, s, P->nprod > 0));
     }
     return PBPQLP_OK;
@@ -514,6 +543,7 @@ int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* o
     if ((rc = product(false, w.Xn, w.Dm))) return rc;
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
     if ((rc = orth(P, w, m, w.Xm, w.Ym, P->S_gm, P->kc_gm))) return rc;
+    TimedGroup tr(P, PBPQLP_TIME_OTHER);
     if (P->oz_gram) {
         const OzOperand qd = panel_digits(w.ozS1, w.ozE1, l, m), dd = panel_digits(w.ozS2, w.ozE2, l, m);
         PBQ_TRY(launch_oz_panel(m, l, w.Xm, ldp, w.ozE1, w.ozS1, nullptr, s));
@@ -524,9 +554,13 @@ int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* o
         PBQ_TRY(launch_upper_product(l, m, w.Xm, w.Dm, ldp, w.part, ps, P->S_gm, P->kc_gm, nullptr, s));
         PBQ_TRY(launch_reduce_partials(l, l, P->S_gm, w.part, ps, ldp, w.R, l, nullptr, s, true));
     }
+    tr.end();
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
+    TimedGroup tq(P, PBPQLP_TIME_SMALLQR);
     if (P->cluster_qr) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
     else PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
+    tq.end();
+    TimedGroup tb(P, PBPQLP_TIME_OTHER);
     if (P->oz_gram) {
         // Qb[i][j] = sum_k Pbar[i][k] Ptil[k][j]: Pbar by rows, Ptil^T by rows
         OzOperand xd, yd;
@@ -744,22 +778,32 @@ int pbpqlp_rank_revealing(pbpqlp_plan_t P, const double* L, double tol, double* 
 
 int pbpqlp_set_timing(pbpqlp_plan_t P, int enable) {
     if (!P) return PBPQLP_EINVAL;
-    P->timing = enable != 0;
+    P->timing_mask = enable ? (P->timing_mask | 1u) : (P->timing_mask & ~1u);
+    return PBPQLP_OK;
+}
+
+int pbpqlp_read_timing_class(pbpqlp_plan_t P, int cls, double* ms_total, int64_t* launches) {
+    if (!P || !ms_total || !launches || cls < 0 || cls >= kTimeClasses) return PBPQLP_EINVAL;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return PBPQLP_ECUDA;
+    double tot = 0.0;
+    for (size_t i = 0; i < P->ev_used[cls]; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->ev[cls][i].first, P->ev[cls][i].second) != cudaSuccess) return PBPQLP_ECUDA;
+        tot += ms;
+    }
+    *ms_total = tot;
+    *launches = (int64_t)P->ev_used[cls];
+    P->ev_used[cls] = 0;
     return PBPQLP_OK;
 }
 
 int pbpqlp_read_timing(pbpqlp_plan_t P, double* ms_total, int64_t* launches) {
-    if (!P || !ms_total || !launches) return PBPQLP_EINVAL;
-    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return PBPQLP_ECUDA;
-    double tot = 0.0;
-    for (size_t i = 0; i < P->ev_used; ++i) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, P->ev[i].first, P->ev[i].second) != cudaSuccess) return PBPQLP_ECUDA;
-        tot += ms;
-    }
-    *ms_total = tot;
-    *launches = (int64_t)P->ev_used;
-    P->ev_used = 0;
+    return pbpqlp_read_timing_class(P, PBPQLP_TIME_PASS, ms_total, launches);
+}
+
+int pbpqlp_set_timing_classes(pbpqlp_plan_t P, unsigned mask) {
+    if (!P || (mask >> kTimeClasses) != 0) return PBPQLP_EINVAL;
+    P->timing_mask = mask;
     return PBPQLP_OK;
 }
 
