@@ -45,7 +45,7 @@ TIME_CLASSES = ("pass", "chol", "gram", "solve", "smallqr", "other")
 
 PBPQLP_STATIC_SCRATCH_BYTES = 32 << 20
 
-MAX_ELL = 224
+MAX_ELL = 4096          # l = k + p limit (blocked l x l steps beyond 224)
 
 _lib = None
 

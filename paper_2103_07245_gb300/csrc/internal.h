@@ -6,7 +6,9 @@
 
 namespace pbq {
 
-constexpr int kMaxEll = 224;          // l = k + p limit (packed l x l factor fits one SM's smem)
+constexpr int kMaxEll = 224;          // l handled by the one-cluster l x l kernels (factor in shared memory)
+constexpr int kMaxEllBlocked = 4096;  // l limit of the blocked l x l steps (kernels_blocked.cu)
+constexpr int kCholBlock = 128;       // diagonal block of the blocked Cholesky
 constexpr int kGemmBM = 64;           // rows per CTA tile of the skinny FP64 GEMM
 constexpr int kGemmBK = 16;           // contraction depth per shared-memory stage
 
@@ -99,6 +101,35 @@ cudaError_t launch_cholesky_cluster(int l, int64_t rows, const double* G, double
 bool chol_inv_fits(int l);
 cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rpacked, double* T, uint32_t* status,
                             int* ctl, int pass, cudaStream_t s);
+
+// One b x b diagonal block (b <= kMaxEll) of the blocked Cholesky: the cluster
+// kernel on S (leading dimension ld), pivot thresholds from gdiag (stride
+// ld + 1), R_tt (upper) into R and T_tt = R_tt^{-T} (lower) into T (both ld);
+// runs only if *bstate == want, sets *bstate = want + 1 on a failed pivot (4
+// on a non-finite one, with the status bit).
+cudaError_t launch_chol_inv_block(int b, const double* S, int64_t ld, const double* gdiag, double* R, double* T,
+                                  uint32_t* status, int* bstate, int want, cudaStream_t s);
+
+// ---- Blocked l x l steps (kernels_blocked.cu), any l <= kMaxEllBlocked ---
+// C (M x N, ldc) = alpha op(A) op(B) + beta C in FP64 (op(A) = A, M x K, or
+// A^T with A stored K x M; op(B) = B, K x N, or B^T with B stored N x K);
+// with upper, only C[i][j] with j >= i is written.  Each output sums its
+// contraction in index order.  Runs only if state is null or *state == want.
+cudaError_t launch_dgemm_gen(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                             int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, bool upper,
+                             const int* state, int want, cudaStream_t s);
+// Cholesky G = R^T R of the l x l Gram (ld l) of a rows x l panel, with
+// T = R^{-T} (lower, ld l), right-looking over kCholBlock diagonal blocks,
+// one shifted retry of the whole factorization, identity fallback on
+// breakdown; ctl / status / pass as launch_chol_inv.  work: the bytes below.
+size_t chol_inv_blocked_work_bytes(int l);
+cudaError_t launch_chol_inv_blocked(int l, int64_t rows, const double* G, double* T, void* work, uint32_t* status,
+                                    int* ctl, int pass, cudaStream_t s);
+// Householder QR of R^T (R upper, ld l): L = Rtil^T and Ptil (ld l) with
+// diag(Rtil) >= 0, blocked in 32-column panels.  work: the bytes below.
+bool qr_blocked_fits(int l);
+size_t qr_blocked_work_bytes(int l);
+cudaError_t launch_qr_blocked(int l, const double* R, double* L, double* Ptil, void* work, cudaStream_t s);
 
 // Y = X R^{-1} row by row (R from launch_cholesky), rows x l panels; f32
 // solves in FP32 (the mixed modes) instead of FP64.

@@ -52,10 +52,24 @@ constexpr int kCiNb = 16;
 
 }  // namespace
 
+// kBlock: the kernel factors one l x l diagonal block S_tt of a blocked
+// factorization (kernels_blocked.cu) instead of a whole Gram: it reads the
+// block at G (leading dimension ld), its pivot thresholds from the original
+// Gram's diagonal at gdiag (stride ld + 1), writes R_tt (upper, into Rp with
+// leading dimension ld) and T_tt (lower, into Tout, ld), makes one attempt,
+// and on a failed pivot sets *bstate = want + 1 (4 for a non-finite pivot,
+// with the status bit) instead of retrying.  It runs only if *bstate == want.
+template <bool kBlock>
 __global__ void __launch_bounds__(kCiThreads)
 k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
-                   double* __restrict__ Tout, uint32_t* __restrict__ status, int* __restrict__ ctl, int pass) {
-    if (pass >= 3 && ctl[8 + (pass + 1) / 2] == 0) return;   // uniform over the cluster
+                   double* __restrict__ Tout, uint32_t* __restrict__ status, int* __restrict__ ctl, int pass,
+                   int64_t ld, const double* __restrict__ gdiag, int* __restrict__ bstate, int want) {
+    if (kBlock) {
+        if (*bstate != want) return;   // uniform: nothing writes it before the first cluster barrier
+    } else {
+        if (pass >= 3 && ctl[8 + (pass + 1) / 2] == 0) return;   // uniform over the cluster
+        ld = l;
+    }
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -75,13 +89,13 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     if (tid == 0) { s_fail = 0; s_shift = 0.0; }
     __syncthreads();
     int shifted = 0, fail = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int attempt = 0; attempt < (kBlock ? 1 : 2); ++attempt) {
         const double shift = s_shift;
         for (int e = tid; e < ncol * l; e += nth) {
             const int jl = e / l, i = e - jl * l, j = jl * C + rank;
             double sv = 0.0, tv = 0.0;
             if (j < l) {
-                if (i <= j) sv = G[(int64_t)i * l + j] + (i == j ? shift : 0.0);
+                if (i <= j) sv = G[(int64_t)i * ld + j] + (i == j ? shift : 0.0);
                 tv = (i == j) ? 1.0 : 0.0;
             }
             Sown[e] = sv;
@@ -103,7 +117,9 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
                     const double* col = cluster.map_shared_rank(Sown, j % C) + (int64_t)(j / C) * l;
 #pragma unroll
                     for (int i = 0; i < kCiNb; ++i) s[i] = (i <= lane) ? col[a0 + i] : 0.0;
-                    if (attempt == 0) thr_mine = tau * G[(int64_t)j * l + j];
+                    // the shifted retry (attempt 1, or want 1 in block mode) only asks for d > 0
+                    if (attempt == 0 && !(kBlock && want == 1))
+                        thr_mine = tau * (kBlock ? gdiag[(int64_t)j * (ld + 1)] : G[(int64_t)j * l + j]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < kCiNb; ++i) s[i] = 0.0;
@@ -214,6 +230,15 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
         }
         __syncthreads();
         if (!fail) break;
+        if (kBlock) {
+            // every CTA saw the same failure; the host-side sequence retries or falls back
+            if (rank == 0 && tid == 0) {
+                if (fail == 2) atomicOr(status, kStNonFinite);
+                *bstate = fail == 2 ? 4 : want + 1;
+            }
+            cluster.sync();
+            return;
+        }
         if (fail == 2 || attempt == 1) {
             if (rank == 0 && tid == 0) atomicOr(status, fail == 2 ? kStNonFinite : kStBreakdown);
             for (int e = tid; e < ncol * l; e += nth) {
@@ -233,6 +258,17 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
         }
         shifted = 1;
         cluster.sync();   // every CTA is past its reads of the other CTAs' columns
+    }
+    if (kBlock) {
+        // R_tt (upper) and T_tt (lower) into the blocked factorization's matrices
+        for (int e = tid; e < ncol * l; e += nth) {
+            const int jl = e / l, i = e - jl * l, j = jl * C + rank;
+            if (j >= l) continue;
+            if (i <= j) Rp[(int64_t)i * ld + j] = Sown[e];
+            if (i >= j) Tout[(int64_t)i * ld + j] = Town[e];
+        }
+        cluster.sync();   // no CTA leaves while another may still read its shared memory
+        return;
     }
     // R packed (row a at a(2l - a + 1)/2, columns a .. l-1), 1/diag after it; T row-major
     const int64_t P = (int64_t)l * (l + 1) / 2;
@@ -266,11 +302,13 @@ static int chol_inv_ctas(int l) {
     if (best == 0) {
         best = 8;
         cudaFuncAttributes fa;
-        if (cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        if (cudaFuncSetAttribute(k_chol_inv_cluster<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
                 cudaSuccess &&
-            cudaFuncSetAttribute(k_chol_inv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_chol_inv_cluster<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_chol_inv_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)chol_inv_smem(kMaxEll, 8)) == cudaSuccess &&
-            cudaFuncGetAttributes(&fa, k_chol_inv_cluster) == cudaSuccess) {
+            cudaFuncGetAttributes(&fa, k_chol_inv_cluster<false>) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
@@ -283,7 +321,8 @@ static int chol_inv_ctas(int l) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int clusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&clusters, k_chol_inv_cluster, &cfg) == cudaSuccess && clusters > 0)
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_chol_inv_cluster<false>, &cfg) == cudaSuccess &&
+                clusters > 0)
                 best = kCiCtasMax;
         }
         cudaGetLastError();
@@ -294,11 +333,13 @@ static int chol_inv_ctas(int l) {
 
 bool chol_inv_fits(int l) { return l >= 1 && l <= kMaxEll && chol_inv_smem(l, 8) <= 200 * 1024; }
 
-cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rp, double* T, uint32_t* status, int* ctl,
-                            int pass, cudaStream_t s) {
+template <bool kBlock>
+static cudaError_t chol_inv_launch(int l, int64_t rows, const double* G, double* Rp, double* T, uint32_t* status,
+                                   int* ctl, int pass, int64_t ld, const double* gdiag, int* bstate, int want,
+                                   cudaStream_t s) {
     const int C = chol_inv_ctas(l);
     const size_t smem = chol_inv_smem(l, C);
-    cudaError_t e = func_smem_attr((const void*)k_chol_inv_cluster, smem);
+    cudaError_t e = func_smem_attr((const void*)k_chol_inv_cluster<kBlock>, smem);
     if (e != cudaSuccess) return e;
     // (the non-portable cluster size was allowed once, when C = 16 was chosen)
     cudaLaunchConfig_t cfg = {};
@@ -313,9 +354,21 @@ cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rp, do
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_chol_inv_cluster, l, rows, G, Rp, T, status, ctl, pass);
+    e = cudaLaunchKernelEx(&cfg, k_chol_inv_cluster<kBlock>, l, rows, G, Rp, T, status, ctl, pass, ld, gdiag, bstate,
+                           want);
     count_launches(1);
     return e;
+}
+
+cudaError_t launch_chol_inv(int l, int64_t rows, const double* G, double* Rp, double* T, uint32_t* status, int* ctl,
+                            int pass, cudaStream_t s) {
+    return chol_inv_launch<false>(l, rows, G, Rp, T, status, ctl, pass, l, nullptr, nullptr, 0, s);
+}
+
+cudaError_t launch_chol_inv_block(int b, const double* S, int64_t ld, const double* gdiag, double* R, double* T,
+                                  uint32_t* status, int* bstate, int want, cudaStream_t s) {
+    if (b < 1 || b > kMaxEll) return cudaErrorInvalidValue;
+    return chol_inv_launch<true>(b, 0, S, R, T, status, nullptr, 0, ld, gdiag, bstate, want, s);
 }
 
 }  // namespace pbq

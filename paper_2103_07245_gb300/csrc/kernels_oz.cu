@@ -658,7 +658,7 @@ k_oz_list(const CUtensorMap* __restrict__ maps, const OzListUnit* __restrict__ u
 __global__ void k_oz_panel_exp(int64_t rows, int N, const double* __restrict__ P, int64_t ldp, int* __restrict__ eraw,
                                const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
-    const int j = threadIdx.x;
+    const int j = blockIdx.y * 256 + threadIdx.x;
     if (j >= N) return;
     const int64_t r0 = (int64_t)blockIdx.x * 64;
     const int64_t r1 = r0 + 64 < rows ? r0 + 64 : rows;
@@ -958,10 +958,11 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
 
 cudaError_t launch_oz_panel(int64_t rows, int N, const double* P, int64_t ldp, int* eraw, void* S, const int* cond,
                             cudaStream_t s) {
-    if (rows < 1 || N < 1 || N > 256) return cudaErrorInvalidValue;
+    if (rows < 1 || N < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(eraw, 0, sizeof(int) * (size_t)N, s);
     if (e != cudaSuccess) return e;
-    k_oz_panel_exp<<<(unsigned)((rows + 63) / 64), 256, 0, s>>>(rows, N, P, ldp, eraw, cond);
+    k_oz_panel_exp<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((N + 255) / 256)), 256, 0, s>>>(rows, N, P, ldp,
+                                                                                                   eraw, cond);
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
     k_oz_panel_slice<<<grid, block, 0, s>>>(rows, N, P, ldp, eraw, (uint16_t*)S, cond);
     count_launches(2);

@@ -40,6 +40,9 @@ struct pbpqlp_plan_s {
     bool tf32 = false;                  // TF32 operands (modes TF32, TF32X3) instead of BF16
     bool cluster_chol = false;          // Cholesky on an 8-CTA cluster (l > 128)
     bool cluster_qr = false;            // small QR on an 8-CTA cluster (l > 64)
+    bool blocked = false;               // l > kMaxEll: blocked Cholesky and QR, products in column chunks
+    int cw = 0;                         // column chunk of the products with A (<= kMaxEll)
+    size_t off_blk = 0;                 // work area of the blocked Cholesky / QR
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
     size_t off_Ahi = 0, off_Alo = 0, off_Athi = 0, off_Atlo = 0;
@@ -74,6 +77,7 @@ struct Ws {
     int* ctl;
     double* scal;
     double *Xm, *Ym, *Dm, *Xn, *Yn, *part, *G, *Rp, *R, *Pt, *work, *red, *T;
+    void* blk;
     void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
     float* tcpart;
     int *ozE1, *ozE2, *ozEr, *ozEc, *ozEb, *ozEs, *ozcnt;
@@ -100,6 +104,7 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.work = (double*)(b + P->off_work);
     w.red = (double*)(b + P->off_red);
     w.T = P->chol_inv ? (double*)(b + P->off_T) : nullptr;
+    w.blk = P->blocked ? (void*)(b + P->off_blk) : nullptr;
     const bool mixed = P->nprod > 0, split = P->nprod == 3;
     w.Ahi = mixed ? (void*)(b + P->off_Ahi) : nullptr;
     w.Alo = split ? (void*)(b + P->off_Alo) : nullptr;
@@ -181,20 +186,26 @@ struct TimedGroup {
 
 // C (M x l) = op(A) B through the split-K partial buffer when S > 1.  With
 // `timed`, the GEMM kernel launch is bracketed by a plan event pair.
+// Widths beyond kMaxEll run as column chunks of at most kMaxEll (each
+// chunk one pass over A), all inside the one timed group.
 int gemm_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, const double* A, int64_t lda,
               const double* B, int64_t ldb, double* C, int64_t ldc, int N, int S, int64_t kc, bool timed = false) {
     cudaStream_t s = P->stream;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-    if (S <= 1) {
-        PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, C, ldc, 1, K, 0, nullptr, s));
-        if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
-        return PBPQLP_OK;
-    }
+    const int nch = (N + kMaxEll - 1) / kMaxEll, cw = (N + nch - 1) / nch;
     const int64_t ps = M * P->ldp;
-    PBQ_TRY(launch_dgemm_skinny(transA, M, N, K, A, lda, B, ldb, w.part, P->ldp, S, kc, ps, nullptr, s));
+    for (int c0 = 0; c0 < N; c0 += cw) {
+        const int nc = N - c0 < cw ? N - c0 : cw;
+        if (S <= 1) {
+            PBQ_TRY(launch_dgemm_skinny(transA, M, nc, K, A, lda, B + c0, ldb, C + c0, ldc, 1, K, 0, nullptr, s));
+        } else {
+            PBQ_TRY(launch_dgemm_skinny(transA, M, nc, K, A, lda, B + c0, ldb, w.part + c0, P->ldp, S, kc, ps, nullptr,
+                                        s));
+            PBQ_TRY(launch_reduce_partials(M, nc, S, w.part + c0, ps, P->ldp, C + c0, ldc, nullptr, s));
+        }
+    }
     if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
-    PBQ_TRY(launch_reduce_partials(M, N, S, w.part, ps, P->ldp, C, ldc, nullptr, s));
     return PBPQLP_OK;
 }
 
@@ -204,27 +215,35 @@ int gemm_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, int64_t M, int64_t K, 
 int tc_pass(pbpqlp_plan_s* P, const Ws& w, bool transA, const double* Y, int64_t ldy, int N, double* C, int64_t ldc,
             bool timed = false) {
     cudaStream_t s = P->stream;
-    TcOperands op;
-    const TcGeom* g;
-    if (!transA) {
-        PBQ_TRY(launch_split_panel_t(P->n, N, Y, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s, P->tf32));
-        op.Ahi = w.Ahi; op.Alo = w.Alo; op.rows = P->m; op.K = P->n; op.lda = P->ldk_n;
-        op.Bhi = w.Bnhi; op.Blo = w.Bnlo; op.ldb = P->ldk_n;
-        g = &P->g_nn;
-    } else {
-        PBQ_TRY(launch_split_panel_t(P->m, N, Y, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s, P->tf32));
-        op.Ahi = w.Athi; op.Alo = w.Atlo; op.rows = P->n; op.K = P->m; op.lda = P->ldk_m;
-        op.Bhi = w.Bmhi; op.Blo = w.Bmlo; op.ldb = P->ldk_m;
-        g = &P->g_tn;
-    }
-    op.N = N;
-    op.tf32 = P->tf32 ? 1 : 0;
-    TcGeom gg = *g;
-    if (N != P->l) gg = tc_geometry(op.rows, op.K, N, P->num_sms, P->tf32);
-    if (gg.part_floats > g->part_floats) return PBPQLP_EINVAL;
     const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
-    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-    PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, C, ldc, w.status, s, ev.second, P->fault_stall));
+    // widths beyond kMaxEll: column chunks of the plan's chunk width; the
+    // timed group starts at the first product (after its panel split)
+    const int nch = (N + kMaxEll - 1) / kMaxEll, cw = (N + nch - 1) / nch;
+    for (int c0 = 0; c0 < N; c0 += cw) {
+        const int nc = N - c0 < cw ? N - c0 : cw;
+        TcOperands op;
+        const TcGeom* g;
+        if (!transA) {
+            PBQ_TRY(launch_split_panel_t(P->n, nc, Y + c0, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s, P->tf32));
+            op.Ahi = w.Ahi; op.Alo = w.Alo; op.rows = P->m; op.K = P->n; op.lda = P->ldk_n;
+            op.Bhi = w.Bnhi; op.Blo = w.Bnlo; op.ldb = P->ldk_n;
+            g = &P->g_nn;
+        } else {
+            PBQ_TRY(launch_split_panel_t(P->m, nc, Y + c0, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s, P->tf32));
+            op.Ahi = w.Athi; op.Alo = w.Atlo; op.rows = P->n; op.K = P->m; op.lda = P->ldk_m;
+            op.Bhi = w.Bmhi; op.Blo = w.Bmlo; op.ldb = P->ldk_m;
+            g = &P->g_tn;
+        }
+        op.N = nc;
+        op.tf32 = P->tf32 ? 1 : 0;
+        TcGeom gg = *g;
+        if (nc != P->cw) gg = tc_geometry(op.rows, op.K, nc, P->num_sms, P->tf32);
+        if (gg.part_floats > g->part_floats || gg.BN > g->BN) return PBPQLP_EINVAL;
+        const bool last = c0 + nc >= N;
+        if (c0 == 0 && ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+        PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, C + c0, ldc, w.status, s, last ? ev.second : nullptr,
+                                  P->fault_stall));
+    }
     return PBPQLP_OK;
 }
 
@@ -303,7 +322,8 @@ int orth(pbpqlp_plan_s* P, const Ws& w, int64_t rows, double* X, double* Y, int 
         if (P->chol_inv) {
             // dst = src R^{-1} = src T^T as an FP64-accurate digit product
             TimedGroup tc(P, PBPQLP_TIME_CHOL);
-            PBQ_TRY(launch_chol_inv(l, rows, w.G, w.Rp, w.T, w.status, w.ctl, pass, s));
+            if (P->blocked) PBQ_TRY(launch_chol_inv_blocked(l, rows, w.G, w.T, w.blk, w.status, w.ctl, pass, s));
+            else PBQ_TRY(launch_chol_inv(l, rows, w.G, w.Rp, w.T, w.status, w.ctl, pass, s));
             tc.end();
             TimedGroup ts(P, PBPQLP_TIME_SOLVE);
             OzOperand xd, yd;
@@ -339,6 +359,13 @@ int check_device_addressable(const void* p) {
     return PBPQLP_OK;
 }
 
+// Y (m x r, ld ldy) = Qa[:, :r] L[:r, :r] (both ld l).
+cudaError_t qa_times_l(int64_t m, int r, const double* Qa, const double* L, int l, double* Y, int64_t ldy,
+                       cudaStream_t s) {
+    if (r <= kMaxEll) return launch_dgemm_skinny(false, m, r, r, Qa, l, L, l, Y, ldy, 1, r, 0, nullptr, s);
+    return launch_dgemm_gen(false, false, m, r, r, 1.0, Qa, l, L, l, 0.0, Y, ldy, false, nullptr, 0, s);
+}
+
 int check_ws(pbpqlp_plan_t P, void* ws, size_t ws_bytes) {
     if (!ws || ws_bytes < P->total || ((uintptr_t)ws & 255u) != 0) return PBPQLP_EWORKSPACE;
     return PBPQLP_OK;
@@ -371,13 +398,24 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     *out = nullptr;
     const int64_t l64 = (int64_t)k + (int64_t)p;
     if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
-    if (l64 > m || l64 > n || l64 > kMaxEll) return PBPQLP_EINVAL;
+    if (l64 > m || l64 > n || l64 > kMaxEllBlocked) return PBPQLP_EINVAL;
     if (mode < PBPQLP_MODE_FP64 || mode > PBPQLP_MODE_FP64_EMU) return PBPQLP_EINVAL;
+    if (l64 > kMaxEll) {
+        // the blocked l x l steps need the digit-form Grams and solve and the cluster kernels
+        const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
+        const char* no = std::getenv("PBPQLP_NO_OZ_GRAM");
+        if ((nc && nc[0] == '1') || (no && no[0] == '1') || !qr_blocked_fits((int)l64)) return PBPQLP_EUNSUPPORTED;
+    }
     pbpqlp_plan_s* P = new (std::nothrow) pbpqlp_plan_s();
     if (!P) return PBPQLP_ENOMEM;
     P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->l = (int)l64;
     P->seed = seed; P->mode = mode; P->stream = (cudaStream_t)stream;
     P->ldp = round_up(P->l, 8);
+    P->blocked = P->l > kMaxEll;
+    {
+        const int nch = (P->l + kMaxEll - 1) / kMaxEll;
+        P->cw = (P->l + nch - 1) / nch;
+    }
     {
         const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
         P->cluster_chol = cholesky_cluster_fits(P->l) && !(nc && nc[0] == '1');
@@ -392,7 +430,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
             P->num_sms = sms;
     }
-    const int64_t slots = (int64_t)P->num_sms * dgemm_skinny_occupancy(P->l);
+    const int64_t slots = (int64_t)P->num_sms * dgemm_skinny_occupancy(P->cw);
     const int64_t mt = (m + kGemmBM - 1) / kGemmBM, nt = (n + kGemmBM - 1) / kGemmBM;
     const int64_t lt = (P->l + kGemmBM - 1) / kGemmBM;
     choose_split(mt, n, slots, &P->S_nn, &P->kc_nn);
@@ -405,7 +443,8 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     const int64_t ldp = P->ldp, l = P->l;
     int64_t part = (int64_t)P->S_nn * m * ldp;
     part = part > (int64_t)P->S_tn * n * ldp ? part : (int64_t)P->S_tn * n * ldp;
-    int64_t pg = (int64_t)(P->S_gm > P->S_gn ? P->S_gm : P->S_gn) * l * ldp;
+    // FP64 FMA Grams and R = Q^T D (split-K partials), only without the digit form
+    const int64_t pg = P->oz_gram ? 0 : (int64_t)(P->S_gm > P->S_gn ? P->S_gm : P->S_gn) * l * ldp;
     part = part > pg ? part : pg;
     const int64_t tiles = ((m + 63) / 64) * ((n + 63) / 64);   // residual partials of pbpqlp_error
     part = part > tiles ? part : tiles;
@@ -434,7 +473,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         pd = pd > P->og_qb.part_doubles ? pd : P->og_qb.part_doubles;
         {
             const char* nc = std::getenv("PBPQLP_NO_CLUSTER");
-            P->chol_inv = P->oz_gram && chol_inv_fits(P->l) && !(nc && nc[0] == '1');
+            P->chol_inv = P->oz_gram && (P->blocked || chol_inv_fits(P->l)) && !(nc && nc[0] == '1');
         }
         if (P->chol_inv) {
             P->og_tr_m = oz_geometry(m, (int)l, l, false, P->num_sms);
@@ -449,15 +488,16 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
             pd = pd > P->og_nn.part_doubles ? pd : P->og_nn.part_doubles;
             pd = pd > P->og_tn.part_doubles ? pd : P->og_tn.part_doubles;
         }
-        P->off_ozE1 = take(sizeof(int) * 256);
-        P->off_ozE2 = take(sizeof(int) * 256);
+        const size_t ne = (size_t)(l > 256 ? l : 256);   // per-column exponents of an l-column panel
+        P->off_ozE1 = take(sizeof(int) * ne);
+        P->off_ozE2 = take(sizeof(int) * ne);
         // a panel as the transposed operand (l rows, K = m or n) or as rows (n rows, K = l)
         const int64_t mx = m > n ? m : n;
         const size_t sz = oz_digit_bytes(l, mx) > oz_digit_bytes(mx, l) ? oz_digit_bytes(l, mx) : oz_digit_bytes(mx, l);
         P->off_ozS1 = take(sz);
         P->off_ozS2 = take(sz);
         P->off_ozEb = take(sizeof(int) * (size_t)mx);
-        P->off_ozEs = take(sizeof(int) * 256);
+        P->off_ozEs = take(sizeof(int) * ne);
         P->off_ozpart = take(sizeof(double) * (size_t)pd);
         {
             int64_t mt = 0;
@@ -480,8 +520,8 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         P->fault_stall = (fault && std::strcmp(fault, "tc_stall") == 0) ? 1 : 0;
         P->ldk_n = tc_ld(n, P->tf32);
         P->ldk_m = tc_ld(m, P->tf32);
-        P->g_nn = tc_geometry(m, n, P->l, P->num_sms, P->tf32);
-        P->g_tn = tc_geometry(n, m, P->l, P->num_sms, P->tf32);
+        P->g_nn = tc_geometry(m, n, P->cw, P->num_sms, P->tf32);
+        P->g_tn = tc_geometry(n, m, P->cw, P->num_sms, P->tf32);
         const int64_t BN = P->g_nn.BN;
         const bool split = P->nprod == 3;
         const size_t es = P->tf32 ? 4 : 2;   // bytes per operand element
@@ -495,6 +535,10 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         if (split) P->off_Bmlo = take(es * (size_t)BN * P->ldk_m);
         const int64_t pf = P->g_nn.part_floats > P->g_tn.part_floats ? P->g_nn.part_floats : P->g_tn.part_floats;
         P->off_tcpart = take(sizeof(float) * (size_t)pf);
+    }
+    if (P->blocked) {
+        const size_t a = chol_inv_blocked_work_bytes(P->l), b = qr_blocked_work_bytes(P->l);
+        P->off_blk = take(a > b ? a : b);
     }
     P->total = off;
     *out = P;
@@ -557,7 +601,8 @@ int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* o
     tr.end();
     // [Ptil, Rtil] = qr(R^T), L = Rtil^T (Eq. 7); Qb = Pbar Ptil (Eq. 8)
     TimedGroup tq(P, PBPQLP_TIME_SMALLQR);
-    if (P->cluster_qr) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
+    if (P->blocked) PBQ_TRY(launch_qr_blocked(l, w.R, L, w.Pt, w.blk, s));
+    else if (P->cluster_qr) PBQ_TRY(launch_small_qr_cluster(l, w.R, L, w.Pt, s));
     else PBQ_TRY(launch_small_qr(l, w.R, L, w.Pt, w.work, s));
     tq.end();
     TimedGroup tb(P, PBPQLP_TIME_OTHER);
@@ -640,8 +685,13 @@ int pbpqlp_factor_csr(pbpqlp_plan_t P, const int64_t* rowptr, const int32_t* col
     auto product = [&](bool transA, const double* Y, double* C) -> int {
         const auto ev = next_events(P);
         if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
-        if (transA) PBQ_TRY(launch_csr_spmm(n, at.ptr, at.idx, at.val, Y, ldp, l, C, ldp, w.status, P->num_sms, s));
-        else PBQ_TRY(launch_csr_spmm(m, rowptr, colind, values, Y, ldp, l, C, ldp, w.status, P->num_sms, s));
+        for (int c0 = 0; c0 < l; c0 += P->cw) {
+            const int nc = l - c0 < P->cw ? l - c0 : P->cw;
+            if (transA)
+                PBQ_TRY(launch_csr_spmm(n, at.ptr, at.idx, at.val, Y + c0, ldp, nc, C + c0, ldp, w.status, P->num_sms, s));
+            else
+                PBQ_TRY(launch_csr_spmm(m, rowptr, colind, values, Y + c0, ldp, nc, C + c0, ldp, w.status, P->num_sms, s));
+        }
         if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
         return PBPQLP_OK;
     };
@@ -686,7 +736,7 @@ int pbpqlp_reconstruct(pbpqlp_plan_t P, const double* Qa, const double* L, const
     cudaStream_t s = P->stream;
     const int l = P->l;
     // T = Qa_r L_r (m x r), then Ahat = T Qb_r^T
-    PBQ_TRY(launch_dgemm_skinny(false, P->m, r, r, Qa, l, L, l, w.Ym, P->ldp, 1, r, 0, nullptr, s));
+    PBQ_TRY(qa_times_l(P->m, r, Qa, L, l, w.Ym, P->ldp, s));
     PBQ_TRY(launch_dgemm_nt(P->m, P->n, r, w.Ym, P->ldp, Qb, l, Ahat, ldh, nullptr, 0, 0, nullptr, nullptr, s));
     return PBPQLP_OK;
 }
@@ -730,7 +780,7 @@ int pbpqlp_error(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, const
         *rel_err = host[0] > 0.0 ? std::sqrt(d > 0.0 ? d : 0.0) / std::sqrt(host[0]) : 0.0;
     } else if (method == PBPQLP_ERR_RESIDUAL) {
         PBQ_TRY(launch_sumsq(m, n, A, f32, lda, nullptr, 0, w.red, w.scal + 0, s));
-        PBQ_TRY(launch_dgemm_skinny(false, m, r, r, Qa, l, L, l, w.Ym, ldp, 1, r, 0, nullptr, s));
+        PBQ_TRY(qa_times_l(m, r, Qa, L, l, w.Ym, ldp, s));
         int nb = 0;
         PBQ_TRY(launch_dgemm_nt(m, n, r, w.Ym, ldp, Qb, l, nullptr, 0, A, f32, lda, w.part, &nb, s));
         PBQ_TRY(launch_sum(nb, w.part, w.scal + 1, s));

@@ -47,7 +47,7 @@ def test_version_and_strerror(pq):
     (10, 10, 8, 3, 1),     # l > min(m, n)
     (10, 10, 2, -1, 1),    # p < 0
     (10, 10, 2, 1, -1),    # q < 0
-    (500, 500, 200, 30, 1),  # l > 224
+    (5000, 5000, 4090, 10, 1),  # l > 4096
 ])
 def test_plan_rejects_bad_sizes(pq, args):
     with pytest.raises(pq.PbpqlpError) as e:
@@ -101,3 +101,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         pq.load()
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         pq.pbpqlp_version()
+
+
+def test_plan_accepts_blocked_widths_and_rejects_them_without_digit_products(pq, monkeypatch):
+    # l > 224 takes the blocked l x l steps, which need the digit-form products
+    h = pq.pbpqlp_plan(2000, 2000, 990, 10, 1, seed=1, mode=pq.PBPQLP_MODE_FP64, stream=0)
+    assert pq.pbpqlp_workspace_bytes(h) > 3 * 1000 * 1000 * 8
+    pq.pbpqlp_plan_destroy(h)
+    monkeypatch.setenv("PBPQLP_NO_OZ_GRAM", "1")
+    with pytest.raises(pq.PbpqlpError) as e:
+        pq.pbpqlp_plan(2000, 2000, 990, 10, 1, seed=1, mode=pq.PBPQLP_MODE_FP64, stream=0)
+    assert e.value.status == pq.PBPQLP_EUNSUPPORTED
