@@ -49,6 +49,14 @@ WORKLOADS = {
                           mode="FP64", compare=None, emulated=True, paper_seconds=0.81,
                           desc="plain FP64, the paper's Table I runtime case n = 5000, d = 0.04n = 200 (k=190 p=10), "
                                "q=2; dense A = U diag(exp(-i/40)) V^T (the paper: spectrum immaterial for runtime)"),
+    "paper_t1_10000": dict(m=10000, n=10000, k=390, p=10, q=2, gen="svd", spectrum="exp", scale=50.0, rank_cap=800,
+                           mode="FP64", compare=None, emulated=True, paper_seconds=5.9,
+                           desc="plain FP64, the paper's Table I runtime case n = 10000, d = 0.04n = 400 (k=390 "
+                                "p=10), q=2; dense A = U diag(exp(-i/50)) V^T (blocked l x l steps)"),
+    "paper_t2_5000": dict(m=5000, n=5000, k=990, p=10, q=2, gen="svd", spectrum="exp", scale=125.0, rank_cap=2000,
+                          mode="FP64", compare=None, emulated=True, paper_seconds=4.3,
+                          desc="plain FP64, the paper's Table II runtime case n = 5000, d = 0.2n = 1000 (k=990 "
+                               "p=10), q=2; dense A = U diag(exp(-i/125)) V^T (blocked l x l steps)"),
     "csr_100k": dict(sparse=True, m=100000, n=100000, k=100, p=10, q=2, nnz_per_row=100.0, rank=110, support=150,
                      mode="FP64",
                      desc="sparse FP64 (CSR, Section III-C): 100000x100000, ~100 N(0,1) entries per row at uniform "

@@ -96,7 +96,13 @@ const char* pbpqlp_strerror(int status);
  * Create a plan for one factorization shape (Algorithm 3 inputs).
  *   m, n   : rows / columns of A (m, n >= 1).
  *   k, p   : target rank and oversampling; l = k + p must satisfy
- *            1 <= k <= l <= min(m, n) and l <= 224.
+ *            1 <= k <= l <= min(m, n) and l <= 4096.  Up to l = 224 the
+ *            l x l steps run in one thread-block cluster; beyond, they are
+ *            blocked (the Cholesky over 128-row diagonal blocks, the QR of
+ *            R^T in 32-column Householder panels), the products with A run
+ *            in column chunks of at most 224, and the plan needs the
+ *            digit-form Grams (PBPQLP_EUNSUPPORTED with PBPQLP_NO_OZ_GRAM=1
+ *            or PBPQLP_NO_CLUSTER=1).
  *   q      : power iterations, q >= 0 (q = 0 is the basic form, Eqs. 3-8).
  *   seed   : seed of the Philox4x32-10 Gaussian stream of Phi.
  *   mode   : PBPQLP_MODE_*.
@@ -146,6 +152,31 @@ int pbpqlp_generate_omega(pbpqlp_plan_t plan, double* omega);
 int pbpqlp_factor(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
                   void* workspace, size_t ws_bytes, const double* omega,
                   double* Qa, double* L, double* Qb);
+
+/*
+ * Algorithm 3 continued from a basis (Section III-B: the power iterations
+ * only need the current orthonormal basis Pbar).  Because every orth is a
+ * thin QR, the first l' columns of orth(C) are orth of the first l' columns
+ * of C, and A Pbar[:, :l'] is the first l' columns of A Pbar; so a run started
+ * from the first l columns of the basis of a wider run with the same Phi
+ * reproduces, up to rounding, the run with Phi's first l columns, and the
+ * q-th basis of a run is the basis a q-iteration run projects on.  This lets
+ * a caller keep one trajectory and branch off it (the learned (q, p)
+ * proposer continues its q = 0 sketch instead of starting over).
+ *   pbar0     : optional device n x l basis with orthonormal columns, leading
+ *               dimension ld_pbar0 >= l (e.g. the first l columns of a wider
+ *               basis).  It replaces Phi, Eq. 3 and the first orth (Eq. 4);
+ *               the plan's q power iterations follow.  NULL: start from the
+ *               plan's Phi exactly as pbpqlp_factor.
+ *   pbar_out  : optional device n x l (contiguous) output: the basis after the
+ *               power iterations, the one Eq. 5 projects on.
+ *   Qa, L, Qb : as pbpqlp_factor; all three NULL stops after the power
+ *               iterations (pbar_out then required): no projection pass.
+ * Workspace, asynchrony and status as pbpqlp_factor.
+ */
+int pbpqlp_factor_from(pbpqlp_plan_t plan, const void* A, int64_t lda, int a_dtype,
+                       void* workspace, size_t ws_bytes, const double* pbar0, int64_t ld_pbar0,
+                       double* pbar_out, double* Qa, double* L, double* Qb);
 
 /*
  * One product of Algorithm 3 on its own (Eq. 3 / Eq. 5): C = A Y (trans = 0;

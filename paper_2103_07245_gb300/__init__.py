@@ -85,6 +85,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_generate_omega.restype = ci
     L.pbpqlp_factor.argtypes = [vp, vp, i64, ci, vp, sz, vp, vp, vp, vp]
     L.pbpqlp_factor.restype = ci
+    L.pbpqlp_factor_from.argtypes = [vp, vp, i64, ci, vp, sz, vp, i64, vp, vp, vp, vp]
+    L.pbpqlp_factor_from.restype = ci
     L.pbpqlp_csr_workspace_bytes.argtypes = [vp, i64]
     L.pbpqlp_csr_workspace_bytes.restype = sz
     L.pbpqlp_factor_csr.argtypes = [vp, vp, vp, vp, i64, vp, sz, vp, vp, vp, vp]
@@ -212,6 +214,12 @@ def pbpqlp_generate_omega(plan, omega):
 def pbpqlp_factor(plan, A, lda, a_dtype, workspace, ws_bytes, omega, Qa, L, Qb):
     _check(load().pbpqlp_factor(plan, _ptr(A), int(lda), int(a_dtype), _ptr(workspace), int(ws_bytes),
                                 _ptr(omega), _ptr(Qa), _ptr(L), _ptr(Qb)), "pbpqlp_factor")
+
+
+def pbpqlp_factor_from(plan, A, lda, a_dtype, workspace, ws_bytes, pbar0, ld_pbar0, pbar_out, Qa, L, Qb):
+    _check(load().pbpqlp_factor_from(plan, _ptr(A), int(lda), int(a_dtype), _ptr(workspace), int(ws_bytes),
+                                     _ptr(pbar0), int(ld_pbar0), _ptr(pbar_out), _ptr(Qa), _ptr(L), _ptr(Qb)),
+           "pbpqlp_factor_from")
 
 
 def pbpqlp_csr_workspace_bytes(plan, nnz) -> int:
@@ -433,6 +441,24 @@ class Plan:
         Qa, L, Qb = out if out is not None else self.outputs(self.workspace.device)
         pbpqlp_factor(self.handle, A, A.stride(0), a_dtype, self.workspace, self.ws_bytes, omega, Qa, L, Qb)
         return Qa, L, Qb
+
+    def factor_from(self, A, pbar0=None, pbar_out=False, out=None, iterations_only=False):
+        """Algorithm 3 continued from pbar0 (n x >= l, its first l columns are used),
+        or from Phi when pbar0 is None.  Returns (Qa, L, Qb, Pbar) with Pbar the basis
+        after the power iterations when pbar_out is true (else None); with
+        iterations_only the run stops there and Qa, L, Qb are None."""
+        import torch
+        a_dtype = PBPQLP_F32 if A.dtype == torch.float32 else PBPQLP_F64
+        dev = self.workspace.device
+        pb = torch.empty(self.n, self.l, dtype=torch.float64, device=dev) if (pbar_out or iterations_only) else None
+        if iterations_only:
+            Qa = L = Qb = None
+        else:
+            Qa, L, Qb = out if out is not None else self.outputs(dev)
+        ld0 = 0 if pbar0 is None else pbar0.stride(0)
+        pbpqlp_factor_from(self.handle, A, A.stride(0), a_dtype, self.workspace, self.ws_bytes, pbar0, ld0, pb,
+                           Qa, L, Qb)
+        return Qa, L, Qb, pb
 
     def factor_csr(self, rowptr, colind, values, omega=None, out=None):
         """Sparse A in CSR form (rowptr int64 [m+1], colind int32 [nnz], values FP64 [nnz], on the device)."""

@@ -563,19 +563,27 @@ namespace {
 
 // Algorithm 3 on the plan's workspace, with `product(transA, Y, C)` forming
 // C = A Y (transA false, m rows) or C = A^T Y (n rows) for the plan's A.
+// With pbar0 the run starts from that n x l basis (leading dimension ld0)
+// in place of Phi, Eq. 3 and the first orth; pbar_out (optional) receives the
+// basis after the power iterations; with Qa, L and Qb all null the run stops
+// there (no projection pass).
 template <class Product>
 int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* omega, double* Qa, double* L,
-               double* Qb) {
+               double* Qb, const double* pbar0 = nullptr, int64_t ld0 = 0, double* pbar_out = nullptr) {
     cudaStream_t s = P->stream;
     const int64_t m = P->m, n = P->n, ldp = P->ldp;
     const int l = P->l;
     int rc = PBPQLP_OK;
-    // Phi (m x l)
-    if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
-    else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
-    // C = A^T Phi (Eq. 3); Pbar = orth(C) (Eq. 4)
-    if ((rc = product(true, w.Xm, w.Xn))) return rc;
-    if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
+    if (pbar0) {
+        PBQ_TRY(copy2d(pbar0, ld0, w.Xn, ldp, n, l, s));
+    } else {
+        // Phi (m x l)
+        if (omega) PBQ_TRY(copy2d(omega, l, w.Xm, ldp, m, l, s));
+        else PBQ_TRY(launch_gaussian(P->seed, m, l, w.Xm, ldp, s));
+        // C = A^T Phi (Eq. 3); Pbar = orth(C) (Eq. 4)
+        if ((rc = product(true, w.Xm, w.Xn))) return rc;
+        if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
+    }
     // power iterations with an orth after every product (Section III-B)
     for (int it = 0; it < P->q; ++it) {
         if ((rc = product(false, w.Xn, w.Xm))) return rc;
@@ -583,6 +591,8 @@ int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* o
         if ((rc = product(true, w.Xm, w.Xn))) return rc;
         if ((rc = orth(P, w, n, w.Xn, w.Yn, P->S_gn, P->kc_gn))) return rc;
     }
+    if (pbar_out) PBQ_TRY(copy2d(w.Xn, ldp, pbar_out, l, n, l, s));
+    if (!Qa && !L && !Qb) return PBPQLP_OK;
     // D = A Pbar (Eq. 5); [Q, R] = qr(D) (Eq. 6) with R = Q^T D
     if ((rc = product(false, w.Xn, w.Dm))) return rc;
     PBQ_TRY(copy2d(w.Dm, ldp, w.Xm, ldp, m, l, s));
@@ -625,9 +635,13 @@ int run_factor(pbpqlp_plan_s* P, const Ws& w, Product&& product, const double* o
 
 extern "C" {
 
-int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
-                  const double* omega, double* Qa, double* L, double* Qb) {
-    if (!P || !Av || !Qa || !L || !Qb || lda < P->n) return PBPQLP_EINVAL;
+static int factor_impl(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
+                       const double* omega, const double* pbar0, int64_t ld0, double* pbar_out, double* Qa, double* L,
+                       double* Qb) {
+    const bool outs = Qa || L || Qb;
+    if (!P || !Av || lda < P->n) return PBPQLP_EINVAL;
+    if (outs ? !(Qa && L && Qb) : !pbar_out) return PBPQLP_EINVAL;
+    if (pbar0 && ld0 < P->l) return PBPQLP_EINVAL;
     const bool mixed = P->nprod > 0;
     if ((mixed || P->emu) ? (a_dtype != PBPQLP_F64 && a_dtype != PBPQLP_F32) : a_dtype != PBPQLP_F64)
         return PBPQLP_EUNSUPPORTED;
@@ -651,7 +665,18 @@ int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, voi
         return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
                       : gemm_pass(P, w, false, m, n, A, lda, Y, ldp, C, ldp, l, P->S_nn, P->kc_nn, true);
     };
-    return run_factor(P, w, product, omega, Qa, L, Qb);
+    return run_factor(P, w, product, omega, Qa, L, Qb, pbar0, ld0, pbar_out);
+}
+
+int pbpqlp_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
+                  const double* omega, double* Qa, double* L, double* Qb) {
+    if (!Qa || !L || !Qb) return PBPQLP_EINVAL;
+    return factor_impl(P, Av, lda, a_dtype, workspace, ws_bytes, omega, nullptr, 0, nullptr, Qa, L, Qb);
+}
+
+int pbpqlp_factor_from(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, void* workspace, size_t ws_bytes,
+                       const double* pbar0, int64_t ld_pbar0, double* pbar_out, double* Qa, double* L, double* Qb) {
+    return factor_impl(P, A, lda, a_dtype, workspace, ws_bytes, nullptr, pbar0, ld_pbar0, pbar_out, Qa, L, Qb);
 }
 
 size_t pbpqlp_csr_workspace_bytes(pbpqlp_plan_t P, int64_t nnz) {

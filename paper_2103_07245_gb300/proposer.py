@@ -4,16 +4,19 @@ Every numerical step runs in the library's kernels (factorizations, feature
 extraction, MLP forward / backward / AdamW, the a-posteriori estimator); this
 module only moves torch tensors between those calls.
 
-- Labels come from the method itself: each training matrix is factored for
-  every q in {0..4} and p in {5, 10, 20}; the label is the cheapest pair
-  whose relative Frobenius error is <= 1.5 x the optimal tail
-  ||sigma_{k+1:}|| / ||A||_F (with a 10% margin).  Cost is what the guarded
-  proposal pays after its (q = 0, p = 20) sketch: nothing for (0, 20) itself,
-  else (2q + 2)(k + p), passes over A times panel width.
-  The error is read through the identity ||A - A_k||^2 = ||A||^2 - ||L_k||^2
-  of Eq. 8 (FP64 factors).
+- Labels come from the method itself, one trajectory per training matrix:
+  the (q = 0, p = 20) sketch's basis is iterated to q = 4 with
+  pbpqlp_factor_from, and every (q, p), q in {0..4}, p in {5, 10, 20},
+  projects the first k + p columns of the q-th basis (the thin-QR prefix
+  property makes that the (q, p) run with the sketch's Phi prefix).  The
+  label is the cheapest pair whose relative Frobenius error is <= 1.5 x the
+  optimal tail ||sigma_{k+1:}|| / ||A||_F (with a 10% margin).  Cost is what
+  the guarded proposal pays after its sketch: nothing for (0, 20) itself,
+  else (2q + 1)(k + p), passes over A times panel width.  Errors through the
+  identity ||A - A_k||^2 = ||A||^2 - ||L_k||^2 of Eq. 8 (pbpqlp_error).
 - Features: pbpqlp_features on the L-values of the (q = 0, p = 20) sketch.
-- Guarded proposal: the pair the network proposes is run, its error is
+- Guarded proposal: the sketch's trajectory is continued to the proposed
+  (q, p) from the first k + p columns of its basis, the result's error is
   estimated with Gaussian probes (pbpqlp_error, PBPQLP_ERR_PROBES) and, when
   the estimate misses the caller's tolerance, the plain method with fixed
   (q = 2, p = 10) is run instead.
@@ -105,54 +108,67 @@ def features(Ls, ls, ks, ms, ns, device="cuda"):
     return F
 
 
-def _batched_errors(As, ks, p, q, seed, normA2):
-    """Rank-k relative errors of the batched FP64 factorization with (p, q)."""
-    import torch
-    ms = [a.shape[0] for a in As]
-    ns = [a.shape[1] for a in As]
-    old = os.environ.get("PBPQLP_BATCH_NO_GRAPH")
-    os.environ["PBPQLP_BATCH_NO_GRAPH"] = "1"       # one-shot batches: launch eagerly
-    try:
-        B = pq.Batch(ms, ns, ks, p, q, seed)
-    finally:
-        if old is None:
-            del os.environ["PBPQLP_BATCH_NO_GRAPH"]
-        else:
-            os.environ["PBPQLP_BATCH_NO_GRAPH"] = old
-    Qa, L, Qb = B.factor(As)
-    rc, _ = B.sync_status()
-    errs = []
-    for i, k in enumerate(ks):
-        lk2 = float(torch.sum(L[i][:k, :k] ** 2))
-        errs.append(math.sqrt(max(normA2[i] - lk2, 0.0) / normA2[i]))
-    return errs, L, rc
-
-
 MARGIN = 1.1   # labels and the estimator check keep 10% below the tolerance
+P_SKETCH = 20  # oversampling of the q = 0 sketch the features come from
+
+
+def sketch(A, k, seed):
+    """The (q = 0, p = 20) sketch: its factors and its basis Pbar (n x (k + 20)),
+    the start of every trajectory below (2 passes over A)."""
+    plan = pq.Plan(A.shape[0], A.shape[1], k, P_SKETCH, 0, seed)
+    Qa, L, Qb, Pbar = plan.factor_from(A, pbar_out=True)
+    return plan, (Qa, L, Qb), Pbar
+
+
+def trajectory_errors(A, k, seed):
+    """Rank-k relative errors err[q][p] for q in Q_CHOICES, p in P_CHOICES from
+    ONE trajectory: the sketch's basis is iterated to q = 4 (two passes per
+    iteration), and (q, p) projects the first k + p columns of the q-th basis
+    (one pass each).  By the thin-QR prefix property this is, up to rounding,
+    the (q, p) run with the first k + p columns of the sketch's Phi.  Errors
+    through the identity of Eq. 8 (pbpqlp_error, PBPQLP_ERR_IDENTITY).
+    Returns (err, L of the sketch, passes over A)."""
+    m, n = A.shape
+    plan0, (Qa, L0, Qb), P0 = sketch(A, k, seed)
+    err = np.zeros((len(Q_CHOICES), len(P_CHOICES)))
+    err[0, P_CHOICES.index(P_SKETCH)] = plan0.error(A, Qa, L0, Qb, k, method=pq.PBPQLP_ERR_IDENTITY)
+    step = pq.Plan(m, n, k, P_SKETCH, 1, seed)
+    bases = [P0]
+    for _ in Q_CHOICES[1:]:
+        bases.append(step.factor_from(A, pbar0=bases[-1], iterations_only=True)[3])
+    proj = {p: (plan0 if p == P_SKETCH else pq.Plan(m, n, k, p, 0, seed)) for p in P_CHOICES}
+    passes = 2 + 2 * (len(Q_CHOICES) - 1)
+    for qi in range(len(Q_CHOICES)):
+        for pi, p in enumerate(P_CHOICES):
+            if qi == 0 and p == P_SKETCH:
+                continue
+            plan = proj[p]
+            Qa, L, Qb, _ = plan.factor_from(A, pbar0=bases[qi][:, :k + p])
+            err[qi, pi] = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_IDENTITY)
+            passes += 1
+    return err, L0, passes
 
 
 def label(As, ks, tails, seed=0):
-    """Features of the (0, 20) sketch, the error table err[i][q][p] and the labels
-    (the cheapest pair with error <= 1.5 x tail / MARGIN)."""
-    import torch
-    normA2 = [float(torch.sum(a * a)) for a in As]
+    """Features of the (0, 20) sketch, the error table err[i][q][p] (one
+    trajectory per matrix) and the labels: the cheapest pair with error <=
+    1.5 x tail / MARGIN.  Cost is what the guarded proposal pays after its
+    sketch: nothing for (0, 20) itself, else (2q + 1)(k + p) (the continued
+    trajectory: q iterations and the projection, times the panel width)."""
     cnt = len(As)
     err = np.zeros((cnt, len(Q_CHOICES), len(P_CHOICES)))
-    Lsk = None
-    for qi, q in enumerate(Q_CHOICES):
-        for pi, p in enumerate(P_CHOICES):
-            e, L, rc = _batched_errors(As, ks, p, q, seed, normA2)
-            err[:, qi, pi] = e
-            if q == 0 and p == 20:
-                Lsk = L
-    F = features(Lsk, [k + 20 for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
+    Ls = []
+    for i, (A, k) in enumerate(zip(As, ks)):
+        err[i], L0, _ = trajectory_errors(A, k, seed + i)
+        Ls.append(L0)
+    F = features(Ls, [k + P_SKETCH for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
     yq, yp = [], []
     for i, k in enumerate(ks):
         best, bc = None, None
         for qi, q in enumerate(Q_CHOICES):
             for pi, p in enumerate(P_CHOICES):
                 if err[i, qi, pi] <= 1.5 * tails[i] / MARGIN:
-                    c = 0 if (q, p) == (0, 20) else (2 * q + 2) * (k + p)
+                    c = 0 if (q, p) == (0, P_SKETCH) else (2 * q + 1) * (k + p)
                     if bc is None or c < bc:
                         best, bc = (qi, pi), c
         if best is None:
@@ -274,39 +290,76 @@ def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0, ckpt=None, ck
 
 
 def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
-    """Fixed (2, 10) against the guarded proposal on the same matrices.
+    """Fixed (2, 10) against the guarded proposal on the same matrices, with
+    GPU time (CUDA events on the current stream) and passes over A.
 
-    Passes over A: fixed = 2*2+2; proposal = 2 (the (0, 20) sketch) + 2q+2
-    (0 extra when the proposal is (0, 20) itself) + 6 when it falls back.
-    The caller's tolerance is 1.5 x the optimal tail; a proposal is kept when
-    its probe estimate is within tolerance / MARGIN."""
+    Guarded proposal per matrix: the (0, 20) sketch with its basis (2 passes),
+    the network's (q, p) from the sketch's features (one batched launch for
+    all matrices, its time shared out), the sketch's trajectory continued from
+    the first k + p columns of its basis (2q + 1 passes; none when the
+    proposal is (0, 20) itself), the probe estimate of the result's error
+    (1 pass), and fixed (2, 10) (6 passes) when the estimate misses the
+    caller's tolerance (1.5 x the optimal tail) / MARGIN."""
     import torch
-    normA2 = [float(torch.sum(a * a)) for a in As]
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        return out, (e0, e1)
+
     cnt = len(As)
-    e_fixed, _, _ = _batched_errors(As, ks, FIXED[1], FIXED[0], seed, normA2)
-    e0, L0, _ = _batched_errors(As, ks, 20, 0, seed, normA2)
-    F = features(L0, [k + 20 for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
-    qs, ps = prop.propose(F)
-    e_prop, passes, fallback = [], [], []
+    fixed_plans, t_fixed, e_fixed = [], [], []
+    for i, (A, k) in enumerate(zip(As, ks)):
+        plan = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)
+        (Qa, L, Qb), ev = timed(lambda: plan.factor(A))
+        t_fixed.append(ev)
+        e_fixed.append(plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_IDENTITY))
+        del plan
+    sk, t_sketch = [], []
+    for i, (A, k) in enumerate(zip(As, ks)):
+        out, ev = timed(lambda: sketch(A, k, seed + i))
+        sk.append(out)
+        t_sketch.append(ev)
+    (F, (qs, ps)), ev_prop = timed(lambda: (lambda F: (F, prop.propose(F)))(
+        features([o[1][1] for o in sk], [k + P_SKETCH for k in ks], ks, [a.shape[0] for a in As],
+                 [a.shape[1] for a in As])))
+    e_prop, passes, fallback, t_rest = [], [], [], []
     for i, (A, k) in enumerate(zip(As, ks)):
         q, p = qs[i], ps[i]
-        plan = pq.Plan(A.shape[0], A.shape[1], k, p, q, seed=seed + i)
-        Qa, L, Qb = plan.factor(A)
-        est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
-        e = math.sqrt(max(normA2[i] - float(torch.sum(L[:k, :k] ** 2)), 0.0) / normA2[i])
-        n_pass = 2 + (0 if (q, p) == (0, 20) else 2 * q + 2)
-        fb = est > 1.5 * tails[i] / MARGIN
-        if fb:
-            e = e_fixed[i]
-            n_pass += 2 * FIXED[0] + 2
+        plan0, (Qa0, L0, Qb0), P0 = sk[i]
+
+        def run(i=i, A=A, k=k, q=q, p=p, plan0=plan0, Qa0=Qa0, L0=L0, Qb0=Qb0, P0=P0):
+            if (q, p) == (0, P_SKETCH):
+                plan, Qa, L, Qb = plan0, Qa0, L0, Qb0
+            else:
+                plan = pq.Plan(A.shape[0], A.shape[1], k, p, q, seed + i)
+                Qa, L, Qb, _ = plan.factor_from(A, pbar0=P0[:, :k + p])
+            est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
+            fb = est > 1.5 * tails[i] / MARGIN
+            if fb:
+                plan = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)
+                Qa, L, Qb = plan.factor(A)
+            return plan, Qa, L, Qb, fb
+
+        (plan, Qa, L, Qb, fb), ev = timed(run)
+        t_rest.append(ev)
+        e = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_IDENTITY)   # bookkeeping, after the timed region
+        n_pass = 2 + (0 if (q, p) == (0, P_SKETCH) else 2 * q + 1) + 1 + (2 * FIXED[0] + 2 if fb else 0)
         e_prop.append(e)
         passes.append(n_pass)
         fallback.append(fb)
-        del plan
+    torch.cuda.synchronize()
+    ms = lambda ev: ev[0].elapsed_time(ev[1])
+    ms_fixed = np.array([ms(ev) for ev in t_fixed])
+    ms_prop = np.array([ms(a) + ms(b) for a, b in zip(t_sketch, t_rest)]) + ms(ev_prop) / cnt
     ok_fixed = np.array(e_fixed) <= 1.5 * np.array(tails)
     ok_prop = np.array(e_prop) <= 1.5 * np.array(tails)
     return {"fixed_success": float(ok_fixed.mean()), "proposer_success": float(ok_prop.mean()),
             "fixed_passes": float(2 * FIXED[0] + 2), "proposer_passes": float(np.mean(passes)),
+            "fixed_ms": float(ms_fixed.mean()), "proposer_ms": float(ms_prop.mean()),
+            "time_saved": float(1.0 - ms_prop.mean() / ms_fixed.mean()),
             "fallback_rate": float(np.mean(fallback)), "proposals": list(zip(qs, ps))}
 
 
@@ -326,6 +379,7 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=96)
     ap.add_argument("--max-dim", type=int, default=2048)
     ap.add_argument("--eval", type=int, default=64)
+    ap.add_argument("--eval-chunk", type=int, default=128)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--save", default=None)
@@ -353,9 +407,18 @@ def main(argv=None):
     t_train = time.time() - t0 - t_label
     if args.save:
         prop.save(args.save)
-    As, ks, tails = make_matrices(999_000 + args.seed, args.eval, fixed=(2048, 2048, 64), eval_mix=True)
-    res = evaluate(prop, As, ks, tails)
-    props = res.pop("proposals")
+    # held-out 2048 x 2048 matrices, k = 64, evaluated in chunks (each chunk's matrices held at once)
+    parts, props = [], []
+    for c0 in range(0, args.eval, args.eval_chunk):
+        cnt = min(args.eval_chunk, args.eval - c0)
+        As, ks, tails = make_matrices(999_000 + 7919 * args.seed + c0, cnt, fixed=(2048, 2048, 64), eval_mix=True)
+        r = evaluate(prop, As, ks, tails, seed=c0)
+        props += r.pop("proposals")
+        parts.append((cnt, r))
+        del As
+    tot = sum(c for c, _ in parts)
+    res = {key: sum(c * r[key] for c, r in parts) / tot for key in parts[0][1] if key != "time_saved"}
+    res["time_saved"] = 1.0 - res["proposer_ms"] / res["fixed_ms"]
     res.update({"train_matrices": int(F.shape[0]), "eval_matrices": args.eval, "loss_first": hist[0],
                 "loss_last": hist[-1], "label_q_hist": np.bincount(yq, minlength=5).tolist(),
                 "label_p_hist": np.bincount(yp, minlength=3).tolist(),
