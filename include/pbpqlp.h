@@ -74,6 +74,19 @@ enum {
     PBPQLP_MODE_FP64_EMU = 5
 };
 
+/* Flag OR-ed into the mode of pbpqlp_plan: stream A through the mixed and
+ * emulated products instead of holding whole converted copies of it (the
+ * pass-efficient setting of Section III-C, where A is stored externally and
+ * read once per pass).  Every pass splits (BF16 / TF32 modes) or digitises
+ * (MODE_FP64_EMU) one block of rows of A at a time into a staging area of
+ * about 512 MB (PBPQLP_STREAM_ROWS in the environment at plan creation sets
+ * the rows per block), so A may sit in pinned host memory larger than the
+ * device's memory.  C = A Y is written block by block; C = A^T Y adds the
+ * blocks' FP64 partial sums in block order, so results are deterministic but
+ * not bitwise those of the unstreamed plan.  MODE_FP64 reads A in place in
+ * every pass already and ignores the flag. */
+#define PBPQLP_STREAM_A 256
+
 /* Element type of A. */
 enum { PBPQLP_F64 = 0, PBPQLP_F32 = 1 };
 

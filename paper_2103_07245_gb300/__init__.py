@@ -27,6 +27,7 @@ PBPQLP_MODE_BF16X3 = 2
 PBPQLP_MODE_TF32 = 3
 PBPQLP_MODE_TF32X3 = 4
 PBPQLP_MODE_FP64_EMU = 5
+PBPQLP_STREAM_A = 256
 
 PBPQLP_F64 = 0
 PBPQLP_F32 = 1

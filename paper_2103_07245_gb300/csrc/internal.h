@@ -167,6 +167,10 @@ cudaError_t launch_sum(int n, const double* part, double* out, cudaStream_t s);
 // L-values |L_ii| into lv (l), out2[0] = |L_11|, out2[1] = #{i : |L_ii| > tol |L_11|} (as a double).
 cudaError_t launch_lvalues(int l, const double* L, double tol, double* lv, double* out2, cudaStream_t s);
 
+// dst += src for a rows x cols FP64 block (each element once; deterministic).
+cudaError_t launch_add2d(int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst, int64_t ldd,
+                         cudaStream_t s);
+
 // Copy a rows x cols FP64 block between leading dimensions.
 cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
                    cudaStream_t s);

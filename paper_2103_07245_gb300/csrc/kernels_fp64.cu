@@ -441,6 +441,25 @@ cudaError_t launch_lvalues(int l, const double* L, double tol, double* lv, doubl
     return cudaGetLastError();
 }
 
+__global__ void k_add2d(int64_t rows, int64_t cols, const double* __restrict__ src, int64_t lds,
+                        double* __restrict__ dst, int64_t ldd) {
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e - i * cols;
+        dst[i * ldd + j] += src[i * lds + j];
+    }
+}
+
+cudaError_t launch_add2d(int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst, int64_t ldd,
+                         cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    int64_t blocks = (rows * cols + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_add2d<<<(unsigned)blocks, 256, 0, s>>>(rows, cols, src, lds, dst, ldd);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t copy2d(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
                    cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;

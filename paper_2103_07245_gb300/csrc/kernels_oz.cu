@@ -918,9 +918,14 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     }
     g.KI = (int)((K + kOzBK - 1) / kOzBK);
     const int64_t T = g.tiles * g.KI;
-    // at least 16 iterations (32-deep chunks) per CTA: small products use
+    // at least min_it iterations (32-deep chunks) per CTA: small products use
     // fewer CTAs, with fewer partials to fix up
-    const int64_t want = (T + 15) / 16;
+    static const int64_t min_it = [] {
+        const char* v = std::getenv("PBPQLP_OZ_MIN_ITERS");
+        const long long x = v ? std::atoll(v) : 0;
+        return (int64_t)(x > 0 ? x : 16);
+    }();
+    const int64_t want = (T + min_it - 1) / min_it;
     g.G = (int)(want < num_sms ? want : num_sms);
     if (g.G < 1) g.G = 1;
     const int64_t share = (T + g.G - 1) / g.G;

