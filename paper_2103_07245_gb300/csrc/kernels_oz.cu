@@ -919,12 +919,10 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     g.KI = (int)((K + kOzBK - 1) / kOzBK);
     const int64_t T = g.tiles * g.KI;
     // at least min_it iterations (32-deep chunks) per CTA: small products use
-    // fewer CTAs, with fewer partials to fix up
-    static const int64_t min_it = [] {
-        const char* v = std::getenv("PBPQLP_OZ_MIN_ITERS");
-        const long long x = v ? std::atoll(v) : 0;
-        return (int64_t)(x > 0 ? x : 16);
-    }();
+    // fewer CTAs, with fewer partials to fix up.  Short contractions (the
+    // CholeskyQR solve and Qb, K = l) take 4, which measured 20% faster for
+    // them; long ones (Grams, passes over A) 16.
+    const int64_t min_it = g.KI <= 8 ? 4 : 16;
     const int64_t want = (T + min_it - 1) / min_it;
     g.G = (int)(want < num_sms ? want : num_sms);
     if (g.G < 1) g.G = 1;

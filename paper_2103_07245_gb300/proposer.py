@@ -17,9 +17,9 @@ module only moves torch tensors between those calls.
 - Features: pbpqlp_features on the L-values of the (q = 0, p = 20) sketch.
 - Guarded proposal: the sketch's trajectory is continued to the proposed
   (q, p) from the first k + p columns of its basis, the result's error is
-  estimated with Gaussian probes (pbpqlp_error, PBPQLP_ERR_PROBES) and, when
-  the estimate misses the caller's tolerance, the plain method with fixed
-  (q = 2, p = 10) is run instead.
+  taken a posteriori (pbpqlp_error: the identity of Eq. 8 by default, or
+  Gaussian probes) and, when it misses the caller's tolerance, the plain
+  method with fixed (q = 2, p = 10) is run instead.
 """
 import math
 import os
@@ -289,7 +289,7 @@ def train(prop, F, yq, yp, epochs=300, batch=256, lr=2e-3, seed=0, ckpt=None, ck
     return hist
 
 
-def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
+def evaluate(prop, As, ks, tails, seed=0, nprobes=24, guard="identity"):
     """Fixed (2, 10) against the guarded proposal on the same matrices, with
     GPU time (CUDA events on the current stream) and passes over A.
 
@@ -297,8 +297,10 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
     the network's (q, p) from the sketch's features (one batched launch for
     all matrices, its time shared out), the sketch's trajectory continued from
     the first k + p columns of its basis (2q + 1 passes; none when the
-    proposal is (0, 20) itself), the probe estimate of the result's error
-    (1 pass), and fixed (2, 10) (6 passes) when the estimate misses the
+    proposal is (0, 20) itself), the a-posteriori error of the result (1
+    pass: with guard "identity" the exact sqrt(||A||^2 - ||L_k||^2) / ||A||
+    of Eq. 8, which reads A once for ||A||_F; with guard "probes" the
+    Gaussian-probe estimate), and fixed (2, 10) (6 passes) when it misses the
     caller's tolerance (1.5 x the optimal tail) / MARGIN."""
     import torch
 
@@ -342,7 +344,10 @@ def evaluate(prop, As, ks, tails, seed=0, nprobes=24):
             else:
                 plan = cont
                 Qa, L, Qb, _ = plan.factor_from(A, pbar0=P0[:, :k + p])
-            est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
+            if guard == "probes":
+                est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_PROBES, nprobes=nprobes, probe_seed=99 + i)
+            else:
+                est = plan.error(A, Qa, L, Qb, k, method=pq.PBPQLP_ERR_IDENTITY)
             fb = est > 1.5 * tails[i] / MARGIN
             if fb:
                 plan = fixed
