@@ -442,14 +442,16 @@ int64_t pbpqlp_kernel_launch_count(void);
  * Diagnostic of the library's internal FP64 helpers (not part of the paper's
  * method): for each of the n doubles d[i] (device), writes the Newton-refined
  * reciprocal rcp[i] ~ 1/d[i] and reciprocal square root rsqrt[i] ~
- * 1/sqrt(d[i]) (device outputs) that the Cholesky and QR kernels use in
- * place of FP64 division and square root.  Positive normal inputs are within
- * 2 ulp of the correctly rounded results; every other input (zero, subnormal,
- * negative, Inf, NaN, and d >= 2^1023 for the reciprocal) takes CUDA's own
- * division / square root.  Asynchronous on `stream`; PBPQLP_EINVAL for n < 0
- * or null pointers with n > 0.
+ * 1/sqrt(d[i]) (device outputs) and, when rcp_gs is not NULL, the one-step
+ * Goldschmidt reciprocal rcp_gs[i] ~ 1/d[i] of the Cholesky pivot chain; the
+ * kernels use them in place of FP64 division and square root.  Positive
+ * normal inputs are within 2 ulp of the correctly rounded results; for every
+ * other input (zero, subnormal, negative, Inf, NaN, and d >= 2^1023 for the
+ * reciprocal) rcp and rsqrt take CUDA's own division / square root, while
+ * rcp_gs is meaningless there (its callers reject such pivots first).
+ * Asynchronous on `stream`; PBPQLP_EINVAL for n < 0 or null pointers with n > 0.
  */
-int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, void* stream);
+int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, double* rcp_gs, void* stream);
 
 #ifdef __cplusplus
 }

@@ -155,7 +155,7 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_set_timing_classes.restype = ci
     L.pbpqlp_read_timing_class.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.pbpqlp_read_timing_class.restype = ci
-    L.pbpqlp_newton_check.argtypes = [vp, i64, vp, vp, vp]
+    L.pbpqlp_newton_check.argtypes = [vp, i64, vp, vp, vp, vp]
     L.pbpqlp_newton_check.restype = ci
     _lib = L
     return L
@@ -347,9 +347,10 @@ def pbpqlp_kernel_launch_count() -> int:
     return int(load().pbpqlp_kernel_launch_count())
 
 
-def pbpqlp_newton_check(d, n, rcp, rsqrt, stream=None):
-    """The library's Newton-refined 1/d and 1/sqrt(d) for n device doubles (a diagnostic)."""
-    _check(load().pbpqlp_newton_check(_ptr(d), int(n), _ptr(rcp), _ptr(rsqrt), _stream(stream)),
+def pbpqlp_newton_check(d, n, rcp, rsqrt, rcp_gs=None, stream=None):
+    """The library's Newton-refined 1/d and 1/sqrt(d), and its one-step Goldschmidt 1/d,
+    for n device doubles (a diagnostic)."""
+    _check(load().pbpqlp_newton_check(_ptr(d), int(n), _ptr(rcp), _ptr(rsqrt), _ptr(rcp_gs), _stream(stream)),
            "pbpqlp_newton_check")
 
 

@@ -11,24 +11,27 @@
 // in CTA j % C at local column j / C, full length l in shared memory), so the
 // trailing updates, which hold nearly all the l^3 / 3 FMAs, are spread over
 // all C SMs.  Block t:
-//   (a) every CTA gathers the 16 x 16 diagonal block through distributed
-//       shared memory and factors it (one warp, redundantly: all CTAs take the
-//       same pivot decisions without communicating);
-//   (b) each CTA solves its own columns' block rows, R[t, j] = R_tt^{-T} S[t, j]
-//       (columns right of the block) and T[t, j] = R_tt^{-T} T[t, j];
-//   cluster barrier; each CTA copies block row t of R (columns right of the
-//   block) from the owners;
-//   (c) trailing updates of own columns: S[i][j] -= sum_k R[t,k][i] R[t,k][j]
-//       (a1 <= i <= j) and T[i][j] -= sum_k R[t,k][i] T[t,k][j] (i >= a1);
-//   cluster barrier.
-// FP64 has few lanes per SM on GB300 and long latencies, so the sequential
-// parts are kept short: the diagonal block is factored in LDL^T form (one
-// reciprocal per pivot, an FP32 seed refined by Newton-Raphson steps in FP64;
-// the square roots of all pivots come afterwards, in parallel), and the
-// block-row solve updates all remaining right-hand sides after each unknown
-// (two dependent operations per step).  Pivot thresholds and the shifted retry
-// (shifted CholeskyQR, Fukaya et al. 2020) follow the one-CTA kernel; ctl /
-// status conventions are the same.
+//   (a) every CTA factors the 16 x 16 diagonal block (four warps,
+//       redundantly: all CTAs take the same pivot decisions without
+//       communicating), which gives R_tt and T_tt = R_tt^{-T} at once (the
+//       identity beside it is eliminated along with it);
+//   (b) each CTA forms its own columns' block rows as small products,
+//       R[t, j] = T_tt S[t, j] (columns right of the block) and
+//       T[t, j] = T_tt T[t, j], and writes the R values into every CTA's
+//       block-row buffer (distributed shared memory); cluster barrier;
+//   (c1) the owners of block t+1's columns update them first and write them
+//       into every CTA's diagonal-block buffer; cluster barrier;
+//   (a) of block t+1 on warps 0-3, while warps 4-7 run (c2), the trailing
+//       updates of all other own columns: S[i][j] -= sum_k R[t,k][i] R[t,k][j]
+//       (a1 <= i <= j) and T[i][j] -= sum_k R[t,k][i] T[t,k][j] (i >= a1).
+// So the sequential pivot chain of the next block overlaps the trailing
+// update, every value crosses between CTAs as a store (no remote loads), and
+// a block costs two cluster barriers.  FP64 has few lanes per SM on GB300 and
+// long latencies: the pivot chain is LDL^T with one reciprocal per pivot (an
+// FP32 seed and one Goldschmidt step) and the square roots of all pivots come
+// afterwards, in parallel.  Pivot thresholds and the shifted retry (shifted
+// CholeskyQR, Fukaya et al. 2020) follow the one-CTA kernel; ctl / status
+// conventions are the same.
 #include <cooperative_groups.h>
 #include <cmath>
 #include <cstdint>
@@ -42,7 +45,7 @@ namespace pbq {
 
 namespace {
 constexpr int kCiCtasMax = 16;
-constexpr int kCiThreads = 512;
+constexpr int kCiThreads = 256;   // 8 warps: the block factor's 32 live doubles per lane fit in registers
 constexpr int kCiNb = 16;
 
 // Latencies measured on GB300: a dependent FP64 FMA takes 64 cycles, an FP64
@@ -59,6 +62,87 @@ constexpr int kCiNb = 16;
 // leading dimension ld) and T_tt (lower, into Tout, ld), makes one attempt,
 // and on a failed pivot sets *bstate = want + 1 (4 for a non-finite pivot,
 // with the status bit) instead of retrying.  It runs only if *bstate == want.
+//
+// Shared memory of a CTA: its columns of S (then R) and of T (ncol x l
+// each), two buffers of one block row of R for every column (the owners
+// write them into every CTA), the next diagonal block's columns (written by
+// their owners into every CTA), the factored diagonal block's R_tt and T_tt,
+// and the pivot thresholds.
+// Factor the 16 x 16 diagonal block in Dnx with 4 warps (threads t = 0..127,
+// one warp per SM sub-partition: GB300 issues FP64 at half a lane per clock
+// per sub-partition, so one warp alone would serialise the updates).  The
+// augmented block [S_tt | I] (16 x 32, in W) is eliminated by LDL^T row
+// operations: thread t owns column t % 32 (0..15 of S, 16..31 of I) in rows
+// t / 32 + 4r, r = 0..3.  Pivot p: every thread takes 1/d_p from the shared
+// row p (an FP32 seed and one Goldschmidt step), updates its rows below p
+// (row i -= (S[p][i] / d_p) row p; S only on and above the diagonal), and a
+// 128-thread barrier publishes row p + 1.  The S part ends as D U and the I
+// part as L^{-1} = U^{-T}, so R_tt = D^{1/2} U and T_tt = D^{-1/2} L^{-1}.
+// No branches on the data: a failed pivot (not above its threshold, or not
+// finite) is recorded and the block discarded.  Rows and columns past the
+// block's width nb are padded with identity.  Not inlined: inlined at both
+// call sites, its row array was given a stack frame.
+__device__ __noinline__ void chol_block16(double* __restrict__ W, const double* __restrict__ Dnx,
+                                          const double* __restrict__ thr, int a0, int nb, double* __restrict__ Rtt,
+                                          double* __restrict__ Ttt, int* s_fail, int t) {
+    const int c = t & 31, w = t >> 5;
+    const bool idl = c >= kCiNb;
+    double v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = w + 4 * r;
+        double x;
+        if (idl) x = (i == c - kCiNb) ? 1.0 : 0.0;
+        else if (c < nb) x = (i <= c) ? Dnx[c * kCiNb + i] : 0.0;
+        else x = (i == c) ? 1.0 : 0.0;
+        v[r] = x;
+        W[i * 32 + c] = x;
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    int f = 0;
+#pragma unroll
+    for (int p = 0; p < kCiNb; ++p) {
+        const double d = W[p * 32 + p];
+        const double th = p < nb ? thr[a0 + p] : 0.0;
+        const int fp = !isfinite(d) ? 2 : (!(d > th) ? 1 : 0);
+        f = f ? f : fp;
+        const double cp = rcp_gs(d);
+        const double rowp = W[p * 32 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = w + 4 * r;
+            if (i > p) {
+                const double mult = W[p * 32 + i] * cp;   // L[i][p] = S[p][i] / d_p
+                if (idl || c >= i) v[r] = fma(-mult, rowp, v[r]);
+                W[i * 32 + c] = v[r];
+            }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = w + 4 * r;
+        const double di = W[i * 32 + i];
+        const double rs = rsqrt_nr(di);
+        if (!idl) Rtt[i * kCiNb + c] = (i < c) ? v[r] * rs : (i == c ? di * rs : 0.0);
+        else Ttt[i * kCiNb + (c - kCiNb)] = v[r] * rs;   // row i of L^{-1} scaled by 1/sqrt(d_i)
+    }
+    if (t == 0) *s_fail = f;
+}
+
+// Own S columns of block rows [a0, a0 + 16) into Dnx of every CTA of the
+// cluster (rows <= column; the rest 0).
+__device__ __forceinline__ void push_diag16(cg::cluster_group& cluster, const double* __restrict__ Sown, double* Dnx,
+                                            int l, int ncol, int C, int rank, int a0, int tid, int nth) {
+    const int a1 = min(l, a0 + kCiNb);
+    for (int e = tid; e < ncol * kCiNb; e += nth) {
+        const int jl = e / kCiNb, i = e - jl * kCiNb, j = jl * C + rank;
+        if (j < a0 || j >= a1) continue;
+        const double v = (a0 + i <= j) ? Sown[(int64_t)jl * l + a0 + i] : 0.0;
+        for (int r = 0; r < C; ++r) cluster.map_shared_rank(Dnx, r)[(j - a0) * kCiNb + i] = v;
+    }
+}
+
 template <bool kBlock>
 __global__ void __launch_bounds__(kCiThreads)
 k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __restrict__ Rp,
@@ -78,9 +162,12 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     extern __shared__ double smi[];
     double* Sown = smi;                                  // ncol x l: own columns of S (then R)
     double* Town = Sown + (int64_t)ncol * l;             // ncol x l: own columns of T
-    double* Rbuf = Town + (int64_t)ncol * l;             // 16 x l: block row t of R
-    double* Rtt = Rbuf + (int64_t)kCiNb * l;             // 16 x 16: factored diagonal block (upper), [p][k]
-    double* Rinv = Rtt + kCiNb * kCiNb;                  // 16: 1 / R_tt[k][k]
+    double* Rbuf = Town + (int64_t)ncol * l;             // 2 x 16 x l: block row of R, by block parity
+    double* Dnx = Rbuf + (int64_t)2 * kCiNb * l;         // 16 x 16: next diagonal block, [column][row]
+    double* Rtt = Dnx + kCiNb * kCiNb;                   // 16 x 16: R_tt, [row][column]
+    double* Ttt = Rtt + kCiNb * kCiNb;                   // 16 x 16: T_tt = R_tt^{-T}, [row][column]
+    double* Wfb = Ttt + kCiNb * kCiNb;                   // 16 x 32: the block factor's working rows
+    double* thr = Wfb + kCiNb * 32;                      // l: pivot thresholds
     __shared__ int s_fail;
     __shared__ double s_shift;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -101,132 +188,94 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
             Sown[e] = sv;
             Town[e] = tv;
         }
+        // the shifted retry (attempt 1, or want 1 in block mode) only asks for d > 0
+        for (int i = tid; i < l; i += nth)
+            thr[i] = (attempt == 0 && !(kBlock && want == 1))
+                         ? tau * (kBlock ? gdiag[(int64_t)i * (ld + 1)] : G[(int64_t)i * l + i]) : 0.0;
         fail = 0;
-        cluster.sync();
-        for (int t = 0; t < nblk; ++t) {
+        __syncthreads();
+        push_diag16(cluster, Sown, Dnx, l, ncol, C, rank, 0, tid, nth);
+        cluster.sync();                         // Dnx holds diagonal block 0 everywhere
+        if (warp < 4) chol_block16(Wfb, Dnx, thr, 0, min(l, kCiNb), Rtt, Ttt, &s_fail, tid);
+        __syncthreads();
+        fail = s_fail;
+        for (int t = 0; t < nblk && !fail; ++t) {
             const int a0 = t * kCiNb, a1 = min(l, a0 + kCiNb), nb = a1 - a0;
-            // (a) gather and factor the diagonal block (warp 0 of every CTA).  LDL^T
-            // form: step p needs only 1/d_p (the chain from one pivot to the
-            // next is a reciprocal and two FMAs); the rows of R are scaled by
-            // 1/sqrt(d_p) afterwards, all pivots at once.
-            if (warp == 0) {
-                double s[kCiNb];
-                const int j = a0 + lane;
-                double thr_mine = 0.0, d_mine = 1.0;
-                if (lane < nb) {
-                    const double* col = cluster.map_shared_rank(Sown, j % C) + (int64_t)(j / C) * l;
+            const int a2 = min(l, a1 + kCiNb);
+            double* Rb = Rbuf + (int64_t)(t & 1) * kCiNb * l;
+            // (b) block row t of R for own columns right of the block, R[t, j] = T_tt S[t, j], and
+            // T[t, j] = T_tt T[t, j] for own columns left of its end; R_tt into the block's own columns
+            // (at most 4 items per thread: 2 ncol 16 <= 4 x 256 for l <= 256 on 8 CTAs)
+            double yv[4];
 #pragma unroll
-                    for (int i = 0; i < kCiNb; ++i) s[i] = (i <= lane) ? col[a0 + i] : 0.0;
-                    // the shifted retry (attempt 1, or want 1 in block mode) only asks for d > 0
-                    if (attempt == 0 && !(kBlock && want == 1))
-                        thr_mine = tau * (kBlock ? gdiag[(int64_t)j * (ld + 1)] : G[(int64_t)j * l + j]);
-                } else {
+            for (int rep = 0; rep < 4; ++rep) {
+                const int e = tid + rep * nth;
+                const int side = e / (ncol * kCiNb), r = e - side * ncol * kCiNb;
+                const int jl = r / kCiNb, k = r - jl * kCiNb, j = jl * C + rank;
+                double y = 0.0;
+                if (side < 2 && j < l && k < nb && (side == 0 ? j >= a1 : j < a1)) {
+                    const double* x = (side == 0 ? Sown : Town) + (int64_t)jl * l + a0;
 #pragma unroll
-                    for (int i = 0; i < kCiNb; ++i) s[i] = 0.0;
+                    for (int i = 0; i < kCiNb; ++i)
+                        if (i <= k) y = fma(Ttt[k * kCiNb + i], x[i], y);
                 }
-                int f = 0;
+                yv[rep] = y;
+            }
+            __syncthreads();                    // every x read before any is overwritten
 #pragma unroll
-                for (int p = 0; p < kCiNb; ++p) {
-                    if (p < nb && f == 0) {
-                        const double d = __shfl_sync(0xffffffffu, s[p], p);
-                        const double thr = __shfl_sync(0xffffffffu, thr_mine, p);
-                        f = !isfinite(d) ? 2 : (!(d > thr) ? 1 : 0);
-                        if (f == 0) {
-                            const double c = rcp_nr(d);
-                            if (lane == p) d_mine = d;
-                            const double lk = s[p] * c;   // L[lane][p] = S[p][lane] / d_p
-#pragma unroll
-                            for (int i = p + 1; i < kCiNb; ++i) {
-                                const double spi = __shfl_sync(0xffffffffu, s[p], i);
-                                if (lane >= i) s[i] -= spi * lk;
-                            }
-                        }
-                    }
+            for (int rep = 0; rep < 4; ++rep) {
+                const int e = tid + rep * nth;
+                const int side = e / (ncol * kCiNb), r = e - side * ncol * kCiNb;
+                const int jl = r / kCiNb, k = r - jl * kCiNb, j = jl * C + rank;
+                if (side >= 2 || j >= l || k >= nb) continue;
+                if (side == 0 && j >= a1) {
+                    Sown[(int64_t)jl * l + a0 + k] = yv[rep];
+                    for (int rr = 0; rr < C; ++rr) cluster.map_shared_rank(Rb, rr)[(int64_t)k * l + j] = yv[rep];
+                } else if (side == 0 && j >= a0) {
+                    Sown[(int64_t)jl * l + a0 + k] = Rtt[k * kCiNb + (j - a0)];
+                } else if (side == 1 && j < a1) {
+                    Town[(int64_t)jl * l + a0 + k] = yv[rep];
                 }
-                if (f == 0) {
-                    // R[p][k] = S_p[k] / sqrt(d_p) (p < k), R[k][k] = sqrt(d_k)
-                    const double rs = rsqrt_nr(d_mine);
+            }
+            cluster.sync();                     // block row t of R is in every CTA's Rb
+            if (a1 >= l) break;
+            // (c1) own columns of block t+1: their rows [a1, j] first, then into every CTA's Dnx
+            for (int e = tid; e < ncol * kCiNb; e += nth) {
+                const int jl = e / kCiNb, i = a1 + (e - jl * kCiNb), j = jl * C + rank;
+                if (j < a1 || j >= a2 || i > j) continue;
+                double* col = Sown + (int64_t)jl * l;
+                double acc = col[i];
 #pragma unroll
-                    for (int p = 0; p < kCiNb; ++p) {
-                        const double rsp = __shfl_sync(0xffffffffu, rs, p);
-                        if (lane < nb) Rtt[p * kCiNb + lane] = (p < lane) ? s[p] * rsp : (p == lane ? d_mine * rs : 0.0);
-                    }
-                    if (lane < nb) Rinv[lane] = rs;
-                }
-                if (lane == 0) s_fail = f;
+                for (int k = 0; k < kCiNb; ++k)
+                    if (k < nb) acc = fma(-Rb[(int64_t)k * l + i], col[a0 + k], acc);
+                col[i] = acc;
             }
             __syncthreads();
-            fail = s_fail;
-            if (fail) break;   // every CTA factored the same block: same decision everywhere
-            // (b) block-row solves R_tt^T y = x on own columns (one thread per column):
-            // after each unknown all later right-hand sides are updated at once
-            if (tid < 2 * ncol) {
-                const bool right = tid >= ncol;
-                const int jl = right ? tid - ncol : tid;
-                const int j = jl * C + rank;
-                if (j < l && (right ? (j < a1) : (j >= a1))) {
-                    double* x = (right ? Town : Sown) + (int64_t)jl * l + a0;
-                    double acc[kCiNb];
-#pragma unroll
-                    for (int k = 0; k < kCiNb; ++k) acc[k] = (k < nb) ? x[k] : 0.0;
-#pragma unroll
-                    for (int p = 0; p < kCiNb; ++p) {
-                        if (p < nb) {
-                            const double y = acc[p] * Rinv[p];
-                            acc[p] = y;
-#pragma unroll
-                            for (int k = p + 1; k < kCiNb; ++k) acc[k] -= Rtt[p * kCiNb + k] * y;
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < kCiNb; ++k)
-                        if (k < nb) x[k] = acc[k];
-                }
-            }
-            cluster.sync();   // block row t of R is final in its owners
-            // copy block row t of R, columns a1 .. l-1, from the owners
-            const int w1 = l - a1;
-            for (int e = tid; e < nb * w1; e += nth) {
-                const int k = e / w1, j = a1 + (e - k * w1);
-                Rbuf[(int64_t)k * l + j] = cluster.map_shared_rank(Sown, j % C)[(int64_t)(j / C) * l + a0 + k];
-            }
-            __syncthreads();
-            // (c) trailing updates, one warp per own column
-            for (int jl = warp; jl < ncol; jl += nwarp) {
-                const int j = jl * C + rank;
-                if (j >= l) continue;
-                if (j >= a1) {
-                    double* col = Sown + (int64_t)jl * l;
+            push_diag16(cluster, Sown, Dnx, l, ncol, C, rank, a1, tid, nth);
+            cluster.sync();                     // Dnx holds diagonal block t+1 everywhere
+            // (a) of block t+1 by warp 0, while the other warps run (c2): the trailing
+            // updates of own columns past block t+1 and of own T columns left of a1
+            if (warp < 4) chol_block16(Wfb, Dnx, thr, a1, a2 - a1, Rtt, Ttt, &s_fail, tid);
+            if (warp >= 4) {
+                for (int jl = warp - 4; jl < ncol; jl += nwarp - 4) {
+                    const int j = jl * C + rank;
+                    if (j >= l || (j >= a1 && j < a2)) continue;
+                    const bool scol = j >= a2;
+                    double* col = (scol ? Sown : Town) + (int64_t)jl * l;
                     double rj[kCiNb];
 #pragma unroll
                     for (int k = 0; k < kCiNb; ++k) rj[k] = (k < nb) ? col[a0 + k] : 0.0;
-                    for (int i = a1 + lane; i <= j; i += 32) {
+                    const int iend = scol ? j + 1 : l;
+                    for (int i = a1 + lane; i < iend; i += 32) {
                         double acc = col[i];
 #pragma unroll
-                        for (int k = 0; k < kCiNb; ++k)
-                            if (k < nb) acc -= Rbuf[(int64_t)k * l + i] * rj[k];
+                        for (int k = 0; k < kCiNb; ++k) acc = fma(-Rb[(int64_t)k * l + i], rj[k], acc);
                         col[i] = acc;
-                    }
-                } else {
-                    double* tcol = Town + (int64_t)jl * l;
-                    double tj[kCiNb];
-#pragma unroll
-                    for (int k = 0; k < kCiNb; ++k) tj[k] = (k < nb) ? tcol[a0 + k] : 0.0;
-                    for (int i = a1 + lane; i < l; i += 32) {
-                        double acc = tcol[i];
-#pragma unroll
-                        for (int k = 0; k < kCiNb; ++k)
-                            if (k < nb) acc -= Rbuf[(int64_t)k * l + i] * tj[k];
-                        tcol[i] = acc;
-                    }
-                    if (j >= a0) {
-                        // own column of the diagonal block: its rows a0 .. a1-1 of R are R_tt's column
-                        double* col = Sown + (int64_t)jl * l;
-                        for (int k = lane; k < nb; k += 32) col[a0 + k] = Rtt[k * kCiNb + (j - a0)];
                     }
                 }
             }
-            cluster.sync();   // updates visible before the next gather
+            __syncthreads();
+            fail = s_fail;                      // the same in every CTA
         }
         __syncthreads();
         if (!fail) break;
@@ -291,7 +340,8 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
 // share an SM (and its FP64 lanes).
 static size_t chol_inv_smem(int l, int C) {
     const int ncol = (l + C - 1) / C;
-    const size_t need = ((size_t)2 * ncol * l + (size_t)kCiNb * l + kCiNb * kCiNb + kCiNb) * sizeof(double);
+    const size_t need =
+        ((size_t)2 * ncol * l + (size_t)2 * kCiNb * l + 3 * kCiNb * kCiNb + kCiNb * 32 + (size_t)l) * sizeof(double);
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 

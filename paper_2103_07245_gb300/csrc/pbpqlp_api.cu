@@ -596,6 +596,13 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
             const int64_t ra = P->stream_a ? P->srows : m;   // rows of A in one product
             P->og_nn = oz_geometry(ra, (int)l, n, false, P->num_sms);
             P->og_tn = oz_geometry(n, (int)l, ra, false, P->num_sms);
+            if (P->stream_a && m % ra) {
+                // the last, shorter block may split differently: room for either
+                const OzGeom a = oz_geometry(m % ra, (int)l, n, false, P->num_sms);
+                const OzGeom b = oz_geometry(n, (int)l, m % ra, false, P->num_sms);
+                if (a.part_doubles > P->og_nn.part_doubles) P->og_nn.part_doubles = a.part_doubles;
+                if (b.part_doubles > P->og_tn.part_doubles) P->og_tn.part_doubles = b.part_doubles;
+            }
             pd = pd > P->og_nn.part_doubles ? pd : P->og_nn.part_doubles;
             pd = pd > P->og_tn.part_doubles ? pd : P->og_tn.part_doubles;
         }
@@ -643,6 +650,12 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         P->ldk_m = tc_ld(ra, P->tf32);
         P->g_nn = tc_geometry(ra, n, P->cw, P->num_sms, P->tf32);
         P->g_tn = tc_geometry(n, ra, P->cw, P->num_sms, P->tf32);
+        if (P->stream_a && m % ra) {
+            const TcGeom a = tc_geometry(m % ra, n, P->cw, P->num_sms, P->tf32);
+            const TcGeom b = tc_geometry(n, m % ra, P->cw, P->num_sms, P->tf32);
+            if (a.part_floats > P->g_nn.part_floats) P->g_nn.part_floats = a.part_floats;
+            if (b.part_floats > P->g_tn.part_floats) P->g_tn.part_floats = b.part_floats;
+        }
         const int64_t BN = P->g_nn.BN;
         const bool split = P->nprod == 3;
         const size_t es = P->tf32 ? 4 : 2;   // bytes per operand element

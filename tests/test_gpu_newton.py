@@ -1,5 +1,6 @@
-"""The Newton-refined FP64 reciprocal and reciprocal square root that the
-Cholesky and QR kernels use on their pivot chains, against correctly rounded
+"""The Newton-refined FP64 reciprocal and reciprocal square root, and the
+one-step Goldschmidt reciprocal, that the Cholesky and QR kernels use on
+their pivot chains, against correctly rounded
 results (numpy's IEEE division, and 1/sqrt taken in extended precision), over
 every exponent of the double format and its edge cases.
 
@@ -53,9 +54,10 @@ def test_newton_helpers_within_ulp_bound(pq):
     td = torch.from_numpy(d).cuda()
     rcp = torch.empty_like(td)
     rsq = torch.empty_like(td)
-    pq.pbpqlp_newton_check(td, td.numel(), rcp, rsq)
+    rgs = torch.empty_like(td)
+    pq.pbpqlp_newton_check(td, td.numel(), rcp, rsq, rgs)
     torch.cuda.synchronize()
-    rcp, rsq = rcp.cpu().numpy(), rsq.cpu().numpy()
+    rcp, rsq, rgs = rcp.cpu().numpy(), rsq.cpu().numpy(), rgs.cpu().numpy()
     npos = normal.size + edges.size
     x = d[:npos]
     with np.errstate(divide="ignore", invalid="ignore", over="ignore", under="ignore"):
@@ -67,6 +69,9 @@ def test_newton_helpers_within_ulp_bound(pq):
     u = _ulps(rcp[:npos][~big], ref_rcp[~big])
     assert np.max(u) <= ULP_BOUND, (np.max(u), x[~big][np.argmax(u)])
     assert np.array_equal(rcp[:npos][big], ref_rcp[big])
+    # the Goldschmidt reciprocal: every positive normal input, including d >= 2^1023
+    u = _ulps(rgs[:npos], ref_rcp)
+    assert np.max(u) <= ULP_BOUND, (np.max(u), x[np.argmax(u)])
     u = _ulps(rsq[:npos], ref_rsq)
     assert np.max(u) <= ULP_BOUND, (np.max(u), x[np.argmax(u)])
     # the rest takes IEEE division and square root: bit-identical (NaN as NaN)
