@@ -73,10 +73,10 @@ constexpr int kCiNb = 16;
 // per sub-partition, so one warp alone would serialise the updates).  The
 // augmented block [S_tt | I] (16 x 32, in W) is eliminated by LDL^T row
 // operations: thread t owns column t % 32 (0..15 of S, 16..31 of I) in rows
-// t / 32 + 4r, r = 0..3.  Pivot p: every thread takes 1/d_p from the shared
-// row p (an FP32 seed and one Goldschmidt step), updates its rows below p
-// (row i -= (S[p][i] / d_p) row p; S only on and above the diagonal), and a
-// 128-thread barrier publishes row p + 1.  The S part ends as D U and the I
+// t / 32 + 4r, r = 0..3.  Pivot p: warp 0 forms 1/d_p (an FP32 seed and one
+// Goldschmidt step) and the multipliers S[p][i] / d_p; after a 128-thread
+// barrier every thread updates its rows below p (row i -= multiplier_i row p;
+// S only on and above the diagonal), and a second barrier publishes row p + 1.  The S part ends as D U and the I
 // part as L^{-1} = U^{-T}, so R_tt = D^{1/2} U and T_tt = D^{-1/2} L^{-1}.
 // No branches on the data: a failed pivot (not above its threshold, or not
 // finite) is recorded and the block discarded.  Rows and columns past the
@@ -99,21 +99,27 @@ __device__ __noinline__ void chol_block16(double* __restrict__ W, const double* 
         W[i * 32 + c] = x;
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
+    double* Mv = W + kCiNb * 32;   // 16: the multipliers S[p][i] / d_p of the current pivot
     int f = 0;
 #pragma unroll
     for (int p = 0; p < kCiNb; ++p) {
-        const double d = W[p * 32 + p];
-        const double th = p < nb ? thr[a0 + p] : 0.0;
-        const int fp = !isfinite(d) ? 2 : (!(d > th) ? 1 : 0);
-        f = f ? f : fp;
-        const double cp = rcp_gs(d);
+        // warp 0: 1/d_p and the multipliers (each FP64 warp instruction occupies a
+        // sub-partition's FP64 unit for 64 cycles, so the other warps do not repeat them)
+        if (w == 0) {
+            const double d = W[p * 32 + p];
+            const double th = p < nb ? thr[a0 + p] : 0.0;
+            const int fp = !isfinite(d) ? 2 : (!(d > th) ? 1 : 0);
+            f = f ? f : fp;
+            const double cp = rcp_gs(d);
+            if (c > p && c < kCiNb) Mv[c] = W[p * 32 + c] * cp;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
         const double rowp = W[p * 32 + c];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = w + 4 * r;
             if (i > p) {
-                const double mult = W[p * 32 + i] * cp;   // L[i][p] = S[p][i] / d_p
-                if (idl || c >= i) v[r] = fma(-mult, rowp, v[r]);
+                if (idl || c >= i) v[r] = fma(-Mv[i], rowp, v[r]);
                 W[i * 32 + c] = v[r];
             }
         }
@@ -166,8 +172,8 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
     double* Dnx = Rbuf + (int64_t)2 * kCiNb * l;         // 16 x 16: next diagonal block, [column][row]
     double* Rtt = Dnx + kCiNb * kCiNb;                   // 16 x 16: R_tt, [row][column]
     double* Ttt = Rtt + kCiNb * kCiNb;                   // 16 x 16: T_tt = R_tt^{-T}, [row][column]
-    double* Wfb = Ttt + kCiNb * kCiNb;                   // 16 x 32: the block factor's working rows
-    double* thr = Wfb + kCiNb * 32;                      // l: pivot thresholds
+    double* Wfb = Ttt + kCiNb * kCiNb;                   // 16 x 32 + 16: the block factor's rows, multipliers
+    double* thr = Wfb + kCiNb * 32 + kCiNb;              // l: pivot thresholds
     __shared__ int s_fail;
     __shared__ double s_shift;
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -341,7 +347,7 @@ k_chol_inv_cluster(int l, int64_t rows, const double* __restrict__ G, double* __
 static size_t chol_inv_smem(int l, int C) {
     const int ncol = (l + C - 1) / C;
     const size_t need =
-        ((size_t)2 * ncol * l + (size_t)2 * kCiNb * l + 3 * kCiNb * kCiNb + kCiNb * 32 + (size_t)l) * sizeof(double);
+        ((size_t)2 * ncol * l + (size_t)2 * kCiNb * l + 3 * kCiNb * kCiNb + kCiNb * 33 + (size_t)l) * sizeof(double);
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 
