@@ -696,7 +696,7 @@ CLASS_KERNELS = {
 }
 
 
-def class_roofline(name, bd, m, n, l, q):
+def class_roofline(name, bd, m, n, l, q, fp64_probe=None):
     """Roofline of a non-pass class: its algorithmic FP64 flops per factorization
     (FP64-equivalent for the digit forms) over its measured time, against the
     FP64 issue rate of the whole GPU."""
@@ -722,14 +722,15 @@ def class_roofline(name, bd, m, n, l, q):
     return {"kernel": CLASS_KERNELS[name], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS if ach else None, "traffic": None,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (FP64-equivalent algorithmic flops)",
+            "peak_probe": fp64_probe, "frac_probe": ach / fp64_probe if (ach and fp64_probe) else None,
             "launches_timed": per, "avg_launch_ms": bd[name]["ms"] / per,
             "share_of_step": None}
 
 
-def dominant_roofline(bd, pass_roofline, m, n, l, q, step_ms):
+def dominant_roofline(bd, pass_roofline, m, n, l, q, step_ms, fp64_probe=None):
     """The roofline of the class that takes the most time per factorization."""
     name = max(bd, key=lambda c: bd[c]["ms"])
-    r = dict(pass_roofline) if name == "pass" else class_roofline(name, bd, m, n, l, q)
+    r = dict(pass_roofline) if name == "pass" else class_roofline(name, bd, m, n, l, q, fp64_probe)
     r["share_of_step"] = bd[name]["ms"] / step_ms if step_ms else None
     r["class"] = name
     return r
@@ -823,6 +824,8 @@ def run_dense(args, w, world, rank, local):
 
     flops = algorithmic_flops(m, n, l, q)
     avg_pass_ms = (pass_ms / pass_launches) if pass_launches else None
+    sink = torch.zeros(4096, dtype=torch.float64, device=dev)
+    fp64_probe = pq.pbpqlp_fp64_rate_probe(sink)   # measured FP64 FMA issue rate, beside the derived peak
     if w["mode"] == "FP64":
         achieved = 2.0 * m * n * l / (avg_pass_ms / 1e3) / 1e12 if avg_pass_ms else None
         roofline = {"kernel": "k_dgemm_skinny (A / A^T pass, 2mnl flop per launch)", "bound": "alu",
@@ -830,6 +833,9 @@ def run_dense(args, w, world, rank, local):
                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                     "traffic": read_traffic("dgemm_skinny_fp64_8000"),
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
+                    "peak_probe": fp64_probe, "frac_probe": (achieved / fp64_probe) if achieved else None,
+                    "peak_probe_source": "pbpqlp_fp64_rate_probe: 8 independent FMA chains per thread, 4 CTAs per SM, "
+                                         "CUDA events, measured in this run",
                     "launches_timed": pass_launches, "avg_launch_ms": avg_pass_ms}
         dtype = "f64"
     elif w["mode"] == "FP64_EMU":
@@ -848,7 +854,7 @@ def run_dense(args, w, world, rank, local):
         dtype = "bf16x3" if nprod == 3 else "bf16"
     bd = class_breakdown(pq, plan, A, (Qa, L, Qb))
     pass_roofline = roofline
-    roofline = dominant_roofline(bd, roofline, m, n, l, q, ms) if roofline else None
+    roofline = dominant_roofline(bd, roofline, m, n, l, q, ms, fp64_probe) if roofline else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -902,7 +908,7 @@ def run_dense(args, w, world, rank, local):
                          "tflops_algorithmic": world / (cms / 1e3) * flops / 1e12,
                          "rel_err_rank_k": err_c, "rel_err_rank_k_fp64": err_main,
                          "error_ratio_vs_fp64": err_c / err_main, "speedup_vs_fp64": ms / cms,
-                         "roofline": dominant_roofline(cbd, cpass, m, n, l, q, cms) if cpass else None,
+                         "roofline": dominant_roofline(cbd, cpass, m, n, l, q, cms, fp64_probe) if cpass else None,
                          "pass_roofline": cpass,
                          "breakdown_ms_per_step": {c: round(v["ms"], 4) for c, v in cbd.items()}}
         del cplan
@@ -930,7 +936,7 @@ def run_dense(args, w, world, rank, local):
                      traffic=read_traffic("oz_gemm_fp64emu_8000") if (m, n, l) == (8000, 8000, 110) else None) \
             if epn else None
         ebd = class_breakdown(pq, eplan, A, eouts)
-        line["fp64_emulated"]["roofline"] = dominant_roofline(ebd, epass, m, n, l, q, ems) if epass else None
+        line["fp64_emulated"]["roofline"] = dominant_roofline(ebd, epass, m, n, l, q, ems, fp64_probe) if epass else None
         line["fp64_emulated"]["pass_roofline"] = epass
         line["fp64_emulated"]["breakdown_ms_per_step"] = {c: round(v["ms"], 4) for c, v in ebd.items()}
         del eplan, eouts

@@ -453,6 +453,17 @@ int64_t pbpqlp_kernel_launch_count(void);
  */
 int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, double* rcp_gs, void* stream);
 
+/*
+ * Measured FP64 FMA issue rate of the current device (a microbenchmark, not
+ * part of the method): 4 CTAs per SM of 256 threads each run 8 independent
+ * FMA chains; *tflops_out (host) gets 2 x FMAs / the CUDA-event time of the
+ * timed launch, in TFLOP/s.  sink: device scratch of at least 4 x (SM count)
+ * doubles (written only if a chain hits a sentinel value).  Synchronous.
+ * The benchmark reports FP64 roofline fractions against this measured rate
+ * beside the rate derived from unit counts and the maximum clock.
+ */
+int pbpqlp_fp64_rate_probe(double* sink, double* tflops_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

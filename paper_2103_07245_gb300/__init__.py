@@ -156,6 +156,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_read_timing_class.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.pbpqlp_read_timing_class.restype = ci
     L.pbpqlp_newton_check.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.pbpqlp_fp64_rate_probe.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.pbpqlp_fp64_rate_probe.restype = ci
     L.pbpqlp_newton_check.restype = ci
     _lib = L
     return L
@@ -352,6 +354,13 @@ def pbpqlp_newton_check(d, n, rcp, rsqrt, rcp_gs=None, stream=None):
     for n device doubles (a diagnostic)."""
     _check(load().pbpqlp_newton_check(_ptr(d), int(n), _ptr(rcp), _ptr(rsqrt), _ptr(rcp_gs), _stream(stream)),
            "pbpqlp_newton_check")
+
+
+def pbpqlp_fp64_rate_probe(sink, stream=None) -> float:
+    """Measured FP64 FMA issue rate of the current device in TFLOP/s (sink: >= 4 x SMs device doubles)."""
+    out = ctypes.c_double(0.0)
+    _check(load().pbpqlp_fp64_rate_probe(_ptr(sink), ctypes.byref(out), _stream(stream)), "pbpqlp_fp64_rate_probe")
+    return out.value
 
 
 def _ptr_array(xs):
