@@ -455,9 +455,10 @@ int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, 
 
 /*
  * Measured FP64 FMA issue rate of the current device (a microbenchmark, not
- * part of the method): 4 CTAs per SM of 256 threads each run 8 independent
- * FMA chains; *tflops_out (host) gets 2 x FMAs / the CUDA-event time of the
- * timed launch, in TFLOP/s.  sink: device scratch of at least 4 x (SM count)
+ * part of the method): CTAs of 256 threads, 1, 2 and 4 per SM, each thread
+ * updating a 4 x 4 block of accumulators as a register-blocked GEMM does;
+ * *tflops_out (host) gets the best of 2 x FMAs / the CUDA-event time of a
+ * launch, in TFLOP/s.  sink: device scratch of at least 4 x (SM count)
  * doubles (written only if a chain hits a sentinel value).  Synchronous.
  * The benchmark reports FP64 roofline fractions against this measured rate
  * beside the rate derived from unit counts and the maximum clock.

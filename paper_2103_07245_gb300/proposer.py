@@ -149,18 +149,35 @@ def trajectory_errors(A, k, seed):
     return err, L0, passes
 
 
-def label(As, ks, tails, seed=0):
+def label(As, ks, tails, seed=0, workers=1):
     """Features of the (0, 20) sketch, the error table err[i][q][p] (one
     trajectory per matrix) and the labels: the cheapest pair with error <=
     1.5 x tail / MARGIN.  Cost is what the guarded proposal pays after its
     sketch: nothing for (0, 20) itself, else (2q + 1)(k + p) (the continued
     trajectory: q iterations and the projection, times the panel width)."""
+    import torch
     cnt = len(As)
     err = np.zeros((cnt, len(Q_CHOICES), len(P_CHOICES)))
-    Ls = []
-    for i, (A, k) in enumerate(zip(As, ks)):
-        err[i], L0, _ = trajectory_errors(A, k, seed + i)
-        Ls.append(L0)
+    Ls = [None] * cnt
+    if workers <= 1:
+        for i, (A, k) in enumerate(zip(As, ks)):
+            err[i], Ls[i], _ = trajectory_errors(A, k, seed + i)
+    else:
+        # one CUDA stream per worker thread: the trajectories are independent and
+        # latency-bound, so several run at once (the library calls release the GIL)
+        import concurrent.futures as cf
+        torch.cuda.synchronize()
+        streams = [torch.cuda.Stream() for _ in range(workers)]
+
+        def run(wid):
+            with torch.cuda.stream(streams[wid]):
+                for i in range(wid, cnt, workers):
+                    err[i], Ls[i], _ = trajectory_errors(As[i], ks[i], seed + i)
+            streams[wid].synchronize()
+
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(run, range(workers)))
+        torch.cuda.synchronize()
     F = features(Ls, [k + P_SKETCH for k in ks], ks, [a.shape[0] for a in As], [a.shape[1] for a in As])
     yq, yp = [], []
     for i, k in enumerate(ks):
@@ -194,8 +211,17 @@ def random_family(rng, m, n):
     return s
 
 
-def make_matrices(seed, count, m_range=(512, 2048), k_range=(8, 64), fixed=None, eval_mix=False, device="cuda"):
-    """Seeded matrices, their k and their optimal relative tails ||sigma_{k+1:}|| / ||sigma||."""
+def make_matrices(seed, count, m_range=(512, 2048), k_range=(8, 64), fixed=None, eval_mix=False, device="cuda",
+                  diagonal=False):
+    """Seeded matrices, their k and their optimal relative tails ||sigma_{k+1:}|| / ||sigma||.
+
+    With diagonal, A = Sigma (m x n, the singular values on the diagonal) instead
+    of U Sigma V^T with Haar U, V.  For a Gaussian Phi the factorization's
+    output distribution depends on Sigma only (U^T Phi is again Gaussian, and
+    V^T is undone by the basis), so the errors, the L-values and hence the
+    features and labels have the same distribution at no generation cost;
+    the held-out evaluation keeps Haar factors."""
+    import torch
     import synth
     rng = np.random.default_rng(seed)
     As, ks, tails = [], [], []
@@ -211,7 +237,14 @@ def make_matrices(seed, count, m_range=(512, 2048), k_range=(8, 64), fixed=None,
             sig = i ** (-rng.uniform(0.5, 3.0)) if rng.random() < 0.5 else np.exp(-i * rng.uniform(1 / 80, 1 / 10))
         else:
             sig = random_family(rng, m, n)
-        As.append(synth.torch_svd_matrix_device(int(rng.integers(1 << 30)), m, n, sig, device=device))
+        sseed = int(rng.integers(1 << 30))
+        if diagonal:
+            A = torch.zeros(m, n, dtype=torch.float64, device=device)
+            r = min(m, n)
+            A[torch.arange(r, device=device), torch.arange(r, device=device)] = torch.as_tensor(sig[:r], device=device)
+            As.append(A)
+        else:
+            As.append(synth.torch_svd_matrix_device(sseed, m, n, sig, device=device))
         ks.append(k)
         tails.append(float(np.linalg.norm(sig[k:]) / np.linalg.norm(sig)))
     return As, ks, tails
@@ -393,6 +426,9 @@ def main(argv=None):
     ap.add_argument("--max-dim", type=int, default=2048)
     ap.add_argument("--eval", type=int, default=64)
     ap.add_argument("--eval-chunk", type=int, default=128)
+    ap.add_argument("--workers", type=int, default=1, help="concurrent label trajectories (one stream each)")
+    ap.add_argument("--diagonal", action="store_true",
+                    help="training matrices A = Sigma (same label distribution as Haar U Sigma V^T)")
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--save", default=None)
@@ -405,8 +441,9 @@ def main(argv=None):
     t0 = time.time()
 
     def make_chunk(c):
-        As, ks, tails = make_matrices(1000 * args.seed + c, args.chunk, m_range=(512, args.max_dim))
-        F, err, yq, yp = label(As, ks, tails, seed=c)
+        As, ks, tails = make_matrices(1000 * args.seed + c, args.chunk, m_range=(512, args.max_dim),
+                                      diagonal=args.diagonal)
+        F, err, yq, yp = label(As, ks, tails, seed=c, workers=args.workers)
         return F, yq, yp
 
     F_all, yq_all, yp_all = labelled_chunks(args.chunks, make_chunk, args.shards)
