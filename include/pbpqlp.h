@@ -455,8 +455,9 @@ int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, 
 
 /*
  * Measured FP64 FMA issue rate of the current device (a microbenchmark, not
- * part of the method): CTAs of 256 threads, 1, 2 and 4 per SM, each thread
- * updating a 4 x 4 block of accumulators as a register-blocked GEMM does;
+ * part of the method): CTAs of 256 threads, 1, 2 and 4 per SM, running the
+ * inner loop of a register-blocked FP64 GEMM (operands from shared memory,
+ * a 4 x 4 block of accumulators per thread);
  * *tflops_out (host) gets the best of 2 x FMAs / the CUDA-event time of a
  * launch, in TFLOP/s.  sink: device scratch of at least 4 x (SM count)
  * doubles (written only if a chain hits a sentinel value).  Synchronous.

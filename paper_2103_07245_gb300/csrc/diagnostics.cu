@@ -34,31 +34,44 @@ extern "C" int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, doub
 
 namespace {
 
-// Independent FP64 FMA chains for the issue-rate probe, in the instruction
-// mix of a register-blocked GEMM: a 4 x 4 block of accumulators updated with
-// products of 4 + 4 register operands (16 chains per thread).  The result is
-// stored only on a sentinel value, so the chains are kept.
+// The FP64 issue-rate probe runs the inner loop of a register-blocked FP64
+// GEMM: each k step loads 4 values of a 64-row tile and 4 of a 64-column tile
+// from shared memory and updates a 4 x 4 block of accumulators (16 FMA
+// chains per thread).  The result is stored only on a sentinel value, so the
+// work is kept.
 __global__ void __launch_bounds__(256) k_dfma_probe(int iters, double seed, double* __restrict__ sink) {
-    double a[4], b[4], acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        a[i] = 1.0 - 1e-9 * (i + 1);
-        b[i] = 1e-12 * (threadIdx.x + i + 1);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = seed + 1e-3 * (i * 4 + j);
+    __shared__ double As[16][65], Bs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int e = tid; e < 16 * 64; e += 256) {
+        As[e / 64][e % 64] = 1e-9 * (e % 61 + 1);
+        Bs[e / 64][e % 64] = 1e-9 * (e % 59 + 1);
     }
-    for (int it = 0; it < iters; ++it) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(acc[i][j], a[i], b[j]);
-    }
-    double s = 0.0;
+    __syncthreads();
+    double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) s += acc[i][j];
-    if (s == 12345.678) sink[blockIdx.x] = s;   // practically never true; keeps the work alive
+        for (int j = 0; j < 4; ++j) acc[i][j] = seed + 1e-3 * (i * 4 + j);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll 2
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sum += acc[i][j];
+    if (sum == 12345.678) sink[blockIdx.x] = sum;   // practically never true; keeps the work alive
 }
 
 }  // namespace
@@ -73,7 +86,7 @@ extern "C" int pbpqlp_fp64_rate_probe(double* sink, double* tflops_out, void* st
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PBPQLP_ECUDA;
     // 1, 2 and 4 CTAs of 256 threads per SM; the best rate is reported
-    const int threads = 256, iters = 2048;
+    const int threads = 256, iters = 128;   // 16 k steps of 16 FMAs per iteration
     int rc = PBPQLP_OK;
     double best = 0.0;
     k_dfma_probe<<<sms, threads, 0, s>>>(64, 1.0, sink);   // warm-up
@@ -89,7 +102,7 @@ extern "C" int pbpqlp_fp64_rate_probe(double* sink, double* tflops_out, void* st
             rc = PBPQLP_ECUDA;
             break;
         }
-        const double tf = 2.0 * 16.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+        const double tf = 2.0 * 16.0 * 16.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
         best = tf > best ? tf : best;
     }
     if (rc == PBPQLP_OK) *tflops_out = best;
