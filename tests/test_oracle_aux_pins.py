@@ -17,7 +17,8 @@
   orthogonal W as well; it is 0 when A has rank r and the factors recover it.
 
 The check functions take the module under test, so that the mutation tests
-can run them against copies of the oracle with one planted mistake.
+can run them against copies of the oracle with one planted mistake.  A last
+pin fixes the rotation invariance that lets the proposer train on A = Sigma.
 """
 import numpy as np
 
@@ -93,3 +94,26 @@ def test_adamw_against_closed_forms():
 
 def test_probe_estimate_against_closed_forms(orc):
     check_probe_estimate(orc)
+
+
+def test_factorization_depends_on_the_spectrum_only(orc):
+    """The reading behind the proposer's diagonal training matrices: for
+    A = U Sigma V^T and any Phi, Algorithm 3 on (A, Phi) and on (Sigma, U^T Phi)
+    give the same L and the same errors (every orth is a thin QR, and
+    qr(W X) = W qr(X) for orthogonal W), and U^T Phi is Gaussian when Phi is."""
+    rng = np.random.default_rng(11)
+    m, n, ell, k = 70, 50, 12, 8
+    U = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    V = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    sig = 0.8 ** np.arange(n)
+    S = np.zeros((m, n))
+    S[np.arange(n), np.arange(n)] = sig
+    A = U @ S @ V.T
+    phi = rng.standard_normal((m, ell))
+    for q in (0, 1, 2):
+        a = orc.pbpqlp(A, ell, q, phi=phi)
+        b = orc.pbpqlp(S, ell, q, phi=U.T @ phi)
+        assert np.allclose(a["L"], b["L"], rtol=0, atol=1e-12 * sig[0]), q
+        ea = orc.rel_fro_error(A, a["Q"], a["L"], a["P"], k)
+        eb = orc.rel_fro_error(S, b["Q"], b["L"], b["P"], k)
+        assert abs(ea - eb) <= 1e-12, (q, ea, eb)
