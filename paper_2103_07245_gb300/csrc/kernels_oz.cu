@@ -119,6 +119,21 @@ __host__ __device__ inline void oz_tile(int64_t t, int NT, int upper, int64_t* m
     }
 }
 
+// Virtual tile v of CTA blockIdx.x -> (row tile, column tile) and the tile's own
+// index: with lock > 1 the virtual tiles are the row tiles and the CTA's column
+// tile is blockIdx.x % lock.
+template <bool kLock>
+__device__ __forceinline__ int64_t oz_vtile(int64_t v, int NT, int upper, int lock, int64_t* mt, int* nt) {
+    if (kLock) {
+        const int j = (int)(blockIdx.x % (unsigned)lock);
+        *mt = v;
+        *nt = j;
+        return v * NT + j;
+    }
+    oz_tile(v, NT, upper, mt, nt);
+    return v;
+}
+
 // CTA whose stream-K range holds iteration it.
 __device__ __forceinline__ int64_t sk_owner(int64_t it, int64_t T, int64_t G) {
     int64_t c = (it * G) / T;
@@ -272,9 +287,10 @@ __device__ __forceinline__ void oz_store(double* crow, int ncol, int exr, const 
 // The product kernel
 // ---------------------------------------------------------------------------
 // 448 threads are allocated registers as 16 warps: at most 65536 / 512 = 128 each.
+template <bool kLock>
 __global__ void __maxnreg__(128)
-k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t tiles, int NT,
-          int upper, int KI, int smax, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
+k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t T, int NT,
+          int upper, int lock_, int64_t G, int KI, int smax, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
           const int* __restrict__ ey_raw, double* __restrict__ part, int* __restrict__ cnt, double* __restrict__ Cout,
           int64_t ldc, uint32_t* __restrict__ status, uint64_t timeout_ns, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
@@ -287,8 +303,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
     __shared__ int issued_sh, consumed_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t G = gridDim.x, c = blockIdx.x;
-    const int64_t T = tiles * (int64_t)KI;
+    // Stream-K over T = (virtual tiles) x KI iterations on G = gridDim / lock
+    // virtual CTAs.  lock > 1: CTAs lock c .. lock c + lock - 1 run column tiles
+    // 0 .. NT - 1 of the same row tiles over the same k-chunks at the same time,
+    // so X's digits come from DRAM once and from L2 for the other column tiles;
+    // the virtual tiles are then the row tiles.
+    const int lock = kLock ? lock_ : 1;
+    const int64_t c = kLock ? blockIdx.x / lock : blockIdx.x;
     const int64_t it_begin = sk_begin(c, T, G), it_end = sk_begin(c + 1, T, G);
     const uint64_t deadline = globaltimer() + timeout_ns;
 
@@ -329,7 +350,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                 const int kc = (int)(it - tile * KI);
                 int64_t mt;
                 int nt;
-                oz_tile(tile, NT, upper, &mt, &nt);
+                oz_vtile<kLock>(tile, NT, upper, lock, &mt, &nt);
                 unsigned char* st = smem + (size_t)s * kOzStageBytes;
                 mbar_expect_tx(&full_bar[s], kOzStageBytes);
                 tma_load_4d(st, &tmX, &full_bar[s], 0, (int)(mt * kOzBM), kc, 0);
@@ -409,7 +430,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                 const int64_t tile = it_begin / KI + tl;
                 int64_t mt;
                 int nt;
-                oz_tile(tile, NT, upper, &mt, &nt);
+                const int64_t rtile = oz_vtile<kLock>(tile, NT, upper, lock, &mt, &nt);
                 const int64_t row = mt * kOzBM + rloc;
                 const int exr = row < Rx ? ex_raw[row] : 0;
                 oz_unbias(nwin, hi, lo);   // exact integer sums of this segment, in units of 2^(e_i + f_j - 63)
@@ -424,7 +445,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     // stream-K fix-up per 32 x 16 slice: publish the integer sums; the
                     // CTA that completes the slice adds all of them (exact, so the
                     // order is immaterial) and writes C
-                    int64_t* slot = (int64_t*)part + ((size_t)c * smax + (size_t)tl) * (size_t)(2 * kOzBM * kOzBN);
+                    int64_t* slot = (int64_t*)part + ((size_t)blockIdx.x * smax + (size_t)tl) * (size_t)(2 * kOzBM * kOzBN);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         slot[(size_t)(g * 16 + j) * kOzBM + rloc] = (int64_t)hi[j];
@@ -432,7 +453,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     }
                     __threadfence();
                     __syncwarp();
-                    int* ctr = cnt + tile * 12 + q * 3 + g;
+                    int* ctr = cnt + rtile * 12 + q * 3 + g;
                     int old = 0;
                     if (lane == 0) old = atomicAdd(ctr, 1);
                     old = __shfl_sync(0xffffffffu, old, 0);
@@ -444,7 +465,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                         for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
                         for (int64_t c2 = cf; c2 <= cl; ++c2) {
                             const long long* s2 = (const long long*)part +
-                                                  ((size_t)c2 * smax + (size_t)(tile - sk_begin(c2, T, G) / KI)) *
+                                                  ((size_t)(kLock ? c2 * lock + blockIdx.x % lock : c2) * smax +
+                                                   (size_t)(tile - sk_begin(c2, T, G) / KI)) *
                                                       (size_t)(2 * kOzBM * kOzBN);
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -917,16 +939,21 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
         g.tiles = MT * g.NT;
     }
     g.KI = (int)((K + kOzBK - 1) / kOzBK);
-    const int64_t T = g.tiles * g.KI;
+    // the column tiles of a row tile run in lockstep on NT CTAs (X read from
+    // DRAM once) for full rectangles of 2 .. 8 column tiles
+    g.lock = (!upper && g.NT >= 2 && g.NT <= 8 && num_sms >= g.NT) ? g.NT : 1;
+    const int64_t T = (g.lock > 1 ? MT : g.tiles) * g.KI;
+    const int sms = num_sms / g.lock;
     // at least min_it iterations (32-deep chunks) per CTA: small products use
     // fewer CTAs, with fewer partials to fix up.  Short contractions (the
     // CholeskyQR solve and Qb, K = l) take 4, which measured 20% faster for
     // them; long ones (Grams, passes over A) 16.
     const int64_t min_it = g.KI <= 8 ? 4 : 16;
     const int64_t want = (T + min_it - 1) / min_it;
-    g.G = (int)(want < num_sms ? want : num_sms);
-    if (g.G < 1) g.G = 1;
-    const int64_t share = (T + g.G - 1) / g.G;
+    int Gv = (int)(want < sms ? want : sms);
+    if (Gv < 1) Gv = 1;
+    const int64_t share = (T + Gv - 1) / Gv;
+    g.G = Gv * g.lock;
     g.smax = (int)((share + g.KI - 1) / g.KI + 1);
     g.part_doubles = (int64_t)g.G * g.smax * 2 * kOzBM * kOzBN;   // two int64 sums per element
     return g;
@@ -941,15 +968,24 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
     if (!make_map_oz(&mx, X, kOzBM)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of X refused
     if (!make_map_oz(&my, Y, kOzBN)) return PBQ_DBG(cudaErrorInvalidValue);   // tensor map of Y refused
     const size_t smem = (size_t)kOzStages * kOzStageBytes + 1024;
-    cudaError_t e = PBQ_DBG(func_smem_attr((const void*)k_oz_gemm, smem));
+    const void* fn = g.lock > 1 ? (const void*)k_oz_gemm<true> : (const void*)k_oz_gemm<false>;
+    cudaError_t e = PBQ_DBG(func_smem_attr(fn, smem));
     if (e != cudaSuccess) return e;
-    k_oz_gemm<<<g.G, kOzThreads, smem, s>>>(mx, my, g.tiles, g.NT, g.upper, g.KI, g.smax, X.rows, Y.rows, X.eraw,
-                                            Y.eraw, part, cnt, C, ldc, status, 2000000000ull, cond);
+    if (g.lock < 1 || g.G % g.lock != 0 || (g.lock > 1 && (g.upper || g.lock != g.NT))) return cudaErrorInvalidValue;
+    const int64_t T = (g.lock > 1 ? g.tiles / g.NT : g.tiles) * (int64_t)g.KI;
+    if (g.lock > 1)
+        k_oz_gemm<true><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, g.lock, (int64_t)(g.G / g.lock), g.KI,
+                                                      g.smax, X.rows, Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
+                                                      2000000000ull, cond);
+    else
+        k_oz_gemm<false><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, 1, (int64_t)g.G, g.KI, g.smax, X.rows,
+                                                       Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
+                                                       2000000000ull, cond);
     count_launches(1);
     if ((e = PBQ_DBG(cudaGetLastError())) != cudaSuccess) {
         const char* v = std::getenv("PBPQLP_DEBUG");
         cudaFuncAttributes fa;
-        if (v && v[0] == '1' && cudaFuncGetAttributes(&fa, k_oz_gemm) == cudaSuccess)
+        if (v && v[0] == '1' && cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
             std::fprintf(stderr, "pbpqlp: k_oz_gemm regs %d, max threads %d, static smem %zu, max dyn smem %d, local %zu, "
                          "launch %d x %d with %zu bytes\n", fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
                          fa.maxDynamicSharedSizeBytes, fa.localSizeBytes, g.G, kOzThreads, smem);

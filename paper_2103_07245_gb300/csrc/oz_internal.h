@@ -31,6 +31,7 @@ inline size_t oz_digit_bytes(int64_t rows, int64_t K) { return 2 * (size_t)kOzDi
 struct OzGeom {
     int64_t tiles = 0;
     int NT = 1, KI = 1, G = 1, smax = 1, upper = 0;
+    int lock = 1;   // > 1: the NT column tiles of a row tile on NT CTAs in lockstep
     int64_t part_doubles = 0;
 };
 OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms);
