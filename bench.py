@@ -124,13 +124,16 @@ def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
     """Roofline of one FP64-emulated product launch (k_oz_gemm): rows x K
     operand in 8 BF16 digits, l columns in 48-column tiles.
 
-    Bytes: the digits of A, read once per column tile (16 bytes per element
-    and tile), the panel digits, the FP64 partials.  Flops: the 36 digit
-    products per element the tensor pipe executes (N padded to the tiles)."""
+    Bytes: the digits of A (16 bytes per element), read from DRAM once per
+    pass when the 2 .. 8 column tiles of a row tile run in lockstep (else once
+    per column tile), the panel digits, the FP64 partials.  Flops: the 36
+    digit products per element the tensor pipe executes (N padded to the
+    tiles); `tensor_frac_l` counts them on the l columns alone."""
     nt = (l + 47) // 48
     t = avg_ms / 1e3
     hw_flops = 36 * 2.0 * rows * K * nt * 48
-    nbytes = 16.0 * rows * K * nt + 16.0 * K * nt * 48 + 8.0 * rows * nt * 48
+    reads = 1 if 2 <= nt <= 8 else nt
+    nbytes = 16.0 * rows * K * reads + 16.0 * K * nt * 48 + 8.0 * rows * nt * 48
     t_tensor = hw_flops / (tc_peak * 1e12)
     t_hbm = nbytes / (hbm_peak * 1e9)
     tensor = t_tensor >= t_hbm
@@ -140,8 +143,9 @@ def oz_roofline(rows, K, l, avg_ms, hbm_peak, tc_peak):
             "bound": "tensor" if tensor else "hbm", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s" if tensor else "GB/s", "frac": ach / peak,
             "achieved_basis": "tensor-pipe MMA flops (36 digit products, N padded to %d)" % (nt * 48)
-            if tensor else "bytes of the digits of A per column tile + panel digits + partials",
+            if tensor else "bytes of the digits of A (once per pass) + panel digits + partials",
             "tensor_frac": hw_flops / t / 1e12 / tc_peak, "hbm_frac": nbytes / t / 1e9 / hbm_peak,
+            "tensor_frac_l": 36 * 2.0 * rows * K * l / t / 1e12 / tc_peak,
             # the same launch on the algorithmic bytes of the FP64 product it replaces
             # (A once in FP64, the panels): what the digit re-reads cost
             "frac_algorithmic_bytes": (8.0 * rows * K + 8.0 * (rows + K) * l) / t / 1e9 / hbm_peak,
@@ -839,8 +843,9 @@ def run_dense(args, w, world, rank, local):
                     "traffic": read_traffic("dgemm_skinny_fp64_8000"),
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (not in MEASURED_PEAKS.json)",
                     "peak_probe": fp64_probe, "frac_probe": (achieved / fp64_probe) if achieved else None,
-                    "peak_probe_source": "pbpqlp_fp64_rate_probe: 8 independent FMA chains per thread, 4 CTAs per SM, "
-                                         "CUDA events, measured in this run",
+                    "peak_probe_source": "pbpqlp_fp64_rate_probe: the shared-memory inner loop of a register-blocked "
+                                         "FP64 GEMM (4 x 4 accumulators per thread), best of 1, 2 and 4 CTAs "
+                                         "per SM, CUDA events, measured in this run",
                     "launches_timed": pass_launches, "avg_launch_ms": avg_pass_ms}
         dtype = "f64"
     elif w["mode"] == "FP64_EMU":
