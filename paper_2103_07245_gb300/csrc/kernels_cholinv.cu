@@ -78,8 +78,9 @@ constexpr int kCiNb = 16;
 // barrier every thread updates its rows below p (row i -= multiplier_i row p;
 // S only on and above the diagonal), and a second barrier publishes row p + 1.  The S part ends as D U and the I
 // part as L^{-1} = U^{-T}, so R_tt = D^{1/2} U and T_tt = D^{-1/2} L^{-1}.
-// No branches on the data: a failed pivot (not above its threshold, or not
-// finite) is recorded and the block discarded.  Rows and columns past the
+// No branches on the data: the pivots are checked after the elimination, and
+// a failed one (not above its threshold, or not finite) is recorded and the
+// block discarded.  Rows and columns past the
 // block's width nb are padded with identity.  Not inlined: inlined at both
 // call sites, its row array was given a stack frame.
 __device__ __noinline__ void chol_block16(double* __restrict__ W, const double* __restrict__ Dnx,
@@ -100,17 +101,13 @@ __device__ __noinline__ void chol_block16(double* __restrict__ W, const double* 
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     double* Mv = W + kCiNb * 32;   // 16: the multipliers S[p][i] / d_p of the current pivot
-    int f = 0;
 #pragma unroll
     for (int p = 0; p < kCiNb; ++p) {
-        // warp 0: 1/d_p and the multipliers (each FP64 warp instruction occupies a
-        // sub-partition's FP64 unit for 64 cycles, so the other warps do not repeat them)
+        // warp 0: 1/d_p and the multipliers, four FP64 instructions (each FP64 warp
+        // instruction occupies a sub-partition's FP64 unit for 64 cycles, so the
+        // other warps do not repeat them, and the pivots are checked after the loop)
         if (w == 0) {
-            const double d = W[p * 32 + p];
-            const double th = p < nb ? thr[a0 + p] : 0.0;
-            const int fp = !isfinite(d) ? 2 : (!(d > th) ? 1 : 0);
-            f = f ? f : fp;
-            const double cp = rcp_gs(d);
+            const double cp = rcp_gs(W[p * 32 + p]);
             if (c > p && c < kCiNb) Mv[c] = W[p * 32 + c] * cp;
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -125,15 +122,28 @@ __device__ __noinline__ void chol_block16(double* __restrict__ W, const double* 
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
     }
+    // The pivots d_i = W[i][i] (row i is final after pivot i - 1), one per lane:
+    // every warp forms the 16 values 1 / sqrt(d_i) in one instruction sequence,
+    // and warp 0 checks them; the first failed pivot in order decides the flag
+    // (2: not finite, 1: not above its threshold), as a check at each pivot would.
+    const int il = c & (kCiNb - 1);
+    const double dl = W[il * 33];
+    const double rsl = rsqrt_nr(dl);
+    if (w == 0) {
+        const double th = il < nb ? thr[a0 + il] : 0.0;
+        const int fp = c >= kCiNb ? 0 : (!isfinite(dl) ? 2 : (!(dl > th) ? 1 : 0));
+        const unsigned bad = __ballot_sync(0xffffffffu, fp != 0);
+        const int f = bad ? __shfl_sync(0xffffffffu, fp, __ffs((int)bad) - 1) : 0;
+        if (c == 0) *s_fail = f;
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = w + 4 * r;
-        const double di = W[i * 32 + i];
-        const double rs = rsqrt_nr(di);
+        const double rs = __shfl_sync(0xffffffffu, rsl, i);
+        const double di = __shfl_sync(0xffffffffu, dl, i);
         if (!idl) Rtt[i * kCiNb + c] = (i < c) ? v[r] * rs : (i == c ? di * rs : 0.0);
         else Ttt[i * kCiNb + (c - kCiNb)] = v[r] * rs;   // row i of L^{-1} scaled by 1/sqrt(d_i)
     }
-    if (t == 0) *s_fail = f;
 }
 
 // Own S columns of block rows [a0, a0 + 16) into Dnx of every CTA of the

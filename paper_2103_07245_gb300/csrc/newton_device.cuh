@@ -51,18 +51,26 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 // 1/d for a positive normal double in one Goldschmidt step: d = m 2^k with m
 // in [1, 2), y0 an FP32 seed for 1/m (relative error e0 < 2^-22), e = 1 - m y0,
 // 1/m = y0 (1 + e + e^2 + ...) truncated after e^2 (error e^3 < 2^-66, below
-// FP64 rounding); the scale 2^-k is applied to the seed in two normal factors
-// off the dependent chain.  No branches: zero, subnormal, negative and
-// non-finite d give meaningless (but finite or NaN) results, so callers check
-// d themselves.  Within 2 ulp of the correctly rounded 1/d for normal d.
+// FP64 rounding).  The scale 2^-k goes into the seed's exponent field with an
+// integer subtraction (exact while the result is normal, i.e. k <= 1021, since
+// y0 lies in (1/2, 1]), so the chain holds three FP64 instructions; d >= 2^1022
+// takes two FP64 multiplications by normal factors instead.  No checks: zero,
+// subnormal, negative and non-finite d give meaningless (but finite or NaN)
+// results, so callers check d themselves.  Within 2 ulp of the correctly
+// rounded 1/d for normal d.
 __device__ __forceinline__ double rcp_gs(double d) {
     const long long b = __double_as_longlong(d);
     const int k = (int)((b >> 52) & 0x7FF) - 1023;
     const double m = __longlong_as_double((b & 0x800FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
     const double y0 = (double)__frcp_rn((float)m);
-    const int k1 = k >> 1, k2 = k - k1;
-    const double ys = (y0 * __longlong_as_double((long long)(1023 - k1) << 52)) *
-                      __longlong_as_double((long long)(1023 - k2) << 52);
+    double ys;
+    if (k <= 1021) {
+        ys = __longlong_as_double(__double_as_longlong(y0) - ((long long)k << 52));
+    } else {
+        const int k1 = k >> 1, k2 = k - k1;
+        ys = (y0 * __longlong_as_double((long long)(1023 - k1) << 52)) *
+             __longlong_as_double((long long)(1023 - k2) << 52);
+    }
     const double e = fma(-m, y0, 1.0);
     const double t = fma(e, e, e);
     return fma(ys, t, ys);
