@@ -24,10 +24,11 @@
 // and at the end of a segment writes the FP64 partial
 // (2^28 hi + lo) 2^(e_i + f_j - 63), rounded once to FP64 with integer
 // operations.  A CTA that ran the whole contraction of a tile writes C;
-// otherwise each epilogue warp publishes its 32 x 16 slice of exact int64
-// sums and counts in on a per-slice counter, and the last contributor adds
-// them (exactly, so the result does not depend on the split) and writes C,
-// then clears the counter.
+// otherwise each epilogue warp adds its 32 x 16 slice of exact int64 sums
+// into the tile's accumulator with 64-bit integer reductions and counts in on
+// a per-slice counter, and the last contributor reads the accumulator once
+// (the sum is exact, so the result does not depend on the split or the
+// order), writes C, and clears the accumulator and the counter.
 //
 // MMAs.  The eight Y digit tiles of a stage sit one after the other in shared
 // memory, so X digit s times Y digits t0 .. t0 + c - 1 is one MMA of N = 48 c
@@ -290,7 +291,7 @@ __device__ __forceinline__ void oz_store(double* crow, int ncol, int exr, const 
 template <bool kLock>
 __global__ void __maxnreg__(128)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t T, int NT,
-          int upper, int lock_, int64_t G, int KI, int smax, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
+          int upper, int lock_, int64_t G, int KI, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
           const int* __restrict__ ey_raw, double* __restrict__ part, int* __restrict__ cnt, double* __restrict__ Cout,
           int64_t ldc, uint32_t* __restrict__ status, uint64_t timeout_ns, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
@@ -442,14 +443,16 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     // the whole contraction of this tile ran here
                     if (row < Rx) oz_store(crow, ncol, exr, ey_raw + col0, hi, lo);
                 } else {
-                    // stream-K fix-up per 32 x 16 slice: publish the integer sums; the
-                    // CTA that completes the slice adds all of them (exact, so the
-                    // order is immaterial) and writes C
-                    int64_t* slot = (int64_t*)part + ((size_t)blockIdx.x * smax + (size_t)tl) * (size_t)(2 * kOzBM * kOzBN);
+                    // stream-K fix-up per 32 x 16 slice: every contributor adds its integer
+                    // sums into the tile's accumulator (64-bit integer reductions: exact
+                    // and order-free, modulo 2^64 like the sums themselves), and the one
+                    // that completes the slice reads it once, writes C and clears it
+                    unsigned long long* acc = (unsigned long long*)part + (size_t)rtile * (size_t)(2 * kOzBM * kOzBN);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        slot[(size_t)(g * 16 + j) * kOzBM + rloc] = (int64_t)hi[j];
-                        slot[(size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc] = (int64_t)lo[j];
+                        atomicAdd(acc + (size_t)(g * 16 + j) * kOzBM + rloc, (unsigned long long)hi[j]);
+                        atomicAdd(acc + (size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc,
+                                  (unsigned long long)lo[j]);
                     }
                     __threadfence();
                     __syncwarp();
@@ -460,22 +463,17 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
                     const int64_t cf = sk_owner(it0, T, G), cl = sk_owner(it1, T, G);
                     if (old == (int)(cl - cf)) {
                         __threadfence();
-                        // the published sums are re-read with the others: hi / lo now add them up
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
-                        for (int64_t c2 = cf; c2 <= cl; ++c2) {
-                            const long long* s2 = (const long long*)part +
-                                                  ((size_t)(kLock ? c2 * lock + blockIdx.x % lock : c2) * smax +
-                                                   (size_t)(tile - sk_begin(c2, T, G) / KI)) *
-                                                      (size_t)(2 * kOzBM * kOzBN);
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                hi[j] += (uint64_t)__ldcg(s2 + (size_t)(g * 16 + j) * kOzBM + rloc);
-                                lo[j] += (uint64_t)__ldcg(s2 + (size_t)(kOzBM * kOzBN) + (size_t)(g * 16 + j) * kOzBM + rloc);
-                            }
+                        for (int j = 0; j < 16; ++j) {
+                            unsigned long long* ph = acc + (size_t)(g * 16 + j) * kOzBM + rloc;
+                            unsigned long long* pl = ph + (size_t)(kOzBM * kOzBN);
+                            hi[j] = __ldcg(ph);
+                            lo[j] = __ldcg(pl);
+                            *ph = 0ull;   // ready for the next product
+                            *pl = 0ull;
                         }
                         if (row < Rx) oz_store(crow, ncol, exr, ey_raw + col0, hi, lo);
-                        if (lane == 0) *ctr = 0;   // ready for the next product
+                        if (lane == 0) *ctr = 0;
                     }
                 }
 #pragma unroll
@@ -945,17 +943,15 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     const int64_t T = (g.lock > 1 ? MT : g.tiles) * g.KI;
     const int sms = num_sms / g.lock;
     // at least min_it iterations (32-deep chunks) per CTA: small products use
-    // fewer CTAs, with fewer partials to fix up.  Short contractions (the
-    // CholeskyQR solve and Qb, K = l) take 4, which measured 20% faster for
-    // them; long ones (Grams, passes over A) 16.
-    const int64_t min_it = g.KI <= 8 ? 4 : 16;
+    // fewer CTAs.  Short contractions (the CholeskyQR solve and Qb, K = l) and
+    // the Grams (a few tiles over a long K, split over many CTAs) take 4; the
+    // passes over A take 16 (8 measured the same).
+    const int64_t min_it = (g.KI <= 8 || upper) ? 4 : 16;
     const int64_t want = (T + min_it - 1) / min_it;
     int Gv = (int)(want < sms ? want : sms);
     if (Gv < 1) Gv = 1;
-    const int64_t share = (T + Gv - 1) / Gv;
     g.G = Gv * g.lock;
-    g.smax = (int)((share + g.KI - 1) / g.KI + 1);
-    g.part_doubles = (int64_t)g.G * g.smax * 2 * kOzBM * kOzBN;   // two int64 sums per element
+    g.part_doubles = g.tiles * 2 * kOzBM * kOzBN;   // a tile's two int64 accumulators per element
     return g;
 }
 
@@ -975,10 +971,10 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
     const int64_t T = (g.lock > 1 ? g.tiles / g.NT : g.tiles) * (int64_t)g.KI;
     if (g.lock > 1)
         k_oz_gemm<true><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, g.lock, (int64_t)(g.G / g.lock), g.KI,
-                                                      g.smax, X.rows, Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
+                                                      X.rows, Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
                                                       2000000000ull, cond);
     else
-        k_oz_gemm<false><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, 1, (int64_t)g.G, g.KI, g.smax, X.rows,
+        k_oz_gemm<false><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, 1, (int64_t)g.G, g.KI, X.rows,
                                                        Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
                                                        2000000000ull, cond);
     count_launches(1);

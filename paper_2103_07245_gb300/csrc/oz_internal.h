@@ -27,10 +27,11 @@ inline size_t oz_digit_bytes(int64_t rows, int64_t K) { return 2 * (size_t)kOzDi
 
 // Work split of one product C (Mrows x N) = X Y^T over K: 128 x 48 tiles
 // (with `upper`, only the tiles that touch the upper triangle), stream-K over
-// (tile, 32-deep window) iterations, FP64 partials of kOzBM x kOzBN per slot.
+// (tile, 32-deep chunk) iterations; a tile split between CTAs is summed in
+// its own pair of int64 accumulators per element (part_doubles in all).
 struct OzGeom {
     int64_t tiles = 0;
-    int NT = 1, KI = 1, G = 1, smax = 1, upper = 0;
+    int NT = 1, KI = 1, G = 1, upper = 0;
     int lock = 1;   // > 1: the NT column tiles of a row tile on NT CTAs in lockstep
     int64_t part_doubles = 0;
 };
@@ -38,8 +39,9 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms);
 
 // C[i*ldc + j] = sum_k X[i][k] Y[j][k] (FP64), i < X.rows, j < Y.rows, in one
 // launch.  X.K == Y.K is the contraction length.  part: >= g.part_doubles
-// doubles; cnt: >= 12 g.tiles ints, zero on entry and left zero (a call that
-// timed out may leave them nonzero: clear them before the next one).
+// doubles (int64 accumulators); part and cnt (>= 12 g.tiles ints) zero on
+// entry and left zero (a call that timed out may leave them nonzero: clear
+// them before the next one).
 // cond (device, optional): nothing runs when *cond == 0.
 cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGeom& g, double* part, int* cnt,
                               double* C, int64_t ldc, uint32_t* status, const int* cond, cudaStream_t s,

@@ -56,6 +56,7 @@ struct pbpqlp_plan_s {
     OzGeom og_gm, og_gn, og_nn, og_tn;  // Grams over m / n rows; C = A Y; C = A^T Y
     size_t off_ozE1 = 0, off_ozE2 = 0, off_ozS1 = 0, off_ozS2 = 0, off_ozpart = 0, off_ozEb = 0, off_ozEs = 0;
     size_t off_ozcnt = 0, ozcnt_bytes = 0;   // stream-K fix-up counters (12 per tile), cleared per call
+    size_t ozpart_bytes = 0;                 // stream-K fix-up accumulators (int64), cleared per call
     OzGeom og_qb;                       // Qb = Pbar Ptil (n rows, K = l)
     bool chol_inv = false;              // cluster Cholesky with T = R^{-T}; CholeskyQR solve as a digit product
     OzGeom og_tr_m, og_tr_n;            // Q = C T^T over m or n rows (K = l)
@@ -646,7 +647,8 @@ int pbpqlp_plan(pbpqlp_plan_t* out, int64_t m, int64_t n, int k, int p, int q, u
         P->off_ozS2 = take(sz);
         P->off_ozEb = take(sizeof(int) * (size_t)mx);
         P->off_ozEs = take(sizeof(int) * ne);
-        P->off_ozpart = take(sizeof(double) * (size_t)pd);
+        P->ozpart_bytes = sizeof(double) * (size_t)pd;
+        P->off_ozpart = take(P->ozpart_bytes);
         {
             int64_t mt = 0;
             for (const OzGeom* g : {&P->og_gm, &P->og_gn, &P->og_qb, &P->og_nn, &P->og_tn, &P->og_tr_m, &P->og_tr_n})
@@ -886,6 +888,7 @@ static int enqueue_factor(pbpqlp_plan_t P, const void* Av, int64_t lda, int a_dt
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
+    if (w.ozpart) PBQ_TRY(cudaMemsetAsync(w.ozpart, 0, P->ozpart_bytes, s));
     const int a_f32 = a_dtype == PBPQLP_F32;
     if (!P->stream_a && mixed && (rc = tc_prepare_a(P, w, Av, a_f32, lda))) return rc;
     if (!P->stream_a && P->emu && (rc = emu_prepare_a(P, w, Av, a_f32, lda))) return rc;
@@ -936,6 +939,7 @@ int pbpqlp_factor_csr(pbpqlp_plan_t P, const int64_t* rowptr, const int32_t* col
     const int l = P->l;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
+    if (w.ozpart) PBQ_TRY(cudaMemsetAsync(w.ozpart, 0, P->ozpart_bytes, s));
     // A^T as a CSR (checks the structure first), once per call
     CsrT at;
     void* scratch = (char*)workspace + (P->total + 255) / 256 * 256;
@@ -972,6 +976,7 @@ int pbpqlp_sketch(pbpqlp_plan_t P, const void* A, int64_t lda, int a_dtype, int 
     cudaStream_t s = P->stream;
     PBQ_TRY(cudaMemsetAsync(w.status, 0, 256, s));
     if (w.ozcnt) PBQ_TRY(cudaMemsetAsync(w.ozcnt, 0, P->ozcnt_bytes, s));
+    if (w.ozpart) PBQ_TRY(cudaMemsetAsync(w.ozpart, 0, P->ozpart_bytes, s));
     (void)rowsY;
     if (P->stream_a && mixed) return tc_pass_stream(P, w, trans != 0, A, a_dtype == PBPQLP_F32, lda, Y, ldy, ncols, C, ldc, false);
     if (P->stream_a) return emu_pass_stream(P, w, trans != 0, A, a_dtype == PBPQLP_F32, lda, Y, ldy, ncols, C, ldc, false);
