@@ -291,7 +291,7 @@ __device__ __forceinline__ void oz_store(double* crow, int ncol, int exr, const 
 template <bool kLock>
 __global__ void __maxnreg__(128)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int64_t T, int NT,
-          int upper, int lock_, int64_t G, int KI, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
+          int upper, int lock_, int64_t G, int KI, int tilewise, int64_t Rx, int64_t Ry, const int* __restrict__ ex_raw,
           const int* __restrict__ ey_raw, double* __restrict__ part, int* __restrict__ cnt, double* __restrict__ Cout,
           int64_t ldc, uint32_t* __restrict__ status, uint64_t timeout_ns, const int* __restrict__ cond) {
     if (cond && *cond == 0) return;
@@ -311,7 +311,9 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
     // the virtual tiles are then the row tiles.
     const int lock = kLock ? lock_ : 1;
     const int64_t c = kLock ? blockIdx.x / lock : blockIdx.x;
-    const int64_t it_begin = sk_begin(c, T, G), it_end = sk_begin(c + 1, T, G);
+    // tilewise: whole tiles per CTA (short contractions: no partials, no fix-up)
+    const int64_t it_begin = tilewise ? sk_begin(c, T / KI, G) * KI : sk_begin(c, T, G);
+    const int64_t it_end = tilewise ? sk_begin(c + 1, T / KI, G) * KI : sk_begin(c + 1, T, G);
     const uint64_t deadline = globaltimer() + timeout_ns;
 
     if (threadIdx.x == 0) {
@@ -949,6 +951,14 @@ OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms) {
     const int64_t min_it = (g.KI <= 8 || upper) ? 4 : 16;
     const int64_t want = (T + min_it - 1) / min_it;
     int Gv = (int)(want < sms ? want : sms);
+    // short contractions (K <= 256) run whole tiles on each CTA: splitting them
+    // gains no parallelism worth its fix-up (measured: the fix-up of a 4-chunk
+    // split took as long as the MMAs)
+    g.tilewise = g.KI <= 8 ? 1 : 0;
+    if (g.tilewise) {
+        const int64_t vt = T / g.KI;
+        Gv = (int)(vt < sms ? vt : sms);
+    }
     if (Gv < 1) Gv = 1;
     g.G = Gv * g.lock;
     g.part_doubles = g.tiles * 2 * kOzBM * kOzBN;   // a tile's two int64 accumulators per element
@@ -971,10 +981,10 @@ cudaError_t launch_oz_product(const OzOperand& X, const OzOperand& Y, const OzGe
     const int64_t T = (g.lock > 1 ? g.tiles / g.NT : g.tiles) * (int64_t)g.KI;
     if (g.lock > 1)
         k_oz_gemm<true><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, g.lock, (int64_t)(g.G / g.lock), g.KI,
-                                                      X.rows, Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
+                                                      g.tilewise, X.rows, Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
                                                       2000000000ull, cond);
     else
-        k_oz_gemm<false><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, 1, (int64_t)g.G, g.KI, X.rows,
+        k_oz_gemm<false><<<g.G, kOzThreads, smem, s>>>(mx, my, T, g.NT, g.upper, 1, (int64_t)g.G, g.KI, g.tilewise, X.rows,
                                                        Y.rows, X.eraw, Y.eraw, part, cnt, C, ldc, status,
                                                        2000000000ull, cond);
     count_launches(1);

@@ -33,6 +33,7 @@ struct OzGeom {
     int64_t tiles = 0;
     int NT = 1, KI = 1, G = 1, upper = 0;
     int lock = 1;   // > 1: the NT column tiles of a row tile on NT CTAs in lockstep
+    int tilewise = 0;   // 1: whole tiles per CTA (no split, no fix-up)
     int64_t part_doubles = 0;
 };
 OzGeom oz_geometry(int64_t Mrows, int N, int64_t K, bool upper, int num_sms);
