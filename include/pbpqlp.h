@@ -454,6 +454,20 @@ int64_t pbpqlp_kernel_launch_count(void);
 int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, double* rsqrt, double* rcp_gs, void* stream);
 
 /*
+ * Diagnostic of the conversion that ends every FP64-accurate digit product
+ * (not part of the paper's method): the digit products accumulate each
+ * output as two exact 64-bit integer sums hi and lo, worth (hi 2^28 + lo) 2^e.
+ * For each of the n triples (hi[i], lo[i], e[i]) (device arrays), writes
+ * fast[i] from the form the kernels use (64-bit operations and one hardware
+ * integer-to-double conversion) and exact[i] from the reference form (92-bit
+ * integer normalisation); both are the value rounded once to the nearest
+ * double, ties to even, for |hi| < 2^62 (device outputs).  Asynchronous on
+ * `stream`; PBPQLP_EINVAL for n < 0 or null pointers with n > 0.
+ */
+int pbpqlp_oz_convert_check(const int64_t* hi, const int64_t* lo, const int* e, int64_t n, double* fast,
+                            double* exact, void* stream);
+
+/*
  * Measured FP64 FMA issue rate of the current device (a microbenchmark, not
  * part of the method): CTAs of 256 threads, 1, 2 and 4 per SM, running the
  * inner loop of a register-blocked FP64 GEMM (operands from shared memory,

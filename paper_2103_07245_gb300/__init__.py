@@ -159,6 +159,8 @@ def load(build_if_missing: bool = False):
     L.pbpqlp_fp64_rate_probe.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp]
     L.pbpqlp_fp64_rate_probe.restype = ci
     L.pbpqlp_newton_check.restype = ci
+    L.pbpqlp_oz_convert_check.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.pbpqlp_oz_convert_check.restype = ci
     _lib = L
     return L
 
@@ -354,6 +356,13 @@ def pbpqlp_newton_check(d, n, rcp, rsqrt, rcp_gs=None, stream=None):
     for n device doubles (a diagnostic)."""
     _check(load().pbpqlp_newton_check(_ptr(d), int(n), _ptr(rcp), _ptr(rsqrt), _ptr(rcp_gs), _stream(stream)),
            "pbpqlp_newton_check")
+
+
+def pbpqlp_oz_convert_check(hi, lo, e, n, fast, exact, stream=None):
+    """Both forms of the digit products' exact-integer-to-FP64 conversion of
+    (hi 2^28 + lo) 2^e for n device triples (a diagnostic)."""
+    _check(load().pbpqlp_oz_convert_check(_ptr(hi), _ptr(lo), _ptr(e), int(n), _ptr(fast), _ptr(exact),
+                                          _stream(stream)), "pbpqlp_oz_convert_check")
 
 
 def pbpqlp_fp64_rate_probe(sink, stream=None) -> float:

@@ -3,10 +3,14 @@
 // square root and the one-step Goldschmidt reciprocal that replace FP64
 // division and square root on the pivot chains of the Cholesky and QR
 // kernels, so that tests can hold them to an ulp bound against correctly
-// rounded results.
+// rounded results; pbpqlp_oz_convert_check evaluates both forms of the
+// exact-integer-to-FP64 conversion that ends every FP64-accurate digit
+// product, so that tests can hold them to Python's correctly rounded
+// integer-to-float conversion.
 #include "../../include/pbpqlp.h"
 #include "internal.h"
 #include "newton_device.cuh"
+#include "oz_convert.cuh"
 
 namespace {
 
@@ -28,6 +32,28 @@ extern "C" int pbpqlp_newton_check(const double* d, int64_t n, double* rcp, doub
     if (n == 0) return PBPQLP_OK;
     const int64_t blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
     k_newton_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, d, rcp, rsqrt, rcp_gs);
+    pbq::count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA;
+}
+
+namespace {
+
+__global__ void k_oz_convert_check(int64_t n, const int64_t* __restrict__ hi, const int64_t* __restrict__ lo,
+                                   const int* __restrict__ e, double* __restrict__ fast, double* __restrict__ exact) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        fast[i] = pbq::oz_to_double_fast(hi[i], lo[i], e[i]);
+        exact[i] = pbq::oz_to_double(hi[i], lo[i], e[i]);
+    }
+}
+
+}  // namespace
+
+extern "C" int pbpqlp_oz_convert_check(const int64_t* hi, const int64_t* lo, const int* e, int64_t n, double* fast,
+                                       double* exact, void* stream) {
+    if (n < 0 || (n > 0 && (!hi || !lo || !e || !fast || !exact))) return PBPQLP_EINVAL;
+    if (n == 0) return PBPQLP_OK;
+    const int64_t blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    k_oz_convert_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, hi, lo, e, fast, exact);
     pbq::count_launches(1);
     return cudaGetLastError() == cudaSuccess ? PBPQLP_OK : PBPQLP_ECUDA;
 }

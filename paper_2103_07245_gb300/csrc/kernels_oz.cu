@@ -50,6 +50,7 @@
 #include "internal.h"
 #include "oz_internal.h"
 #include "tc_device.cuh"
+#include "oz_convert.cuh"
 
 namespace pbq {
 
@@ -141,47 +142,6 @@ __device__ __forceinline__ int64_t sk_owner(int64_t it, int64_t T, int64_t G) {
     while (c + 1 < G && sk_begin(c + 1, T, G) <= it) ++c;
     while (c > 0 && sk_begin(c, T, G) > it) --c;
     return c;
-}
-
-// (hi 2^28 + lo) 2^e as the nearest double (ties to even), with integer
-// operations only (FP64 arithmetic runs at 2 lanes per clock per SM on GB300
-// and would dominate the epilogue): the 92-bit magnitude is normalised with a
-// leading-zero count and rounded on its dropped bits.  Results outside the
-// normal range take the FP64 route (x 2^k in exact power-of-two factors).
-__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
-__device__ __forceinline__ double oz_to_double(int64_t hi, int64_t lo, int e) {
-    const __int128 N = ((__int128)hi << 28) + (__int128)lo;
-    if (N == 0) return 0.0;
-    const bool neg = N < 0;
-    const unsigned __int128 U = neg ? (unsigned __int128)(-N) : (unsigned __int128)N;
-    const uint64_t uh = (uint64_t)(U >> 64), ul = (uint64_t)U;
-    const int p = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);   // leading 1 at bit p
-    uint64_t m;
-    int pe = p;
-    if (p <= 52) {
-        m = ul << (52 - p);
-    } else {
-        const int sh = p - 52;
-        m = (uint64_t)(U >> sh);
-        const unsigned __int128 rem = U & ((((unsigned __int128)1) << sh) - 1);
-        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-        if (rem > half || (rem == half && (m & 1))) {
-            ++m;
-            if (m >> 53) { m >>= 1; ++pe; }
-        }
-    }
-    const int biased = pe + e + 1023;
-    if (biased <= 0 || biased >= 2047) {
-        // subnormal or overflowing result: m 2^(pe - 52 + e) in exact power-of-two factors
-        const double v = neg ? -(double)m : (double)m;   // m < 2^53: exact
-        int k = pe - 52 + e;
-        const int k1 = k > 900 ? 900 : (k < -900 ? -900 : k);
-        k -= k1;
-        const int k2 = k > 900 ? 900 : (k < -900 ? -900 : k);
-        return v * pow2i(k1) * pow2i(k2) * pow2i(k - k2);
-    }
-    const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)biased << 52) | (m & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
 }
 
 // BF16 bits of a small integer d (|d| < 2^22): exact through FP32.
@@ -279,7 +239,7 @@ __device__ __forceinline__ void oz_store(double* crow, int ncol, int exr, const 
             const int eyr = ey[j];
             crow[j] = (exr >= 2047 || eyr >= 2047)
                           ? __longlong_as_double(0x7FF8000000000000LL)
-                          : oz_to_double((int64_t)hi[j], (int64_t)lo[j], exr + eyr - 2 * 1021 - 63);
+                          : oz_to_double_fast((int64_t)hi[j], (int64_t)lo[j], exr + eyr - 2 * 1021 - 63);
         }
     }
 }
